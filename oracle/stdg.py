@@ -1,0 +1,518 @@
+"""Space-time DG slab residual by full tensor Gauss quadrature in physical space.
+
+Test infrastructure (see the package docstring).  Everything here follows the
+paper's definitions literally:
+
+* trial functions (Sec. 5.1): U = DF^{-T} [ l_m(xi) L_j(x^) L_k(y^) L_l(z^) e_c ],
+  test functions: V = DF^{-T} [ L_i(xi) L_j L_k L_l e_c ], i < q
+  (covariant transformation, Sec. 2.3), xi = (t - t0) / dt;
+* the bilinear form (Eq. bilinearform:C)
+      C_h(U, V) = (eps d_t E, v) + (mu d_t H, w) - (H, curl v) + (curl E, w)
+                  + <{H}, [v]_T>_{F0 u Fb} - <[E]_T, {w}>_{F0 u Fb},
+  with {v} = (v1 + v2)/2, [v]_T = n1 x v1 + n2 x v2 on interior faces and
+  {v} = v, [v]_T = n x v on boundary faces (Sec. 2.4);
+* the stabilisation S_h of Eq. bilinearform:S on interior faces whose two
+  elements have different temporal degrees, with the projector onto the
+  common temporal test space computed as an L2 projection by quadrature;
+* the load L(V) = (J, v) - <n x g, w>_{Fb} and the residual
+  R_h(V) = B_h(U, V) - L(V) (Eq. residual).
+
+Inner products are space-time integrals over I_n x K; they are evaluated with
+p+2 Gauss points per spatial direction and q+2 in time (for a face shared by
+elements of different degree: the larger of the two).  Physical fields are
+obtained from reference fields through DF^{-T} (values) and (1/J) DF (curl,
+the Piola identity, checked against finite differences in the tests).
+
+Coefficient layout of one element (trial): [field E,H][component x,y,z]
+[temporal mode m = 0..q][spatial index s], s = (l (p+1) + k)(p+1) + j with j
+the x^ degree.  Test/residual layout: the same with modes i = 0..q-1.
+
+Face neighbours are found from the element-to-vertex lists (shared vertex
+quadruples); the neighbour's reference coordinates of every face quadrature
+point are obtained by inverting its map with Newton's method.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import basis, geometry
+
+_LEVI = np.zeros((3, 3, 3))
+_LEVI[0, 1, 2] = _LEVI[1, 2, 0] = _LEVI[2, 0, 1] = 1.0
+_LEVI[0, 2, 1] = _LEVI[2, 1, 0] = _LEVI[1, 0, 2] = -1.0
+
+# reference corners on face (d, s): vertices with bit d equal to s
+_FACE_VERTS = [[v for v in range(8) if ((v >> d) & 1) == s] for d in range(3) for s in (0, 1)]
+
+
+def _cross(a, b):
+    a, b = np.broadcast_arrays(a, b)
+    return np.cross(a, b, axis=-1)
+
+
+# ----------------------------------------------------------------------------
+# spatial basis tables
+# ----------------------------------------------------------------------------
+
+def spatial_basis(p: int, xh: np.ndarray):
+    """phi[P, s] and grad phi[P, s, 3] of L_j(x^)L_k(y^)L_l(z^) at points xh [P, 3]."""
+    n = p + 1
+    Lx = basis.legendre(p, xh[:, 0])  # [n, P]
+    Ly = basis.legendre(p, xh[:, 1])
+    Lz = basis.legendre(p, xh[:, 2])
+    dLx = basis.legendre_deriv(p, xh[:, 0])
+    dLy = basis.legendre_deriv(p, xh[:, 1])
+    dLz = basis.legendre_deriv(p, xh[:, 2])
+    P = xh.shape[0]
+    phi = np.empty((P, n, n, n))  # [P, l, k, j]
+    g = np.empty((P, n, n, n, 3))
+    for l in range(n):
+        for k in range(n):
+            for j in range(n):
+                phi[:, l, k, j] = Lx[j] * Ly[k] * Lz[l]
+                g[:, l, k, j, 0] = dLx[j] * Ly[k] * Lz[l]
+                g[:, l, k, j, 1] = Lx[j] * dLy[k] * Lz[l]
+                g[:, l, k, j, 2] = Lx[j] * Ly[k] * dLz[l]
+    return phi.reshape(P, n ** 3), g.reshape(P, n ** 3, 3)
+
+
+def _grid3(nq: int):
+    x, w = basis.gauss01(nq)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    W = np.einsum("i,j,k->ijk", w, w, w)
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1), W.ravel()
+
+
+def _face_grid(d: int, s: int, nq: int):
+    """Gauss points on reference face x^_d = s: points [A, 3], weights [A]."""
+    x, w = basis.gauss01(nq)
+    a1, a2 = [a for a in range(3) if a != d]
+    U, V = np.meshgrid(x, x, indexing="ij")
+    pts = np.zeros((nq * nq, 3))
+    pts[:, d] = float(s)
+    pts[:, a1] = U.ravel()
+    pts[:, a2] = V.ravel()
+    return pts, np.outer(w, w).ravel()
+
+
+# ----------------------------------------------------------------------------
+# mesh topology (from vertex ids only)
+# ----------------------------------------------------------------------------
+
+def face_neighbours(hexes: np.ndarray) -> np.ndarray:
+    """[n_elem, 6, 2] array (neighbour element, neighbour face) or -1, by shared vertex quadruples."""
+    ne = hexes.shape[0]
+    table = {}
+    out = np.full((ne, 6, 2), -1, dtype=np.int64)
+    for e in range(ne):
+        for f in range(6):
+            key = tuple(sorted(int(hexes[e, v]) for v in _FACE_VERTS[f]))
+            if key in table:
+                e2, f2 = table.pop(key)
+                out[e, f] = (e2, f2)
+                out[e2, f2] = (e, f)
+            else:
+                table[key] = (e, f)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# field evaluation
+# ----------------------------------------------------------------------------
+
+@dataclass
+class _Pts:
+    """Geometry and basis at a set of reference points of one element."""
+    xh: np.ndarray      # [P, 3]
+    x: np.ndarray       # [P, 3] physical
+    DF: np.ndarray      # [P, 3, 3]
+    DFinv: np.ndarray   # [P, 3, 3]
+    J: np.ndarray       # [P]
+    phi: np.ndarray     # [P, N3]
+    gphi: np.ndarray    # [P, N3, 3]
+
+
+def _points(X8, p, xh) -> _Pts:
+    DF = geometry.jacobian(X8, xh)
+    J = np.linalg.det(DF)
+    if np.any(J <= 0):
+        raise ValueError("element map with non-positive Jacobian")
+    phi, gphi = spatial_basis(p, xh)
+    return _Pts(xh, geometry.map_points(X8, xh), DF, np.linalg.inv(DF), J, phi, gphi)
+
+
+def _fields(u, pts: _Pts, q: int, tau: np.ndarray, dt: float, derivs: bool = True):
+    """Physical E (or H) values, time derivative and curl at (tau x points).
+
+    u: [B, 3, q+1, N3] trial coefficients of one field (None means zero).
+    Returns val, dtval, curl, each [B, T, P, 3] (dtval, curl are None unless
+    ``derivs``).
+    """
+    if u is None:
+        return 0.0, 0.0, 0.0
+    B = u.shape[0]
+    P = pts.phi.shape[0]
+    lt = basis.trial_time(q, tau)        # [q+1, T]
+    S = (u.reshape(-1, u.shape[-1]) @ pts.phi.T).reshape(B, 3, q + 1, P)
+    ref = np.einsum("mt,bcmp->btpc", lt, S, optimize=True)      # reference field
+    val = np.einsum("pci,btpc->btpi", pts.DFinv, ref, optimize=True)  # DF^{-T} ref
+    if not derivs:
+        return val, None, None
+    dlt = basis.trial_time_deriv(q, tau)  # [q+1, T]
+    dref = np.einsum("mt,bcmp->btpc", dlt, S, optimize=True)
+    gp = pts.gphi.transpose(1, 0, 2).reshape(pts.gphi.shape[1], -1)   # [N3, P*3]
+    G = (u.reshape(-1, u.shape[-1]) @ gp).reshape(B, 3, q + 1, P, 3)
+    gref = np.einsum("mt,bcmpa->btpca", lt, G, optimize=True)   # d ref_c / d x^_a
+    # reference curl: (curl)_i = eps_{i a c} d_a ref_c
+    cref = np.einsum("iac,btpca->btpi", _LEVI, gref, optimize=True)
+    dtval = np.einsum("pci,btpc->btpi", pts.DFinv, dref, optimize=True) / dt
+    # Piola identity: curl (DF^{-T} ref) = (1/J) DF curl_ref
+    curl = np.einsum("pij,btpj->btpi", pts.DF, cref, optimize=True) / pts.J[None, None, :, None]
+    return val, dtval, curl
+
+
+def _test_project(a: np.ndarray, pts: _Pts, Lt: np.ndarray, wgt: np.ndarray) -> np.ndarray:
+    """sum over points of wgt * a . v for every test function v = DF^{-T} L_i phi_s e_d.
+
+    a: [B, T, P, 3] physical vector field; Lt: [q, T] temporal test factors;
+    wgt: [T, P] quadrature weights (including dt and the measure).
+    Returns [B, 3, q, N3].
+    """
+    # a . DF^{-T} e_d = (DF^{-1} a)_d
+    b = np.einsum("pdi,btpi->btpd", pts.DFinv, a) * wgt[None, :, :, None]
+    return np.einsum("it,ps,btpd->bdis", Lt, pts.phi, b, optimize=True)
+
+
+def _test_project_curl(a: np.ndarray, pts: _Pts, Lt: np.ndarray, wgt: np.ndarray) -> np.ndarray:
+    """sum over points of wgt * a . curl v, curl v = (1/J) DF (grad^ phi_s x e_d) L_i."""
+    # a . (1/J) DF (g x e_d) = (1/J) (DF^T a) . (g x e_d) = (1/J) ((DF^T a) x g)_d
+    b = np.einsum("pij,btpi->btpj", pts.DF, a) / pts.J[None, None, :, None]
+    b = b * wgt[None, :, :, None]
+    # ((b) x g)_d = eps_{d a c} b_a g_c
+    return np.einsum("it,dac,btpa,psc->bdis", Lt, _LEVI, b, pts.gphi, optimize=True)
+
+
+# ----------------------------------------------------------------------------
+# the oracle
+# ----------------------------------------------------------------------------
+
+class Oracle:
+    """Residual, assembly, slab solve and energy for one mesh.
+
+    mesh: dict with vert [nv,3], hex [ne,8], p [ne], q [ne], eps [ne], mu [ne].
+    """
+
+    def __init__(self, mesh: dict):
+        self.vert = np.asarray(mesh["vert"], dtype=np.float64)
+        self.hex = np.asarray(mesh["hex"], dtype=np.int64)
+        self.ne = self.hex.shape[0]
+        self.p = np.asarray(mesh["p"], dtype=np.int64).reshape(self.ne)
+        self.q = np.asarray(mesh["q"], dtype=np.int64).reshape(self.ne)
+        self.eps = np.asarray(mesh["eps"], dtype=np.float64).reshape(self.ne)
+        self.mu = np.asarray(mesh["mu"], dtype=np.float64).reshape(self.ne)
+        self.nbr = face_neighbours(self.hex)
+        n3 = (self.p + 1) ** 3
+        self.trial_sz = 6 * (self.q + 1) * n3
+        self.test_sz = 6 * self.q * n3
+        self.trial_off = np.concatenate([[0], np.cumsum(self.trial_sz)])
+        self.test_off = np.concatenate([[0], np.cumsum(self.test_sz)])
+        self._vol_cache = {}
+
+    # -- helpers -------------------------------------------------------------
+    def X8(self, e: int) -> np.ndarray:
+        return self.vert[self.hex[e]]
+
+    def trial_block(self, U: np.ndarray, e: int) -> np.ndarray:
+        """[..., 2, 3, q+1, N3] view of element e's trial coefficients (U [..., N_trial])."""
+        p, q = self.p[e], self.q[e]
+        blk = U[..., self.trial_off[e]:self.trial_off[e + 1]]
+        return blk.reshape(blk.shape[:-1] + (2, 3, q + 1, (p + 1) ** 3))
+
+    def _pts(self, e: int, p: int, xh: np.ndarray, tag) -> _Pts:
+        """Geometry/basis tables at reference points xh of element e.
+
+        Tables that only depend on the element's shape (not its position) are
+        cached, keyed by the vertex coordinates relative to vertex 0.
+        """
+        X8 = self.X8(e)
+        key = (p, tag, tuple(np.round(X8 - X8[0], 13).ravel()))
+        hit = self._vol_cache.get(key)
+        if hit is None:
+            if len(self._vol_cache) > 20000:
+                self._vol_cache.clear()
+            hit = _points(X8, p, xh)
+            self._vol_cache[key] = hit
+        return _Pts(hit.xh, geometry.map_points(X8, xh), hit.DF, hit.DFinv, hit.J, hit.phi, hit.gphi)
+
+    # -- volume terms ----------------------------------------------------------
+    def _volume(self, e, uE, uH, dt, t0, src):
+        """Volume part of R for element e: [B, 2, 3, q, N3]."""
+        p, q = int(self.p[e]), int(self.q[e])
+        X8 = self.X8(e)
+        xh, wx = _grid3(p + 2)
+        pts = self._pts(e, p, xh, ("vol", p + 2))
+        tau, wt = basis.gauss01(q + 2)
+        Lt = basis.legendre(q - 1, tau)  # [q, T]
+        wgt = dt * np.outer(wt, wx * pts.J)  # [T, P] : dt dxi * J dx^
+        E, dE, cE = _fields(uE, pts, q, tau, dt)
+        H, dH, cH = _fields(uH, pts, q, tau, dt)
+        RE = _test_project(self.eps[e] * dE, pts, Lt, wgt) - _test_project_curl(H, pts, Lt, wgt)
+        RH = _test_project(self.mu[e] * dH + cE, pts, Lt, wgt)
+        if src is not None:
+            # l_E(v) = (J, v): subtract
+            t = t0 + dt * tau
+            Jv = src(pts.x[None, :, :], t[:, None])  # [T, P, 3]
+            RE = RE - _test_project(np.broadcast_to(Jv, (1,) + Jv.shape), pts, Lt, wgt)
+        return np.stack([RE, RH], axis=1)
+
+    # -- face terms ------------------------------------------------------------
+    def _face(self, e, f, uE, uH, vE, vH, dt, t0, g):
+        """Face (e, f) contribution to the rows of e.
+
+        uE/uH: own coefficients [B, 3, q+1, N3]; vE/vH: the neighbour's (or None).
+        """
+        p, q = int(self.p[e]), int(self.q[e])
+        d, s = divmod(f, 2)
+        X8 = self.X8(e)
+        e2, f2 = self.nbr[e, f]
+        interior = e2 >= 0
+        p2 = int(self.p[e2]) if interior else p
+        q2 = int(self.q[e2]) if interior else q
+        nq = max(p, p2) + 2
+        xh, wa = _face_grid(d, s, nq)
+        pts = self._pts(e, p, xh, ("face", f, nq))
+        # surface measure and outward normal from the two tangent vectors
+        a1, a2 = [a for a in range(3) if a != d]
+        t1, t2 = pts.DF[:, :, a1], pts.DF[:, :, a2]
+        c = _cross(t1, t2)
+        dS = np.linalg.norm(c, axis=1)
+        n = c / dS[:, None]
+        outward = pts.DF[:, :, d] * (1.0 if s == 1 else -1.0)
+        n = n * np.sign(np.sum(n * outward, axis=1))[:, None]
+        T = max(q, q2) + 2
+        tau, wt = basis.gauss01(T)
+        Lt = basis.legendre(q - 1, tau)  # [q, T]
+        wgt = dt * np.outer(wt, wa * dS)  # [T, A]
+        E1, _, _ = _fields(uE, pts, q, tau, dt, derivs=False)
+        H1, _, _ = _fields(uH, pts, q, tau, dt, derivs=False)
+        nn = n[None, None, :, :]
+        if interior:
+            X8b = self.X8(e2)
+            key = ("inv", f, nq, p2, tuple(np.round(X8b - X8[0], 13).ravel()))
+            xh2 = self._vol_cache.get(key + (tuple(np.round(X8 - X8[0], 13).ravel()),))
+            if xh2 is None:
+                xh2 = geometry.inverse_map(X8b, pts.x)
+                self._vol_cache[key + (tuple(np.round(X8 - X8[0], 13).ravel()),)] = xh2
+            pts2 = self._pts(e2, p2, xh2, ("nbrface", tuple(np.round(xh2, 12).ravel())))
+            E2, _, _ = _fields(vE, pts2, q2, tau, dt, derivs=False)
+            H2, _, _ = _fields(vH, pts2, q2, tau, dt, derivs=False)
+            Havg = 0.5 * (H1 + H2)
+            Eavg = 0.5 * (E1 + E2)
+            jE = _cross(nn, E1) - _cross(nn, E2)  # [E]_T = n1 x E1 + n2 x E2, n2 = -n1
+            jH = _cross(nn, H1) - _cross(nn, H2)
+            # E-eq:  <{H}, n x v>  = v . ({H} x n)
+            RE = _test_project(_cross(Havg, nn), pts, Lt, wgt)
+            # H-eq: -<[E]_T, {w}> , {w} = w / 2
+            RH = _test_project(-0.5 * jE, pts, Lt, wgt)
+            qt = min(q, q2)
+            if qt < q:
+                # S_h: test factors (Pi~ L_i - L_i) with Pi~ the L2 projection onto P_{qt-1}
+                Lq = basis.legendre(qt - 1, tau)
+                proj = np.einsum("kt,t,it->ik", Lq, wt, Lt)       # <L_i, L_k>, k < qt
+                Ld = np.einsum("ik,kt->it", proj, Lq) - Lt          # (Pi~ - I) L_i at tau
+                # E rows: 1/2 ( <{H}, n x (Pi~v - v)> + <[H]_T, (Pi~v - v)/2> )
+                RE = RE + 0.5 * _test_project(_cross(Havg, nn) + 0.5 * jH, pts, Ld, wgt)
+                # H rows: -1/2 ( <{E}, n x (Pi~w - w)> + <[E]_T, (Pi~w - w)/2> )
+                RH = RH - 0.5 * _test_project(_cross(Eavg, nn) + 0.5 * jE, pts, Ld, wgt)
+        else:
+            # boundary: {H} = H, [v]_T = n x v ; [E]_T = n x E, {w} = w
+            RE = _test_project(_cross(H1, nn), pts, Lt, wgt)
+            RH = _test_project(-_cross(nn, E1), pts, Lt, wgt)
+            if g is not None:
+                # -l_H(w) = + <n x g, w>
+                t = t0 + dt * tau
+                gv = g(pts.x[None, :, :], t[:, None])  # [T, A, 3]
+                RH = RH + _test_project(_cross(nn, gv[None]), pts, Lt, wgt)
+        return np.stack([RE, RH], axis=1)
+
+    # -- public API ------------------------------------------------------------
+    def element_residual(self, e, U, t0, dt, src=None, g=None, parts="all"):
+        """R for the test functions of element e, layout [B, 2, 3, q, N3].
+
+        U: [B, N_trial] or [N_trial]; ``parts`` = "all" | "own" | ("nbr", f)
+        selects the contribution of element e's own coefficients (volume and
+        own face traces, no load) or of the neighbour across face f.
+        """
+        U = np.atleast_2d(U)
+        B = U.shape[0]
+        u = self.trial_block(U, e)
+        p, q = int(self.p[e]), int(self.q[e])
+        R = np.zeros((B, 2, 3, q, (p + 1) ** 3))
+        if parts in ("all", "own"):
+            R += self._volume(e, u[:, 0], u[:, 1], dt, t0, src if parts == "all" else None)
+        for f in range(6):
+            e2 = self.nbr[e, f, 0]
+            if parts == "all":
+                own, nb, gg = u, (self.trial_block(U, e2) if e2 >= 0 else None), g
+            elif parts == "own":
+                own, nb, gg = u, None, None
+            else:
+                if parts[1] != f or e2 < 0:
+                    continue
+                own, nb, gg = None, self.trial_block(U, e2), None
+            R += self._face(e, f, None if own is None else own[:, 0], None if own is None else own[:, 1],
+                            None if nb is None else nb[:, 0], None if nb is None else nb[:, 1],
+                            dt, t0, gg)
+        return R
+
+    def residual(self, U, t0, dt, src=None, g=None, elems=None) -> np.ndarray:
+        """R_h(U) = B_h(U, .) - L(.) in the test layout (concatenated over ``elems``)."""
+        elems = range(self.ne) if elems is None else elems
+        out = [self.element_residual(e, U, t0, dt, src, g)[0].ravel() for e in elems]
+        return np.concatenate(out) if out else np.zeros(0)
+
+    def assemble(self, t0, dt, src=None, g=None):
+        """Sparse A (test x trial) and b with R_h(U) = A U - b."""
+        rows, cols, vals = [], [], []
+        ntr = int(self.trial_off[-1])
+        b = -self.residual(np.zeros(ntr), t0, dt, src, g)
+        for e in range(self.ne):
+            r0 = self.test_off[e]
+            blocks = [("own", e)] + [(("nbr", f), self.nbr[e, f, 0]) for f in range(6) if self.nbr[e, f, 0] >= 0]
+            for part, e2 in blocks:
+                m = int(self.trial_sz[e2])
+                Ub = np.zeros((m, ntr))
+                Ub[np.arange(m), self.trial_off[e2] + np.arange(m)] = 1.0
+                Rb = self.element_residual(e, Ub, t0, dt, None, None, parts=part).reshape(m, -1)
+                Rb = Rb.T  # [test, m]
+                ii, jj = np.nonzero(Rb)
+                rows.append(r0 + ii)
+                cols.append(self.trial_off[e2] + jj)
+                vals.append(Rb[ii, jj])
+        A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(int(self.test_off[-1]), ntr))
+        A.sum_duplicates()
+        return A, b
+
+    def unknown_mask(self) -> np.ndarray:
+        """Boolean mask over the trial vector: True for modes m >= 1 (the slab unknowns)."""
+        mask = np.zeros(int(self.trial_off[-1]), dtype=bool)
+        for e in range(self.ne):
+            n3 = (self.p[e] + 1) ** 3
+            q = self.q[e]
+            blk = np.zeros((2, 3, q + 1, n3), dtype=bool)
+            blk[:, :, 1:, :] = True
+            mask[self.trial_off[e]:self.trial_off[e + 1]] = blk.ravel()
+        return mask
+
+    def slab_solve(self, u0, t0, dt, src=None, g=None, A_b=None):
+        """Solve R_h(U) = 0 for modes m >= 1 given the slab-start coefficients.
+
+        u0: spatial coefficients at t0, layout per element [2, 3, N3] concatenated.
+        Returns the full trial vector U.
+        """
+        A, b = self.assemble(t0, dt, src, g) if A_b is None else A_b
+        U = self.embed_start(u0)
+        mask = self.unknown_mask()
+        rhs = b - A[:, ~mask] @ U[~mask]
+        if getattr(self, "_lu_key", None) is not A:
+            # sparse LU of the unknown block, reused while the operator is the same object
+            self._lu = spla.splu(A[:, mask].tocsc())
+            self._lu_key = A
+        U[mask] = self._lu.solve(rhs)
+        return U
+
+    def embed_start(self, u0) -> np.ndarray:
+        """Trial vector with mode 0 = u0 and all other modes 0."""
+        U = np.zeros(int(self.trial_off[-1]))
+        o0 = 0
+        for e in range(self.ne):
+            n3 = int((self.p[e] + 1) ** 3)
+            q = int(self.q[e])
+            blk = np.zeros((2, 3, q + 1, n3))
+            blk[:, :, 0, :] = u0[o0:o0 + 6 * n3].reshape(2, 3, n3)
+            o0 += 6 * n3
+            U[self.trial_off[e]:self.trial_off[e + 1]] = blk.ravel()
+        return U
+
+    def end_state(self, U) -> np.ndarray:
+        """Spatial coefficients of the trial function at xi = 1 (sum_m l_m(1) u_m)."""
+        out = []
+        for e in range(self.ne):
+            q = int(self.q[e])
+            u = self.trial_block(U, e)
+            l1 = basis.trial_time(q, np.array([1.0]))[:, 0]
+            out.append(np.einsum("m,fcms->fcs", l1, u).ravel())
+        return np.concatenate(out)
+
+    def start_state(self, U) -> np.ndarray:
+        out = []
+        for e in range(self.ne):
+            q = int(self.q[e])
+            u = self.trial_block(U, e)
+            l0 = basis.trial_time(q, np.array([0.0]))[:, 0]
+            out.append(np.einsum("m,fcms->fcs", l0, u).ravel())
+        return np.concatenate(out)
+
+    def energy(self, u) -> float:
+        """E(t) = 1/2 int eps E.E + mu H.H for spatial coefficients u [per element 2,3,N3]."""
+        tot = 0.0
+        o = 0
+        for e in range(self.ne):
+            p = int(self.p[e])
+            n3 = (p + 1) ** 3
+            blk = u[o:o + 6 * n3].reshape(2, 3, n3)
+            o += 6 * n3
+            xh, w = _grid3(p + 2)
+            pts = _points(self.X8(e), p, xh)
+            ref = np.einsum("fcs,ps->fpc", blk, pts.phi)
+            phys = np.einsum("pci,fpc->fpi", pts.DFinv, ref)
+            dens = self.eps[e] * np.sum(phys[0] ** 2, axis=1) + self.mu[e] * np.sum(phys[1] ** 2, axis=1)
+            tot += 0.5 * np.sum(w * pts.J * dens)
+        return tot
+
+    def project(self, Efn, Hfn) -> np.ndarray:
+        """L2 projection of E0(x), H0(x) onto the covariant spatial spaces (per element [2,3,N3])."""
+        out = []
+        for e in range(self.ne):
+            p = int(self.p[e])
+            n3 = (p + 1) ** 3
+            xh, w = _grid3(p + 2)
+            pts = _points(self.X8(e), p, xh)
+            # basis functions DF^{-T} phi_s e_c at points: [P, 3(phys), 3(c), N3]
+            Bf = np.einsum("pci,ps->pics", pts.DFinv, pts.phi).reshape(len(w), 3, 3 * n3)
+            M = np.einsum("p,pia,pib->ab", w * pts.J, Bf, Bf)
+            blk = []
+            for fn in (Efn, Hfn):
+                v = fn(pts.x) if fn is not None else np.zeros((len(w), 3))
+                rhs = np.einsum("p,pia,pi->a", w * pts.J, Bf, v)
+                blk.append(np.linalg.solve(M, rhs))
+            out.append(np.concatenate(blk))
+        return np.concatenate(out)
+
+    def evaluate(self, u, e, xh) -> np.ndarray:
+        """Physical (E, H) of spatial coefficients u at reference points xh of element e -> [2, P, 3]."""
+        p = int(self.p[e])
+        n3 = (p + 1) ** 3
+        o = int(np.sum(6 * (self.p[:e] + 1) ** 3))
+        blk = u[o:o + 6 * n3].reshape(2, 3, n3)
+        pts = _points(self.X8(e), p, np.atleast_2d(xh))
+        ref = np.einsum("fcs,ps->fpc", blk, pts.phi)
+        return np.einsum("pci,fpc->fpi", pts.DFinv, ref)
+
+    def test_projection_in_time(self, U) -> np.ndarray:
+        """pi U: Legendre-in-time coefficients (modes 0..q-1) of U, in the test layout."""
+        out = []
+        for e in range(self.ne):
+            q = int(self.q[e])
+            u = self.trial_block(U, e)
+            tau, wt = basis.gauss01(q + 2)
+            lt = basis.trial_time(q, tau)
+            Lt = basis.legendre(q - 1, tau)
+            B = np.einsum("it,t,mt->im", Lt, wt, lt)
+            out.append(np.einsum("im,fcms->fcis", B, u).ravel())
+        return np.concatenate(out)

@@ -1,0 +1,444 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties the oracle to something other than itself: closed forms of the
+1-D tables, a library Legendre routine, finite differences, a hand-derived
+two-element result, the discrete energy identity (Theorems 3.1 / 4.1), an
+exact polynomial solution, the Gauss-collocation / Pade equivalence of
+continuous Galerkin in time, rigid-motion invariance and the analytic PEC
+cavity mode of Sec. 6.1.1.  The last tests plant mistakes in the oracle and
+check that the pins catch them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import basis, geometry, stdg
+from paper_1307_5310_gb300 import meshgen
+
+W_CAV = math.sqrt(2.0) * math.pi
+
+
+def cavity_E(x, t=0.0):
+    z = np.zeros(x.shape[0])
+    return np.stack([z, z, np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.cos(W_CAV * t)], 1)
+
+
+def cavity_H(x, t=0.0):
+    s = math.sin(W_CAV * t) / math.sqrt(2.0)
+    return np.stack([-np.sin(np.pi * x[:, 0]) * np.cos(np.pi * x[:, 1]) * s,
+                     np.cos(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * s,
+                     np.zeros(x.shape[0])], 1)
+
+
+# --------------------------------------------------------------------------
+# P1: 1-D tables against closed forms
+# --------------------------------------------------------------------------
+
+def _quad_tables(q, n):
+    tau, wt = basis.gauss01(q + 4)
+    L = basis.legendre(q, tau)
+    l = basis.trial_time(q, tau)
+    dl = basis.trial_time_deriv(q, tau)
+    A = np.einsum("it,t,mt->im", L[:q], wt, dl)
+    B = np.einsum("it,t,mt->im", L[:q], wt, l)
+    x, w = basis.gauss01(n + 2)
+    Ls = basis.legendre(n - 1, x)
+    dLs = basis.legendre_deriv(n - 1, x)
+    D = np.einsum("ax,x,bx->ab", Ls, w, dLs)
+    M = np.einsum("ax,x,bx->ab", Ls, w, Ls)
+    return A, B, D, M
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+def test_time_tables_closed_form(q):
+    A, B, _, _ = _quad_tables(q, 3)
+    # A_im = int L_i l_m' : -delta_i0 for m = 0, delta_{i,m-1} for m >= 1
+    Ac = np.zeros((q, q + 1))
+    Ac[0, 0] = -1.0
+    for m in range(1, q + 1):
+        Ac[m - 1, m] = 1.0
+    assert np.abs(A - Ac).max() < 1e-14
+    # B_im = int L_i l_m (banded; derived from l_m = (P_m - P_{m-2}) / (2 sqrt(2m-1)))
+    Bc = np.zeros((q, q + 1))
+    Bc[0, 0] = 0.5
+    Bc[0, 1] = 0.5
+    if q >= 2:
+        Bc[1, 0] = -1.0 / (2 * math.sqrt(3.0))
+        Bc[1, 1] = 1.0 / (2 * math.sqrt(3.0))
+    for m in range(2, q + 1):
+        if m <= q - 1:
+            Bc[m, m] = 1.0 / (2 * math.sqrt(2 * m - 1) * math.sqrt(2 * m + 1))
+        Bc[m - 2, m] = -1.0 / (2 * math.sqrt(2 * m - 1) * math.sqrt(2 * m - 3))
+    assert np.abs(B - Bc).max() < 1e-14
+    assert np.count_nonzero(np.abs(B) > 1e-14) == (2 if q == 1 else 2 * q + 1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_space_tables_closed_form(n):
+    _, _, D, M = _quad_tables(1, n)
+    assert np.abs(M - np.eye(n)).max() < 1e-13
+    Dc = np.zeros((n, n))
+    for a in range(n):
+        for b in range(n):
+            if a < b and (b - a) % 2 == 1:
+                Dc[a, b] = 2 * math.sqrt(2 * a + 1) * math.sqrt(2 * b + 1)
+    assert np.abs(D - Dc).max() < 1e-12
+    assert np.count_nonzero(np.abs(D) > 1e-12) == n * n // 4
+    # face values L_j(1) = sqrt(2j+1), L_j(0) = (-1)^j sqrt(2j+1)
+    v1 = basis.legendre(n - 1, np.array([1.0]))[:, 0]
+    v0 = basis.legendre(n - 1, np.array([0.0]))[:, 0]
+    j = np.arange(n)
+    assert np.abs(v1 - np.sqrt(2 * j + 1)).max() < 1e-13
+    assert np.abs(v0 - (-1.0) ** j * np.sqrt(2 * j + 1)).max() < 1e-13
+
+
+def test_legendre_matches_library():
+    x = np.linspace(0, 1, 17)
+    L = basis.legendre(7, x)
+    for k in range(8):
+        ref = np.polynomial.legendre.Legendre.basis(k)(2 * x - 1) * math.sqrt(2 * k + 1)
+        assert np.abs(L[k] - ref).max() < 1e-12
+        dref = np.polynomial.legendre.Legendre.basis(k).deriv()(2 * x - 1) * 2 * math.sqrt(2 * k + 1)
+        assert np.abs(basis.legendre_deriv(7, x)[k] - dref).max() < 1e-10
+
+
+def test_trial_time_end_values():
+    l0 = basis.trial_time(5, np.array([0.0]))[:, 0]
+    l1 = basis.trial_time(5, np.array([1.0]))[:, 0]
+    assert np.allclose(l0, [1, 0, 0, 0, 0, 0], atol=1e-15)
+    assert np.allclose(l1, [0, 1, 0, 0, 0, 0], atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# geometry: Piola curl against finite differences
+# --------------------------------------------------------------------------
+
+def test_piola_curl_finite_difference():
+    rng = np.random.Generator(np.random.PCG64(7))
+    X8 = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], float) * 0.5
+    X8 = X8 + 0.05 * rng.uniform(-1, 1, X8.shape)
+    p = 2
+    coef = rng.uniform(-1, 1, (1, 3, 2, 27))
+    coef[:, :, 1] = 0.0
+
+    def field(x):
+        xh = geometry.inverse_map(X8, x)
+        pts = stdg._points(X8, p, xh)
+        val, _, _ = stdg._fields(coef, pts, 1, np.array([0.0]), 1.0, derivs=False)
+        return val[0, 0]
+
+    xh0 = np.array([[0.3, 0.6, 0.45]])
+    pts = stdg._points(X8, p, xh0)
+    _, _, curl = stdg._fields(coef, pts, 1, np.array([0.0]), 1.0)
+    x0 = pts.x[0]
+    h = 1e-5
+    grad = np.zeros((3, 3))  # grad[i, a] = d F_i / d x_a
+    for a in range(3):
+        dx = np.zeros(3)
+        dx[a] = h
+        grad[:, a] = (field((x0 + dx)[None])[0] - field((x0 - dx)[None])[0]) / (2 * h)
+    fd = np.array([grad[2, 1] - grad[1, 2], grad[0, 2] - grad[2, 0], grad[1, 0] - grad[0, 1]])
+    assert np.abs(fd - curl[0, 0, 0]).max() < 1e-6
+
+
+# --------------------------------------------------------------------------
+# P8: brute force, two unit cubes with p = 0, q = 1 (hand-derived)
+# --------------------------------------------------------------------------
+
+def test_two_cube_p0_closed_form():
+    m = meshgen.box_mesh(2, 1, 1, hi=(2.0, 1.0, 1.0), p=0, q=1)
+    m["eps"] = np.array([2.0, 3.0])
+    m["mu"] = np.array([1.5, 0.5])
+    o = stdg.Oracle(m)
+    rng = np.random.Generator(np.random.PCG64(3))
+    U = rng.uniform(-1, 1, o.trial_off[-1])
+    dt = 0.37
+    R = o.residual(U, 0.0, dt).reshape(2, 2, 3)
+    u = U.reshape(2, 2, 3, 2)  # [el][field][c][m]
+    ex = np.array([1.0, 0, 0])
+    for k, other, nrm in ((0, 1, ex), (1, 0, -ex)):
+        # unit cube: covariant = physical for p = 0; constant fields
+        Ebar = 0.5 * (u[:, 0, :, 0] + u[:, 0, :, 1])
+        Hbar = 0.5 * (u[:, 1, :, 0] + u[:, 1, :, 1])
+        RE = m["eps"][k] * (u[k, 0, :, 1] - u[k, 0, :, 0])
+        RH = m["mu"][k] * (u[k, 1, :, 1] - u[k, 1, :, 0])
+        # boundary faces of a cube minus the shared one sum their normals to -nrm
+        for d in range(3):
+            ed = np.eye(3)[d]
+            RE[d] += dt * 0.5 * np.dot(Hbar[other] - Hbar[k], np.cross(nrm, ed))
+            RH[d] += dt * 0.5 * np.cross(nrm, Ebar[k] + Ebar[other])[d]
+        assert np.abs(R[k, 0] - RE).max() < 1e-14
+        assert np.abs(R[k, 1] - RH).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# P4: discrete energy identity for arbitrary U (Theorems 3.1 / 4.1)
+# --------------------------------------------------------------------------
+
+def _energy_identity(m, dt=0.13, seed=11):
+    o = stdg.Oracle(m)
+    U = meshgen.random_coeffs(m, seed)
+    R = o.residual(U, 0.0, dt)
+    piU = o.test_projection_in_time(U)
+    dE = o.energy(o.end_state(U)) - o.energy(o.start_state(U))
+    return R @ piU, dE
+
+
+@pytest.mark.parametrize("case", ["brick", "aniso", "curved", "uneven_q", "uneven_p"])
+def test_energy_identity(case):
+    if case == "brick":
+        m = meshgen.box_mesh(2, p=2, q=2)
+    elif case == "aniso":
+        m = meshgen.box_mesh(3, 2, 1, hi=(1.0, 0.5, 0.25), p=1, q=3)
+    elif case == "curved":
+        m = meshgen.box_mesh(3, p=2, q=2, perturb=0.3)
+    elif case == "uneven_q":
+        m = meshgen.box_mesh(2, p=2, q=1)
+        m["q"] = np.array([1, 2, 3, 1, 2, 3, 4, 1], dtype=np.uint8)
+    else:
+        m = meshgen.box_mesh(2, p=2, q=2)
+        m["p"] = np.array([1, 2, 3, 1, 2, 3, 1, 2], dtype=np.uint8)
+    meshgen.random_materials(m, 5, 6)
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) <= 1e-12 * max(1.0, abs(dE))
+
+
+# --------------------------------------------------------------------------
+# P6: polynomial patch test E = (0,0,x), H = (0,t,0), g = E
+# --------------------------------------------------------------------------
+
+def _patch(m, t0=0.3, dt=0.2):
+    o = stdg.Oracle(m)
+
+    def Ef(x):
+        z = np.zeros(x.shape[0])
+        return np.stack([z, z, x[:, 0]], 1)
+
+    def Hf(t):
+        return lambda x: np.stack([0 * x[:, 0], t + 0 * x[:, 0], 0 * x[:, 0]], 1)
+
+    u0 = o.project(Ef, Hf(t0))
+    u1 = o.project(Ef, Hf(t0 + dt))
+    U = o.embed_start(u0)
+    o0 = 0
+    for e in range(o.ne):
+        n3 = (int(o.p[e]) + 1) ** 3
+        blk = o.trial_block(U, e)
+        blk[:, :, 1, :] = u1[o0:o0 + 6 * n3].reshape(2, 3, n3)
+        o0 += 6 * n3
+
+    def g(x, t):
+        z = np.zeros(np.broadcast(x[..., 0], t).shape)
+        return np.stack([z, z, x[..., 0] + z], -1)
+
+    return o, U, u0, g, t0, dt
+
+
+@pytest.mark.parametrize("case", ["brick", "curved", "uneven"])
+def test_patch_exact(case):
+    if case == "brick":
+        m = meshgen.box_mesh(2, 2, 1, p=1, q=1)
+    elif case == "curved":
+        m = meshgen.box_mesh(2, p=2, q=1, perturb=0.4)
+    else:
+        # S_h replaces the neighbour's temporal test factors by their projection
+        # onto P_{min(q1,q2)-1}; it is consistent for this solution (H linear in
+        # t) only where min(q1, q2) >= 2.  q = 1 faces are covered by the
+        # time-constant patch below.
+        m = meshgen.box_mesh(2, p=2, q=1)
+        m["p"] = np.array([1, 2, 1, 2, 2, 1, 2, 1], dtype=np.uint8)
+        m["q"] = np.array([2, 3, 4, 2, 3, 2, 2, 3], dtype=np.uint8)
+    o, U, u0, g, t0, dt = _patch(m)
+    R = o.residual(U, t0, dt, g=g)
+    assert np.abs(R).max() < 1e-12
+    Us = o.slab_solve(u0, t0, dt, g=g)
+    assert np.abs(Us - U).max() < 1e-11
+
+
+def test_patch_time_constant_uneven_q():
+    """E = (y, x, 0), H = (0, 0, 1) solves Maxwell (eps = mu = 1, J = 0, g = E) and is constant in time."""
+    m = meshgen.box_mesh(2, p=1, q=1)
+    m["p"] = np.array([1, 2, 1, 2, 2, 1, 2, 1], dtype=np.uint8)
+    m["q"] = np.array([1, 2, 3, 1, 2, 1, 4, 2], dtype=np.uint8)
+    o = stdg.Oracle(m)
+    Ef = lambda x: np.stack([x[:, 1], x[:, 0], 0 * x[:, 0]], 1)
+    Hf = lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], 1 + 0 * x[:, 0]], 1)
+    u0 = o.project(Ef, Hf)
+    U = o.embed_start(u0)
+    for e in range(o.ne):
+        blk = o.trial_block(U, e)
+        blk[:, :, 1, :] = blk[:, :, 0, :]
+
+    def g(x, t):
+        z = np.zeros(np.broadcast(x[..., 0], t).shape)
+        return np.stack([x[..., 1] + z, x[..., 0] + z, z], -1)
+
+    assert np.abs(o.residual(U, 0.0, 0.3, g=g)).max() < 1e-12
+    assert np.abs(o.slab_solve(u0, 0.0, 0.3, g=g) - U).max() < 1e-11
+
+
+# --------------------------------------------------------------------------
+# P3: cG(q) in time = q-stage Gauss collocation = diagonal Pade R_{q,q}
+# --------------------------------------------------------------------------
+
+def _pade_num(q, z):
+    return sum(math.factorial(2 * q - k) * math.factorial(q) /
+               (math.factorial(2 * q) * math.factorial(k) * math.factorial(q - k)) * z ** k
+               for k in range(q + 1))
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+def test_scalar_ode_pade(q):
+    tau, wt = basis.gauss01(q + 3)
+    L = basis.legendre(q - 1, tau)
+    l = basis.trial_time(q, tau)
+    dl = basis.trial_time_deriv(q, tau)
+    for z in (-0.7, 0.3, -2.5):
+        # u' = (z/dt) u tested with L_i: sum_m (int L_i l_m' - z int L_i l_m) u_m = 0
+        Mt = np.einsum("it,t,mt->im", L, wt, dl) - z * np.einsum("it,t,mt->im", L, wt, l)
+        u1 = np.linalg.solve(Mt[:, 1:], -Mt[:, 0])  # u_0 = 1
+        end = basis.trial_time(q, np.array([1.0]))[1:, 0] @ u1
+        ref = _pade_num(q, z) / _pade_num(q, -z)
+        assert abs(end - ref) < 1e-13
+
+
+def test_maxwell_gauss_collocation():
+    """Slab solutions for q = 2, 3 equal R_{q,q}(dt L) u0, L = -M^{-1} K from the q = 1 operator."""
+    dt = 0.21
+    base = meshgen.box_mesh(2, 1, 1, hi=(1.0, 0.5, 0.5), p=1, q=1)
+    meshgen.random_materials(base, 1, 2)
+    o1 = stdg.Oracle(base)
+    A1, _ = o1.assemble(0.0, dt)
+    A1 = A1.toarray()
+    mask = o1.unknown_mask()
+    # q = 1 rows: M (u1 - u0) + dt K (u0 + u1) / 2
+    Au0, Au1 = A1[:, ~mask], A1[:, mask]
+    M = 0.5 * (Au1 - Au0)
+    K = (Au1 + Au0) / dt
+    # M must be the plain L2 mass matrix of the covariant space
+    n3 = 8
+    for e in range(o1.ne):
+        blk = slice(e * 6 * n3, (e + 1) * 6 * n3)
+        Mb = M[blk, blk]
+        assert np.abs(Mb - Mb.T).max() < 1e-13
+        assert np.linalg.eigvalsh(Mb).min() > 0
+    Lop = -np.linalg.solve(M, K)
+    rng = np.random.Generator(np.random.PCG64(4))
+    u0 = rng.uniform(-1, 1, M.shape[0])
+    for q in (2, 3):
+        m = dict(base)
+        m["q"] = np.full(base["hex"].shape[0], q, dtype=np.uint8)
+        o = stdg.Oracle(m)
+        U = o.slab_solve(u0, 0.0, dt)
+        end = o.end_state(U)
+        Z = dt * Lop
+        num = sum(math.factorial(2 * q - k) * math.factorial(q) /
+                  (math.factorial(2 * q) * math.factorial(k) * math.factorial(q - k)) *
+                  np.linalg.matrix_power(Z, k) for k in range(q + 1))
+        den = sum(math.factorial(2 * q - k) * math.factorial(q) /
+                  (math.factorial(2 * q) * math.factorial(k) * math.factorial(q - k)) *
+                  np.linalg.matrix_power(-Z, k) for k in range(q + 1))
+        ref = np.linalg.solve(den, num @ u0)
+        assert np.abs(end - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+# --------------------------------------------------------------------------
+# P7: invariance under rigid motions
+# --------------------------------------------------------------------------
+
+def test_rigid_motion_invariance():
+    m = meshgen.box_mesh(2, p=2, q=2, perturb=0.3)
+    meshgen.random_materials(m, 8, 9)
+    U = meshgen.random_coeffs(m, 3)
+    R0 = stdg.Oracle(m).residual(U, 0.0, 0.1)
+    th = 0.7
+    Q = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1.0]])
+    Q = Q @ np.array([[1, 0, 0], [0, math.cos(0.4), -math.sin(0.4)], [0, math.sin(0.4), math.cos(0.4)]])
+    m2 = dict(m)
+    m2["vert"] = m["vert"] @ Q.T + np.array([3.0, -1.0, 0.5])
+    R1 = stdg.Oracle(m2).residual(U, 0.0, 0.1)
+    assert np.abs(R1 - R0).max() < 1e-12 * np.abs(R0).max()
+
+
+# --------------------------------------------------------------------------
+# P5: analytic PEC cavity mode (Sec. 6.1.1 with m = n = 1 on the unit cube)
+# --------------------------------------------------------------------------
+
+def _cavity_run(N, p, q, nslab, dt):
+    m = meshgen.box_mesh(N, p=p, q=q)
+    o = stdg.Oracle(m)
+    u = o.project(cavity_E, None)
+    A_b = o.assemble(0.0, dt)
+    E0 = o.energy(u)
+    energies = [E0]
+    for n in range(nslab):
+        U = o.slab_solve(u, n * dt, dt, A_b=A_b)
+        u = o.end_state(U)
+        energies.append(o.energy(u))
+    T = nslab * dt
+    ue = o.project(lambda x: cavity_E(x, T), lambda x: cavity_H(x, T))
+    err = math.sqrt(2 * o.energy(u - ue))  # eps = mu = 1: L2 norm of (E, H)
+    return err, np.array(energies)
+
+
+@pytest.mark.slow
+def test_cavity_mode_plain_config():
+    # 4^3 bricks, p = 2, q = 1, 20 slabs of 0.05
+    err, en = _cavity_run(4, 2, 1, 20, 0.05)
+    assert abs(en[0] - 0.125) < 1e-5
+    assert np.abs(en - en[0]).max() <= 1e-12 * en[0]
+    assert err < 1.5e-2
+
+
+def test_cavity_mode_p_convergence():
+    errs = [_cavity_run(2, p, p, 2, 0.05)[0] for p in (1, 2, 3)]
+    # exponential in p: the reduction factor per degree does not shrink (an
+    # algebraic rate p^-k would give factors (2/1)^k > (3/2)^k)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert r1 > 4 and r2 >= r1
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: the pins must catch them
+# --------------------------------------------------------------------------
+
+def test_planted_mistakes_fail_pins(monkeypatch):
+    m = meshgen.box_mesh(2, p=1, q=2)
+    meshgen.random_materials(m, 5, 6)
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) < 1e-12
+
+    # 1) sign of the volume curl of the test function flipped
+    orig = stdg._test_project_curl
+    monkeypatch.setattr(stdg, "_test_project_curl", lambda *a: -orig(*a))
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) > 1e-6
+    monkeypatch.setattr(stdg, "_test_project_curl", orig)
+
+    # 2) trial time functions l_0 and l_1 swapped (wrong slab orientation)
+    orig_t = basis.trial_time
+
+    def swapped(q, x):
+        out = orig_t(q, x)
+        return out[[1, 0] + list(range(2, q + 1))]
+    monkeypatch.setattr(basis, "trial_time", swapped)
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) > 1e-6
+    monkeypatch.setattr(basis, "trial_time", orig_t)
+
+    # 3) interior face average taken without the factor 1/2 is caught by the patch test
+    o, U, u0, g, t0, dt = _patch(meshgen.box_mesh(2, 1, 1, p=1, q=1))
+    R = o.residual(U, t0, dt, g=g)
+    assert np.abs(R).max() < 1e-12
+    orig_face = stdg.Oracle._face
+
+    def bad_face(self, e, f, uE, uH, vE, vH, dt, t0, g):
+        r = orig_face(self, e, f, uE, uH, vE, vH, dt, t0, g)
+        if self.nbr[e, f, 0] >= 0:
+            r = r.copy()
+            r[:, 0] *= 2.0
+        return r
+    monkeypatch.setattr(stdg.Oracle, "_face", bad_face)
+    R = o.residual(U, t0, dt, g=g)
+    assert np.abs(R).max() > 1e-3
