@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the slab residual inside the per-slab GMRES solve on one GB300.
+
+Workload (default): 64^3 uniform affine hexahedra on [0,1]^3, p = 4, q = 3,
+eps and mu element-wise U[1,4] (PCG64 seeds 1307, 1308), slab-start state
+U[-1,1] (seed 1310), PEC, J = 0, dt = h/(2p+1).  Elements are numbered along
+the Z-order curve.
+
+One step = one slab solve: GMRES(10) right-preconditioned by the
+time-derivative terms, FP64, to 1e-9 relative residual, restarted from the
+same slab-start state every step (the state is reset by a device copy), so
+every step does the same work.  It runs every row of the hot path: temporal
+contraction, mass, volume curl, face traces and lift (the residual kernels),
+the preconditioner, the Krylov dot products and updates, and the slab-end
+extraction and energy.
+
+value = residual GDoF/s = (trial DoF per slab = 6 (q+1)(p+1)^3 per element)
+        x (residual applies per step) / (seconds per step), summed over GPUs.
+
+Inputs (6.3 GB of coefficients) are far larger than the 129 MB L2, so no L2
+flush is needed between steps.  --impl reference times the CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "residual GDoF/s + %roofline, mixed vs FP64 @1e-9 rel; slab solves/s; p99 ms"
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="elements per direction")
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--q", type=int, default=3)
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, p, q):
+    from paper_1307_5310_gb300 import meshgen
+
+    m = meshgen.box_mesh(n, p=p, q=q, order="morton")
+    meshgen.random_materials(m, 1307, 1308)
+    return m
+
+
+def flops_per_element(p, q):
+    """Algorithmic flops of one residual apply per element (both fields), split by kernel.
+
+    prep : y = B u (nnzB per point) and the folded face traces (one pass per axis, 2 comps)
+    apply: mass (1 FMA per entry), volume curl (6 terms x nnzD per line), folded lift.
+    """
+    n = p + 1
+    n2, n3 = n * n, n ** 3
+    nnzB = 2 if q == 1 else 2 * q + 1
+    nnzD = n * n // 4
+    prep = 2 * (3 * n3 * nnzB + 3 * 2 * q * n3)
+    apply = 2 * (3 * q * n3 + 6 * q * n2 * nnzD + 3 * 2 * q * n3)
+    return 2 * prep, 2 * apply
+
+
+def bytes_per_element(p, q, es=8):
+    """Algorithmic HBM bytes of one apply per element: read U, write R, eps/mu."""
+    n3 = (p + 1) ** 3
+    return es * (6 * (q + 1) * n3 + 6 * q * n3) + 16
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(p, q, target_s=15.0):
+    """The CPU oracle, as it stands, on an 8^3 block of the workload (PEC on the block boundary)."""
+    import numpy as np
+
+    from oracle import stdg
+    from paper_1307_5310_gb300 import meshgen
+
+    n = 8
+    m = meshgen.box_mesh(n, hi=(n / 64.0,) * 3, p=p, q=q)
+    meshgen.random_materials(m, 1307, 1308)
+    U = meshgen.random_coeffs(m, 1309)
+    dt = (1.0 / 64) / (2 * p + 1)
+    t0 = time.perf_counter()
+    o = stdg.Oracle(m)
+    done = 0
+    elems = list(range(m["hex"].shape[0]))
+    while done < len(elems) and time.perf_counter() - t0 < target_s:
+        o.residual(U, 0.0, dt, elems=elems[done:done + 32])
+        done += 32
+    done = min(done, len(elems))
+    t = time.perf_counter() - t0
+    dof = done * 6 * (q + 1) * (p + 1) ** 3
+    return {"value": dof / t / 1e9, "unit": "GDoF/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"residual of {done} elements of an 8^3 block of the workload (h=1/64, p={p}, q={q}, "
+                      f"PEC on the block boundary), numpy FP64 full tensor quadrature, {t:.1f} s"}, t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    base, _ = cpu_baseline(args.p, args.q, target_s=2.0)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.p, args.q, target_s=3.0)
+    for _ in range(args.steps):
+        b, t = cpu_baseline(args.p, args.q, target_s=10.0)
+        vals.append((b["value"], t))
+    v = statistics.median(x for x, _ in vals)
+    tms = statistics.median(t for _, t in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"affine {args.n}^3 bricks p={args.p} q={args.q}",
+                       "sample": "8^3 block per step", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1307_5310_gb300 import stm
+
+    m = workload(args.n, args.p, args.q)
+    ne = m["hex"].shape[0]
+    h = 1.0 / args.n
+    dt = h / (2 * args.p + 1)
+    n3 = (args.p + 1) ** 3
+    dof_slab = ne * 6 * (args.q + 1) * n3
+    s = stm.Slab(m, tol=args.tol, restart=10, max_it=400)
+    rng = np.random.Generator(np.random.PCG64(1310))
+    u_init = torch.from_numpy(rng.uniform(-1, 1, s.n_state)).cuda()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    reps = []
+
+    def step():
+        s.set_state(u_init)
+        rc, rep = s.slab_solve(dt)
+        reps.append(rep)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clk = Clocks(local)
+    s.profile(True)
+    l0 = s.launch_count()
+    reps.clear()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    step_ms = []
+    for _ in range(args.steps):
+        a = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        step_ms.append((time.perf_counter() - a) * 1e3)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = s.launch_count() - l0
+    prof = s.profile_read()
+    s.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    applies = prof["k_apply_fp64"][1] / args.steps
+    value = world * dof_slab * applies / (ms / 1e3) / 1e9
+    iters = statistics.mean(r["iterations"] for r in reps)
+
+    # roofline of the dominant kernel (k_apply, FP64 pipe)
+    fl_prep, fl_apply = flops_per_element(args.p, args.q)
+    apply_ms = prof["k_apply_fp64"][0] / max(1, prof["k_apply_fp64"][1])
+    prep_ms = prof["k_prep_fp64"][0] / max(1, prof["k_prep_fp64"][1])
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    fp64_peak = 4.0 * SMS * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA / clock / SM
+    ach = fl_apply * ne / (apply_ms / 1e3) / 1e12
+    roofline = {"kernel": f"k_apply<double,{args.p},{args.q}>", "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 pipe: 2 FMA/clock/SM x 152 SMs x median SM clock under load (of derived)",
+                "launch_ms": apply_ms, "prep": {"kernel": f"k_prep<double,{args.p},{args.q}>", "launch_ms": prep_ms,
+                                                "achieved": fl_prep * ne / (prep_ms / 1e3) / 1e12,
+                                                "frac": fl_prep * ne / (prep_ms / 1e3) / 1e12 / fp64_peak}}
+
+    # FP32 residual apply (HBM bound) measured separately, same workload
+    fp32 = None
+    try:
+        U32 = torch.empty(s.n_trial, dtype=torch.float32, device="cuda")
+        g = torch.Generator(device="cuda").manual_seed(1309)
+        U32.uniform_(-1, 1, generator=g)
+        R32 = torch.empty(s.n_test, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            s.residual_apply(U32, R32, 0.0, dt, prec=stm.STM_FP32)
+        s.profile(True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(10):
+            s.residual_apply(U32, R32, 0.0, dt, prec=stm.STM_FP32)
+        a1.record()
+        torch.cuda.synchronize()
+        p32 = s.profile_read()
+        s.profile(False)
+        ms32 = a0.elapsed_time(a1) / 10
+        ap32 = p32["k_apply_fp32"][0] / 10
+        pp32 = p32["k_prep_fp32"][0] / 10
+        by = bytes_per_element(args.p, args.q, 4) * ne
+        fp32 = {"gdofs": dof_slab / (ms32 / 1e3) / 1e9, "ms_per_apply": ms32, "k_prep_ms": pp32, "k_apply_ms": ap32,
+                "roofline": {"bound": "hbm", "achieved": by / (ms32 / 1e3) / 1e9, "peak": 6780.0, "unit": "GB/s",
+                             "frac": by / (ms32 / 1e3) / 1e9 / 6780.0, "traffic": None,
+                             "note": "algorithmic bytes (read U, write R) over the prep+apply pair"}}
+        del U32, R32
+    except Exception as ex:  # reported, never silently replaced
+        fp32 = {"error": str(ex)}
+
+    # end to end through the C ABI with host buffers: state in, slab solve, state out
+    u_host = u_init.cpu().numpy()
+    out = np.empty_like(u_host)
+    for _ in range(1):
+        s.set_state(u_host)
+        s.slab_solve(dt)
+        s.get_state(out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_state(u_host)
+        s.slab_solve(dt)
+        s.get_state(out)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * dof_slab * applies / (e2e_ms / 1e3) / 1e9, "unit": "GDoF/s",
+           "h2d_bytes_per_step": int(u_host.nbytes), "d2h_bytes_per_step": int(out.nbytes),
+           "ms_per_step": e2e_ms}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu, _ = cpu_baseline(args.p, args.q)
+        lat = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"affine {args.n}^3 bricks on [0,1]^3, p={args.p}, q={args.q}, eps/mu U[1,4], "
+                                   f"PEC, dt=h/(2p+1); step = one FP64 slab solve (GMRES(10), tol {args.tol:g})",
+                       "elements": ne, "dof_per_slab": dof_slab, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (6.3 GB coefficients)"},
+            "residual_applies_per_step": applies, "gmres_iterations_per_step": iters,
+            "slab_solves_per_s": world / (ms / 1e3),
+            "latency_ms": {"p50": statistics.median(lat), "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+            "roofline": roofline, "fp32_apply": fp32, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,156 @@
+/*
+ * stm.h -- C ABI of the space-time hp-DG Maxwell slab library (GB300, sm_103a).
+ *
+ * The library evaluates, matrix-free on the GPU, the space-time residual of
+ * Lilienthal, Schnepp & Weiland's non-dissipative space-time hp-DG method
+ * for the time-dependent Maxwell equations, and solves the per-slab systems
+ * with restarted GMRES.
+ *
+ * Problem (Eq. maxwell, Sec. 1):   eps E_t - curl H = J,  mu H_t + curl E = 0
+ * in Omega x (0,T],  n x E = n x g on the boundary,  E = E0, H = H0 at t = 0,
+ * eps and mu element-wise constant (Sec. 3, Theorem 3.1).
+ *
+ * Discretisation (Sec. 2.3, Sec. 5.1): per hexahedron K and time slab
+ * (t0, t0 + dt], trial functions DF^{-T} l_m(xi) L_j(x^) L_k(y^) L_l(z^) e_c
+ * (m = 0..q, continuous in time), test functions DF^{-T} L_i(xi) L_j L_k L_l e_c
+ * (i = 0..q-1), with L the orthonormal Legendre polynomials on [0,1] and l_m
+ * the integrated Legendre polynomials (Eq. def:ilegendre).
+ *
+ * Coefficient layouts (all arrays are dense, element after element):
+ *   trial  U[e][field 0=E,1=H][component x,y,z][mode m = 0..q][s]
+ *   test   R[e][field][component][mode i = 0..q-1][s]
+ *   state  u[e][field][component][s]          (spatial coefficients at a time)
+ * with s = (l (p+1) + k)(p+1) + j, j the x^ degree.  Mode 0 of U is the field
+ * at the slab start and mode 1 the field at the slab end (l_0(1) = 0,
+ * l_1(1) = 1, l_m(0) = l_m(1) = 0 for m >= 2); modes 1..q are the slab
+ * unknowns, so the unknown vector has the test layout.
+ *
+ * Status codes: 0 = STM_OK; negative = failure, nothing written; positive =
+ * a result with a warning.  stm_last_error() returns a message for the last
+ * failure of a context.  A context is not thread-safe.
+ *
+ * Memory: the library never frees caller memory.  STM_MEM_HOST pointers are
+ * host arrays copied in and out inside the call; STM_MEM_DEVICE pointers are
+ * device arrays on the context's device that the caller keeps alive until the
+ * call's stream work has finished.  Calls are ordered on the context stream.
+ */
+#ifndef STM_H
+#define STM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STM_OK 0
+#define STM_EINVAL (-1)       /* invalid argument or mesh                       */
+#define STM_ENOMEM (-2)       /* device allocation failed                        */
+#define STM_EDEVICE (-3)      /* CUDA error                                      */
+#define STM_ETIMEOUT (-4)     /* a bounded device wait ran out                   */
+#define STM_ENAN (-5)         /* non-finite value detected                       */
+#define STM_EUNSUPPORTED (-6) /* mesh or option outside what this build handles */
+#define STM_ENOTCONV 1        /* solver stopped at max_it; best iterate kept     */
+
+#define STM_GEOM_BRICK 0     /* axis-aligned boxes (affine, diagonal DF)          */
+#define STM_GEOM_TRILINEAR 2 /* trilinear maps from the 8 vertices (curved)       */
+
+#define STM_FP64 0  /* residual apply / solve in double precision             */
+#define STM_FP32 1  /* residual apply in single precision (float arrays)       */
+#define STM_MIXED 2 /* slab solve: FP32 inner GMRES, FP64 outer refinement     */
+
+#define STM_MEM_HOST 0
+#define STM_MEM_DEVICE 1
+
+typedef struct stm_ctx stm_ctx;
+
+/* Mesh and data of the problem statement (Sec. 1-2).  Host arrays, copied by
+ * stm_create; the caller keeps ownership. */
+typedef struct {
+  int64_t n_elem, n_vert;
+  const double *vert;  /* [n_vert][3] vertex coordinates                          */
+  const int64_t *hex;  /* [n_elem][8] vertex ids, vertex v at reference corner
+                          (v&1, v>>1&1, v>>2&1)                                   */
+  const int64_t *nbr;  /* [n_elem][6] element across face 2d+s (axis d, s = 1 at
+                          x^_d = 1), -1 on the boundary; face 2d+1 of e must meet
+                          face 2d of nbr                                          */
+  const uint8_t *p;    /* [n_elem] spatial degree (isotropic), 0..7              */
+  const uint8_t *q;    /* [n_elem] temporal degree, 1..4                         */
+  const double *eps;   /* [n_elem] permittivity, > 0                             */
+  const double *mu;    /* [n_elem] permeability, > 0                             */
+  int32_t geometry;    /* STM_GEOM_*                                              */
+} stm_mesh;
+
+typedef struct {
+  int32_t precision;     /* STM_FP64 | STM_MIXED for stm_slab_solve               */
+  double tol;            /* relative residual target of the slab solve            */
+  int32_t restart;       /* GMRES restart length n_r (Sec. 5.4: 10)               */
+  int32_t max_it;        /* iteration cap per slab                                */
+  int32_t deterministic; /* 1: fixed-order reductions (bitwise reproducible)      */
+  int64_t stream;        /* cudaStream_t as integer; 0 = the CUDA default stream  */
+} stm_opts;
+
+typedef struct {
+  int32_t iterations;      /* GMRES iterations (inner iterations in STM_MIXED)   */
+  int32_t restarts;        /* restart cycles (outer refinements in STM_MIXED)    */
+  double rel_residual;     /* final ||R(U)||_2 / ||R(U^(0))||_2, FP64            */
+  double energy;           /* discrete energy at the slab end (Eq. stability:energydef) */
+} stm_solve_report;
+
+/* Create a context on the current CUDA device.  Validates the mesh, copies
+ * connectivity, degrees and materials to the device and precomputes the
+ * element metric.  Returns STM_EUNSUPPORTED for non-uniform (p, q) or a
+ * geometry this build does not handle. */
+int32_t stm_create(stm_ctx **ctx, const stm_mesh *mesh, const stm_opts *opts);
+int32_t stm_destroy(stm_ctx *ctx);
+const char *stm_last_error(stm_ctx *ctx);
+
+/* Number of trial coefficients (U), test coefficients (R, unknowns) and state
+ * coefficients (u) of the whole mesh. */
+int32_t stm_sizes(stm_ctx *ctx, int64_t *n_trial, int64_t *n_test, int64_t *n_state);
+
+/* Residual R_h(V) = B_h(U, V) - L(V) of Eq. residual (Sec. 5) for every test
+ * basis function V, with B_h = C_h + S_h (Eq. bilinearform:C, bilinearform:S)
+ * on the slab (t0, t0 + dt].  U: trial layout, R: test layout, both of type
+ * double (prec = STM_FP64) or float (prec = STM_FP32).  Boundary data and
+ * sources set with stm_set_* enter through L; by default g = 0 (PEC), J = 0. */
+int32_t stm_residual_apply(stm_ctx *ctx, double t0, double dt, const void *U, void *R,
+                           int32_t prec, int32_t mem);
+
+/* Set the state (spatial coefficients of E and H at time t, state layout,
+ * double).  The next slab starts from it. */
+int32_t stm_set_state(stm_ctx *ctx, double t, const void *u, int32_t mem);
+int32_t stm_get_state(stm_ctx *ctx, double *t, void *u, int32_t mem);
+
+/* L2 projection of E0(x), H0(x) onto the covariant spatial spaces (initial
+ * data of Eq. maxwell), evaluated by the callback at p+2 Gauss points per
+ * direction; becomes the state at time t.  Either callback may be NULL (0). */
+typedef void (*stm_field_fn)(void *user, int64_t npts, const double *x /*[npts][3]*/,
+                             double *out /*[npts][3]*/);
+int32_t stm_set_initial(stm_ctx *ctx, double t, stm_field_fn E0, stm_field_fn H0, void *user);
+
+/* Solve one slab (Sec. 5.4): find modes 1..q of U with R_h(U) = 0 by GMRES
+ * (restart opts.restart, right preconditioned by the time-derivative terms of
+ * Eq. preconditioner), starting from the state; on return the state is the
+ * field at t + dt.  opts.precision selects FP64 or mixed precision. */
+int32_t stm_slab_solve(stm_ctx *ctx, double dt, stm_solve_report *rep);
+
+/* Discrete energy 1/2 int eps E.E + mu H.H of the state (Eq. stability:energydef), FP64. */
+int32_t stm_energy(stm_ctx *ctx, double *energy);
+
+/* Number of kernels this context has launched (residual, Krylov, energy). */
+int32_t stm_launch_count(stm_ctx *ctx, int64_t *n);
+
+/* Instrumentation: while enabled, CUDA events are recorded on the context
+ * stream around every residual kernel launch.  stm_profile_enable resets the
+ * record.  stm_profile_read synchronises the stream and returns the summed
+ * durations in ms and the launch counts of [k_prep FP64, k_apply FP64,
+ * k_prep FP32, k_apply FP32] (arrays of 4). */
+int32_t stm_profile_enable(stm_ctx *ctx, int32_t on);
+int32_t stm_profile_read(stm_ctx *ctx, double *ms, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STM_H */

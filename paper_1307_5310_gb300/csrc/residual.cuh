@@ -1,0 +1,239 @@
+// Matrix-free space-time residual on affine brick elements (Sec. 5.2).
+//
+// For every element K, field F in {E, H}, component c, temporal test mode
+// i < q and spatial index s the residual of Eq. residual is, written in the
+// reference element (the volume curl and the face terms are metric-free for
+// the covariant transform of Sec. 2.3, so only the mass term sees DF):
+//
+//   R_E[c][i] = eps G_c (u^E_{i+1} - delta_{i0} u^E_0)
+//               - dt [curl^ y^H]_c + dt/2 sum_faces [n^ x (H_K - H_K')]_c
+//   R_H[c][i] = mu  G_c (u^H_{i+1} - delta_{i0} u^H_0)
+//               + dt [curl^ y^E]_c - dt/2 sum_faces [n^ x (E_K - E_K')]_c
+//
+// with y_i = sum_m B_im u_m the temporal contraction (B_im = int L_i l_m),
+// the time-derivative term A_im = int L_i l_m' = -delta_i0 (m = 0),
+// delta_{i,m-1} (m >= 1) (Sec. 5.2, "mass residual"), and G = diag(hy hz/hx,
+// hx hz/hy, hx hy/hz) for a brick of edge lengths (hx, hy, hz).  This is the
+// paper's C_h of Eq. bilinearform:C after one integration by parts of the
+// -(H, curl v) term (the "strong" form): on an interior face the central
+// flux leaves half the tangential jump, on a PEC boundary face the E-equation
+// term cancels and the H-equation keeps the full n x E.  The boundary data g
+// and the current J enter through the load vector b that is subtracted.
+//
+// The 1-D operators: D_ab = int_0^1 L_a L_b' (nonzero only for a < b, b - a
+// odd), face values L_a(1) = sqrt(2a+1), L_a(0) = (-1)^a sqrt(2a+1).
+//
+// Two kernels per launch:
+//   k_prep  : y = B u for both fields (stored), and the tangential traces of
+//             y on the six faces, even/odd folded: one pass along each axis
+//             gives both opposite faces (X+ = e + o at x^_a = 1, X- = e - o).
+//   k_apply : R = mass + per output component two line passes (one per axis
+//             a != c) each doing the 1-D derivative D along a and the lift of
+//             the jumps on the two faces normal to a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stm {
+
+constexpr int kMaxN = 8;   // p <= 7
+constexpr int kMaxQ = 4;   // q <= 4
+
+template <typename T>
+struct Tables {
+  T B[kMaxQ][kMaxQ + 1];  // B[i][m] = int_0^1 L_i l_m
+  T Dt[kMaxN][kMaxN];     // dt * D[a][b]
+  T hf[kMaxN];            // dt/2 * sqrt(2a+1)
+  T lv[kMaxN];            // sqrt(2a+1)
+};
+
+template <typename T>
+struct ApplyArgs {
+  const T* um;            // trial modes 1..q
+  int64_t um_es, um_cs;   //   element stride, (field,component) stride; mode stride = N3
+  const T* u0;            // trial mode 0 (slab start) or nullptr (= 0)
+  int64_t u0_es, u0_cs;
+  const T* b;             // load vector in the test layout, or nullptr
+  T* y;                   // [ne][2][3][q][N3] scratch: temporal contraction
+  T* tr;                  // [ne][2][3 axes][2 sides][2 comps][q][N2] scratch: face traces
+  T* R;                   // [ne][2][3][q][N3] residual (test layout)
+  const int32_t* nbr;     // [ne][6]
+  const T* mass;          // [ne][2][3]: eps G_c (E rows), mu G_c (H rows)
+  int64_t n_elem;
+  Tables<T> tb;
+};
+
+// Nonzero pattern of B (banded): columns 0,1 meet rows 0,1; column m >= 2 meets rows m-2 and m.
+__host__ __device__ constexpr bool b_nz(int i, int m) {
+  return (m <= 1) ? (i <= 1) : (i == m || i == m - 2);
+}
+// Nonzero pattern of D.
+__host__ __device__ constexpr bool d_nz(int a, int b) { return a < b && ((b - a) & 1); }
+
+// Line of the N^3 tensor along axis a at transverse position t (the spatial
+// index with the a-coordinate removed, order preserved).
+template <int N>
+__device__ __forceinline__ void line_geom(int a, int t, int& base, int& stride) {
+  if (a == 0) { base = t * N; stride = 1; }
+  else if (a == 1) { base = (t / N) * N * N + (t % N); stride = N; }
+  else { base = t; stride = N * N; }
+}
+
+template <typename T, int P, int Q>
+__global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
+  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
+    for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
+      const int fc = it / N3, s = it - fc * N3;
+      T u[Q + 1];
+      u[0] = A.u0 ? A.u0[e * A.u0_es + fc * A.u0_cs + s] : T(0);
+#pragma unroll
+      for (int m = 1; m <= Q; ++m) u[m] = A.um[e * A.um_es + fc * A.um_cs + (m - 1) * N3 + s];
+      T* yg = A.y + (e * 6 + fc) * (int64_t)(Q * N3) + s;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        T acc = T(0);
+        bool first = true;
+#pragma unroll
+        for (int m = 0; m <= Q; ++m) {
+          if (b_nz(i, m)) {
+            acc = first ? A.tb.B[i][m] * u[m] : fma(A.tb.B[i][m], u[m], acc);
+            first = false;
+          }
+        }
+        ys[(fc * Q + i) * N3 + s] = acc;
+        yg[i * N3] = acc;
+      }
+    }
+    __syncthreads();
+    // traces: items (f, a, bi, i, t)
+    for (int it = threadIdx.x; it < 12 * Q * N2; it += blockDim.x) {
+      int r = it;
+      const int t = r % N2; r /= N2;
+      const int i = r % Q; r /= Q;
+      const int bi = r % 2; r /= 2;
+      const int a = r % 3;
+      const int f = r / 3;
+      const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
+      int base, stride;
+      line_geom<N>(a, t, base, stride);
+      const T* yl = ys + ((f * 3 + b) * Q + i) * N3 + base;
+      T ev = T(0), od = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const T v = yl[j * stride];
+        if (j & 1) od = fma(A.tb.lv[j], v, od);
+        else ev = fma(A.tb.lv[j], v, ev);
+      }
+      const int64_t o = ((((e * 2 + f) * 3 + a) * 2 + 0) * 2 + bi) * (int64_t)Q + i;
+      A.tr[o * N2 + t] = ev - od;                 // face x^_a = 0
+      A.tr[(o + 2 * Q) * N2 + t] = ev + od;       // face x^_a = 1
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P, int Q>
+__global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
+  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3]
+  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
+    const T* yg = A.y + e * (int64_t)(6 * Q * N3);
+    for (int it = threadIdx.x; it < 6 * Q * N3; it += blockDim.x) {
+      ys[it] = yg[it];
+      const int fc = it / (Q * N3);
+      const int r = it - fc * (Q * N3);
+      const int i = r / N3, s = r - i * N3;
+      const T mc = A.mass[e * 6 + fc];
+      T v = mc * A.um[e * A.um_es + fc * A.um_cs + i * N3 + s];
+      if (i == 0 && A.u0) v = fma(-mc, A.u0[e * A.u0_es + fc * A.u0_cs + s], v);
+      if (A.b) v -= A.b[e * (int64_t)(6 * Q * N3) + it];
+      Rs[it] = v;
+    }
+    __syncthreads();
+    const int32_t* nb = A.nbr + e * 6;
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+      for (int it = threadIdx.x; it < 6 * Q * N2; it += blockDim.x) {
+        int r = it;
+        const int t = r % N2; r /= N2;
+        const int i = r % Q; r /= Q;
+        const int c = r % 3;
+        const int f = r / 3;
+        const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
+        const int b = 3 - c - a;
+        // eps_{c a b}: +1 for cyclic (c, a, b)
+        const int cyc = ((a - c + 3) % 3 == 1) ? 1 : -1;
+        const T sgn = T((f == 0 ? -1 : 1) * cyc);
+        const int fp = 1 - f;
+        const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
+        int base, stride;
+        line_geom<N>(a, t, base, stride);
+        const T* yl = ys + ((fp * 3 + b) * Q + i) * N3 + base;
+        // jumps of the tangential component b of field fp on the faces normal to a
+        const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * Q + i;  // side-0 slot within an element
+        constexpr int64_t per_el = 2 * 3 * 2 * 2 * (int64_t)Q * N2;
+        const T* tre = A.tr + e * per_el;
+        const T xm = tre[so * N2 + t];
+        const T xp = tre[(so + 2 * Q) * N2 + t];
+        const int ep = nb[2 * a + 1], em = nb[2 * a];
+        T jp, jm;
+        if (ep >= 0) jp = xp - A.tr[ep * per_el + so * N2 + t];
+        else jp = (fp == 0) ? xp + xp : T(0);
+        if (em >= 0) jm = xm - A.tr[em * per_el + (so + 2 * Q) * N2 + t];
+        else jm = (fp == 0) ? xm + xm : T(0);
+        const T sp = jp + jm, dm = jp - jm;
+        T yv[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) yv[j] = yl[j * stride];
+        T* Rl = Rs + ((f * 3 + c) * Q + i) * N3 + base;
+#pragma unroll
+        for (int al = 0; al < N; ++al) {
+          T acc = -A.tb.hf[al] * ((al & 1) ? sp : dm);
+#pragma unroll
+          for (int be = 0; be < N; ++be)
+            if (d_nz(al, be)) acc = fma(A.tb.Dt[al][be], yv[be], acc);
+          Rl[al * stride] = fma(sgn, acc, Rl[al * stride]);
+        }
+      }
+      __syncthreads();
+    }
+    T* Rg = A.R + e * (int64_t)(6 * Q * N3);
+    for (int it = threadIdx.x; it < 6 * Q * N3; it += blockDim.x) Rg[it] = Rs[it];
+    __syncthreads();
+  }
+}
+
+// Optional CUDA events recorded before k_prep, between the kernels and after
+// k_apply (all null: no timing).
+struct LaunchEvents {
+  cudaEvent_t start = nullptr, mid = nullptr, stop = nullptr;
+};
+
+template <typename T, int P, int Q>
+int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const LaunchEvents& ev) {
+  constexpr int N = P + 1, N3 = N * N * N;
+  const size_t sm_prep = sizeof(T) * 6 * Q * N3;
+  const size_t sm_apply = 2 * sm_prep;
+  static bool configured = false;
+  if (!configured) {
+    if (sm_prep > 48 * 1024)
+      cudaFuncSetAttribute(k_prep<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+    if (sm_apply > 48 * 1024)
+      cudaFuncSetAttribute(k_apply<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+    configured = true;
+  }
+  if (ev.start) cudaEventRecord(ev.start, s);
+  k_prep<T, P, Q><<<grid, 256, sm_prep, s>>>(args);
+  if (ev.mid) cudaEventRecord(ev.mid, s);
+  k_apply<T, P, Q><<<grid, 256, sm_apply, s>>>(args);
+  if (ev.stop) cudaEventRecord(ev.stop, s);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace stm

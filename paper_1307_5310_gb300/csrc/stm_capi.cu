@@ -1,0 +1,744 @@
+// C ABI of the slab library (declared in include/stm.h).
+//
+// A context owns the device copy of the mesh data (face neighbours, the
+// element mass factors eps G_c / mu G_c), the state (spatial coefficients of
+// E and H at the current time), the scratch of the residual kernels and the
+// GMRES workspace.  All device work is ordered on one stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "krylov.cuh"
+#include "residual.cuh"
+#include "stm.h"
+
+namespace stm {
+#define STM_DECL_P(k)                                                                                  \
+  template <typename T>                                                                                \
+  int launch_residual_p##k(int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev);
+STM_DECL_P(0)
+STM_DECL_P(1)
+STM_DECL_P(2)
+STM_DECL_P(3)
+STM_DECL_P(4)
+STM_DECL_P(5)
+STM_DECL_P(6)
+STM_DECL_P(7)
+#undef STM_DECL_P
+
+template <typename T>
+int launch_residual(int P, int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev) {
+  switch (P) {
+    case 0: return launch_residual_p0<T>(Q, a, s, grid, ev);
+    case 1: return launch_residual_p1<T>(Q, a, s, grid, ev);
+    case 2: return launch_residual_p2<T>(Q, a, s, grid, ev);
+    case 3: return launch_residual_p3<T>(Q, a, s, grid, ev);
+    case 4: return launch_residual_p4<T>(Q, a, s, grid, ev);
+    case 5: return launch_residual_p5<T>(Q, a, s, grid, ev);
+    case 6: return launch_residual_p6<T>(Q, a, s, grid, ev);
+    case 7: return launch_residual_p7<T>(Q, a, s, grid, ev);
+    default: return -1;
+  }
+}
+
+// 1-D tables from their closed forms (Sec. 5.1-5.2): B_im = int L_i l_m with
+// l_m = (P_m - P_{m-2}) / (2 sqrt(2m-1)) in terms of the classical Legendre
+// polynomials P on [-1,1] mapped to [0,1]; D_ab = int L_a L_b' =
+// 2 sqrt(2a+1) sqrt(2b+1) for a < b with b - a odd; L_a(1) = sqrt(2a+1).
+template <typename T>
+Tables<T> make_tables(int P, int Q, double dt) {
+  Tables<T> t;
+  std::memset(&t, 0, sizeof(t));
+  const int N = P + 1;
+  double B[kMaxQ][kMaxQ + 1] = {};
+  B[0][0] = 0.5;
+  B[0][1] = 0.5;
+  if (Q >= 2) {
+    B[1][0] = -0.5 / std::sqrt(3.0);
+    B[1][1] = 0.5 / std::sqrt(3.0);
+  }
+  for (int m = 2; m <= Q; ++m) {
+    if (m <= Q - 1) B[m][m] = 0.5 / (std::sqrt(2.0 * m - 1) * std::sqrt(2.0 * m + 1));
+    B[m - 2][m] = -0.5 / (std::sqrt(2.0 * m - 1) * std::sqrt(2.0 * m - 3));
+  }
+  for (int i = 0; i < kMaxQ; ++i)
+    for (int m = 0; m <= kMaxQ; ++m) t.B[i][m] = (T)B[i][m];
+  for (int a = 0; a < N; ++a) {
+    t.lv[a] = (T)std::sqrt(2.0 * a + 1);
+    t.hf[a] = (T)(0.5 * dt * std::sqrt(2.0 * a + 1));
+    for (int b = 0; b < N; ++b)
+      if (d_nz(a, b)) t.Dt[a][b] = (T)(dt * 2.0 * std::sqrt(2.0 * a + 1) * std::sqrt(2.0 * b + 1));
+  }
+  return t;
+}
+
+// Gauss-Legendre rule on [0,1] by Newton's method on the Legendre polynomial.
+void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1) * z * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 1; k < n; ++k) {
+      const double p2 = ((2.0 * k + 1) * z * p1 - k * p0) / (k + 1);
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Orthonormal Legendre L_0..L_{n-1} on [0,1] at xi.
+void legendre01(int n, double xi, double* out) {
+  const double s = 2.0 * xi - 1.0;
+  double p0 = 1.0, p1 = s;
+  for (int k = 0; k < n; ++k) {
+    double pk;
+    if (k == 0) pk = 1.0;
+    else if (k == 1) pk = s;
+    else {
+      pk = ((2.0 * (k - 1) + 1) * s * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = pk;
+    }
+    out[k] = pk * std::sqrt(2.0 * k + 1);
+  }
+}
+
+}  // namespace stm
+
+using namespace stm;
+
+struct stm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t ne = 0;
+  int P = 0, Q = 0, N = 0, N2 = 0, N3 = 0;
+  int geometry = STM_GEOM_BRICK;
+  int64_t n_trial = 0, n_test = 0, n_state = 0;
+  stm_opts opts{};
+  std::string err;
+  std::vector<double> h_x0, h_h, h_mass;  // [ne][3], [ne][3], [ne][6]
+  int32_t* nbr = nullptr;
+  double* mass64 = nullptr;
+  float* mass32 = nullptr;
+  double* y64 = nullptr;
+  double* tr64 = nullptr;
+  float* y32 = nullptr;
+  float* tr32 = nullptr;
+  double* state = nullptr;
+  double t = 0.0;
+  double* red_partial = nullptr;
+  double* red_out = nullptr;
+  double* h_pinned = nullptr;  // small pinned staging for reductions
+  void* tmp_in = nullptr;
+  size_t tmp_in_bytes = 0;
+  void* tmp_out = nullptr;
+  size_t tmp_out_bytes = 0;
+  // GMRES workspace (FP64)
+  double* V = nullptr;
+  double* z = nullptr;
+  double* x = nullptr;
+  int V_cols = 0;
+  // instrumentation: kernel launch count, optional per-launch event timing
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Timed { cudaEvent_t a, b, c; int prec; };
+  std::vector<Timed> timed;
+};
+
+#define STM_CK(call)                                                                              \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);                                \
+      return STM_EDEVICE;                                                                         \
+    }                                                                                             \
+  } while (0)
+
+namespace {
+
+int fail(stm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int ensure(stm_ctx* c, void** p, size_t* have, size_t need) {
+  if (*have >= need) return STM_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, STM_ENOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+  }
+  *have = need;
+  return STM_OK;
+}
+
+template <typename T>
+int ensure_scratch(stm_ctx* c, T** y, T** tr) {
+  if (*y) return STM_OK;
+  const size_t ny = (size_t)c->ne * 6 * c->Q * c->N3;
+  const size_t nt = (size_t)c->ne * 24 * c->Q * c->N2;
+  if (cudaMalloc((void**)y, ny * sizeof(T)) != cudaSuccess || cudaMalloc((void**)tr, nt * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, STM_ENOMEM, "scratch allocation failed");
+  }
+  return STM_OK;
+}
+
+template <typename T>
+const T* mass_ptr(stm_ctx* c);
+template <>
+const double* mass_ptr<double>(stm_ctx* c) { return c->mass64; }
+template <>
+const float* mass_ptr<float>(stm_ctx* c) { return c->mass32; }
+
+template <typename T>
+int scratch(stm_ctx* c, T** y, T** tr);
+template <>
+int scratch<double>(stm_ctx* c, double** y, double** tr) {
+  int rc = ensure_scratch<double>(c, &c->y64, &c->tr64);
+  *y = c->y64;
+  *tr = c->tr64;
+  return rc;
+}
+template <>
+int scratch<float>(stm_ctx* c, float** y, float** tr) {
+  int rc = ensure_scratch<float>(c, &c->y32, &c->tr32);
+  *y = c->y32;
+  *tr = c->tr32;
+  return rc;
+}
+
+// R = A(um; u0) - b on the context stream.  um holds modes 1..q with element
+// stride um_es and (field, component) stride um_cs; u0 is mode 0 or null.
+template <typename T>
+int apply(stm_ctx* c, double dt, const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_es,
+          int64_t u0_cs, const T* b, T* R) {
+  T *y = nullptr, *tr = nullptr;
+  int rc = scratch<T>(c, &y, &tr);
+  if (rc) return rc;
+  ApplyArgs<T> a;
+  a.um = um;
+  a.um_es = um_es;
+  a.um_cs = um_cs;
+  a.u0 = u0;
+  a.u0_es = u0_es;
+  a.u0_cs = u0_cs;
+  a.b = b;
+  a.y = y;
+  a.tr = tr;
+  a.R = R;
+  a.nbr = c->nbr;
+  a.mass = mass_ptr<T>(c);
+  a.n_elem = c->ne;
+  a.tb = make_tables<T>(c->P, c->Q, dt);
+  const int grid = (int)std::min<int64_t>(c->ne, 1 << 30);
+  LaunchEvents ev;
+  if (c->profiling) {
+    while (c->ev_pool.size() < c->ev_used + 3) {
+      cudaEvent_t x;
+      if (cudaEventCreate(&x) != cudaSuccess) return fail(c, STM_EDEVICE, "event creation failed");
+      c->ev_pool.push_back(x);
+    }
+    ev.start = c->ev_pool[c->ev_used];
+    ev.mid = c->ev_pool[c->ev_used + 1];
+    ev.stop = c->ev_pool[c->ev_used + 2];
+    c->ev_used += 3;
+    c->timed.push_back({ev.start, ev.mid, ev.stop, sizeof(T) == 8 ? 0 : 1});
+  }
+  c->launches += 2;
+  const int e = launch_residual<T>(c->P, c->Q, a, c->stream, grid, ev);
+  if (e) return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
+  return STM_OK;
+}
+
+// Linear operator on the unknowns (Krylov layout, modes 1..q), no u0, no load.
+template <typename T>
+int linop(stm_ctx* c, double dt, const T* xin, T* out) {
+  const int64_t es = 6LL * c->Q * c->N3, cs = (int64_t)c->Q * c->N3;
+  return apply<T>(c, dt, xin, es, cs, nullptr, 0, 0, nullptr, out);
+}
+
+// R(U) with mode 0 = state (FP64) and modes 1..q = xin.
+int resid64(stm_ctx* c, double dt, const double* xin, double* out) {
+  const int64_t es = 6LL * c->Q * c->N3, cs = (int64_t)c->Q * c->N3;
+  return apply<double>(c, dt, xin, es, cs, c->state, 6LL * c->N3, c->N3, nullptr, out);
+}
+
+__global__ void k_init_guess(double* x, const double* state, int64_t q, int64_t n3, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = j / n3, s = j - blk * n3;
+    const int64_t fc = blk / q, i = blk - fc * q;
+    x[j] = (i == 0) ? state[fc * n3 + s] : 0.0;
+  }
+}
+
+__global__ void k_extract_end(double* state, const double* x, int64_t q, int64_t n3, int64_t n) {
+  // end of the slab: l_1(1) = 1, l_m(1) = 0 otherwise, so u(t0+dt) = mode 1 = Krylov index 0
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fc = j / n3, s = j - fc * n3;
+    state[j] = x[(fc * q) * n3 + s];
+  }
+}
+
+__global__ void k_scale(double* v, double a, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    v[j] *= a;
+}
+
+int grid1(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+
+int norm2(stm_ctx* c, const double* v, int64_t n, double* out) {
+  multidot<double>(v, v, 0, 0, true, n, c->red_partial, c->red_out, c->stream);
+  c->launches += 2;
+  STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  STM_CK(cudaStreamSynchronize(c->stream));
+  *out = c->h_pinned[0];
+  return STM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stm_last_error(stm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
+  if (!out || !m) return STM_EINVAL;
+  *out = nullptr;
+  stm_ctx* c = new stm_ctx();
+  auto bad = [&](int code, const std::string& msg) {
+    fprintf(stderr, "stm_create: %s\n", msg.c_str());
+    delete c;
+    return code;
+  };
+  if (m->n_elem <= 0 || !m->vert || !m->hex || !m->nbr || !m->p || !m->q || !m->eps || !m->mu)
+    return bad(STM_EINVAL, "mesh has missing arrays or no elements");
+  c->ne = m->n_elem;
+  c->P = m->p[0];
+  c->Q = m->q[0];
+  for (int64_t e = 0; e < c->ne; ++e)
+    if (m->p[e] != c->P || m->q[e] != c->Q)
+      return bad(STM_EUNSUPPORTED, "elements of different (p, q) are not handled by this build");
+  if (c->P > 7) return bad(STM_EINVAL, "p must be 0..7");
+  if (c->Q < 1 || c->Q > 4) return bad(STM_EINVAL, "q must be 1..4");
+  if (m->geometry != STM_GEOM_BRICK) return bad(STM_EUNSUPPORTED, "only axis-aligned brick elements are handled");
+  c->geometry = m->geometry;
+  c->N = c->P + 1;
+  c->N2 = c->N * c->N;
+  c->N3 = c->N2 * c->N;
+  c->n_trial = c->ne * 6LL * (c->Q + 1) * c->N3;
+  c->n_test = c->ne * 6LL * c->Q * c->N3;
+  c->n_state = c->ne * 6LL * c->N3;
+  if (o) c->opts = *o;
+  else {
+    c->opts.precision = STM_FP64;
+    c->opts.tol = 1e-12;
+    c->opts.restart = 10;
+    c->opts.max_it = 500;
+    c->opts.deterministic = 1;
+    c->opts.stream = 0;
+  }
+  if (c->opts.restart < 1 || c->opts.restart > kMaxDots - 1)
+    return bad(STM_EINVAL, "restart must be 1..15");
+  // element geometry: axis-aligned boxes
+  c->h_x0.resize(3 * c->ne);
+  c->h_h.resize(3 * c->ne);
+  c->h_mass.resize(6 * c->ne);
+  for (int64_t e = 0; e < c->ne; ++e) {
+    const int64_t* hv = m->hex + 8 * e;
+    for (int v = 0; v < 8; ++v)
+      if (hv[v] < 0 || hv[v] >= m->n_vert) return bad(STM_EINVAL, "vertex id out of range");
+    const double* v0 = m->vert + 3 * hv[0];
+    const double* v7 = m->vert + 3 * hv[7];
+    double h[3];
+    for (int d = 0; d < 3; ++d) {
+      h[d] = v7[d] - v0[d];
+      if (!(h[d] > 0)) return bad(STM_EINVAL, "element with non-positive extent (vertex order)");
+    }
+    const double tol = 1e-10 * std::max(h[0], std::max(h[1], h[2]));
+    for (int v = 0; v < 8; ++v) {
+      const double* x = m->vert + 3 * hv[v];
+      const int bit[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+      for (int d = 0; d < 3; ++d)
+        if (std::fabs(x[d] - (v0[d] + bit[d] * h[d])) > tol)
+          return bad(STM_EUNSUPPORTED, "element is not an axis-aligned box");
+    }
+    if (!(m->eps[e] > 0) || !(m->mu[e] > 0)) return bad(STM_EINVAL, "eps and mu must be positive");
+    const double G[3] = {h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2]};
+    for (int d = 0; d < 3; ++d) {
+      c->h_x0[3 * e + d] = v0[d];
+      c->h_h[3 * e + d] = h[d];
+      c->h_mass[6 * e + d] = m->eps[e] * G[d];
+      c->h_mass[6 * e + 3 + d] = m->mu[e] * G[d];
+    }
+  }
+  std::vector<int32_t> nb(6 * c->ne);
+  for (int64_t e = 0; e < c->ne; ++e) {
+    for (int f = 0; f < 6; ++f) {
+      const int64_t e2 = m->nbr[6 * e + f];
+      if (e2 < -1 || e2 >= c->ne) return bad(STM_EINVAL, "neighbour id out of range");
+      if (e2 >= 0) {
+        const int d = f / 2, s = f % 2;
+        if (m->nbr[6 * e2 + (2 * d + 1 - s)] != e) return bad(STM_EINVAL, "neighbour lists are not symmetric");
+        // conforming: the two boxes share the whole face
+        const double tol = 1e-10 * c->h_h[3 * e + d];
+        const double face = c->h_x0[3 * e + d] + (s ? c->h_h[3 * e + d] : 0.0);
+        const double face2 = c->h_x0[3 * e2 + d] + (s ? 0.0 : c->h_h[3 * e2 + d]);
+        bool ok = std::fabs(face - face2) <= tol;
+        for (int t = 0; t < 3; ++t)
+          if (t != d)
+            ok = ok && std::fabs(c->h_x0[3 * e + t] - c->h_x0[3 * e2 + t]) <= tol &&
+                 std::fabs(c->h_h[3 * e + t] - c->h_h[3 * e2 + t]) <= tol;
+        if (!ok) return bad(STM_EUNSUPPORTED, "non-conforming face (hanging nodes) are not handled");
+      }
+      nb[6 * e + f] = (int32_t)e2;
+    }
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bad(STM_EDEVICE, "no CUDA device");
+  // 0 is the CUDA default stream, so work is ordered with a caller that uses it
+  c->stream = (cudaStream_t)(intptr_t)c->opts.stream;
+  std::vector<float> m32(c->h_mass.begin(), c->h_mass.end());
+  bool ok = cudaMalloc(&c->nbr, nb.size() * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->mass64, c->h_mass.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->mass32, m32.size() * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->state, c->n_state * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->red_partial, (kMaxDots + 1) * kRedBlocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->red_out, (kMaxDots + 1) * sizeof(double)) == cudaSuccess &&
+            cudaMallocHost(&c->h_pinned, (kMaxDots + 1) * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    stm_destroy(c);
+    fprintf(stderr, "stm_create: device allocation failed\n");
+    return STM_ENOMEM;
+  }
+  cudaMemcpy(c->nbr, nb.data(), nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->mass64, c->h_mass.data(), c->h_mass.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->mass32, m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemset(c->state, 0, c->n_state * sizeof(double));
+  if (cudaGetLastError() != cudaSuccess) {
+    stm_destroy(c);
+    return STM_EDEVICE;
+  }
+  *out = c;
+  return STM_OK;
+}
+
+int32_t stm_destroy(stm_ctx* c) {
+  if (!c) return STM_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  void* ptrs[] = {c->nbr, c->mass64, c->mass32, c->y64, c->tr64, c->y32, c->tr32, c->state, c->red_partial,
+                  c->red_out, c->tmp_in, c->tmp_out, c->V, c->z, c->x};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return STM_OK;
+}
+
+int32_t stm_sizes(stm_ctx* c, int64_t* n_trial, int64_t* n_test, int64_t* n_state) {
+  if (!c) return STM_EINVAL;
+  if (n_trial) *n_trial = c->n_trial;
+  if (n_test) *n_test = c->n_test;
+  if (n_state) *n_state = c->n_state;
+  return STM_OK;
+}
+
+int32_t stm_residual_apply(stm_ctx* c, double t0, double dt, const void* U, void* R, int32_t prec, int32_t mem) {
+  (void)t0;
+  if (!c || !U || !R) return STM_EINVAL;
+  if (!(dt > 0)) return fail(c, STM_EINVAL, "dt must be positive");
+  if (prec != STM_FP64 && prec != STM_FP32) return fail(c, STM_EINVAL, "prec must be STM_FP64 or STM_FP32");
+  if (mem != STM_MEM_HOST && mem != STM_MEM_DEVICE) return fail(c, STM_EINVAL, "bad memory kind");
+  const size_t es = prec == STM_FP64 ? sizeof(double) : sizeof(float);
+  const void* Ud = U;
+  void* Rd = R;
+  if (mem == STM_MEM_HOST) {
+    int rc = ensure(c, &c->tmp_in, &c->tmp_in_bytes, c->n_trial * es);
+    if (!rc) rc = ensure(c, &c->tmp_out, &c->tmp_out_bytes, c->n_test * es);
+    if (rc) return rc;
+    STM_CK(cudaMemcpyAsync(c->tmp_in, U, c->n_trial * es, cudaMemcpyHostToDevice, c->stream));
+    Ud = c->tmp_in;
+    Rd = c->tmp_out;
+  }
+  const int64_t tes = 6LL * (c->Q + 1) * c->N3, tcs = (int64_t)(c->Q + 1) * c->N3;
+  int rc;
+  if (prec == STM_FP64) {
+    const double* u = (const double*)Ud;
+    rc = apply<double>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, nullptr, (double*)Rd);
+  } else {
+    const float* u = (const float*)Ud;
+    rc = apply<float>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, nullptr, (float*)Rd);
+  }
+  if (rc) return rc;
+  if (mem == STM_MEM_HOST) {
+    STM_CK(cudaMemcpyAsync(R, c->tmp_out, c->n_test * es, cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+  }
+  STM_CK(cudaGetLastError());
+  return STM_OK;
+}
+
+int32_t stm_set_state(stm_ctx* c, double t, const void* u, int32_t mem) {
+  if (!c || !u) return STM_EINVAL;
+  STM_CK(cudaMemcpyAsync(c->state, u, c->n_state * sizeof(double),
+                         mem == STM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+  STM_CK(cudaStreamSynchronize(c->stream));
+  c->t = t;
+  return STM_OK;
+}
+
+int32_t stm_get_state(stm_ctx* c, double* t, void* u, int32_t mem) {
+  if (!c || !u) return STM_EINVAL;
+  STM_CK(cudaMemcpyAsync(u, c->state, c->n_state * sizeof(double),
+                         mem == STM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  STM_CK(cudaStreamSynchronize(c->stream));
+  if (t) *t = c->t;
+  return STM_OK;
+}
+
+int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, void* user) {
+  // Covariant L2 projection on a brick: u_c[s] = h_c int_K^ phi_s (F_c o F_K) dx^,
+  // by the tensor Gauss rule with p+2 points per direction.
+  if (!c) return STM_EINVAL;
+  const int nq = c->P + 2, N = c->N, N3 = c->N3;
+  std::vector<double> xg, wg;
+  gauss01(nq, xg, wg);
+  std::vector<double> Lg(nq * N);
+  for (int g = 0; g < nq; ++g) legendre01(N, xg[g], &Lg[g * N]);
+  const int64_t npe = (int64_t)nq * nq * nq;
+  const int64_t chunk = std::max<int64_t>(1, (1 << 20) / npe);
+  std::vector<double> u(c->n_state, 0.0), pts, val;
+  for (int64_t e0 = 0; e0 < c->ne; e0 += chunk) {
+    const int64_t e1 = std::min(c->ne, e0 + chunk);
+    const int64_t np = (e1 - e0) * npe;
+    pts.resize(3 * np);
+    val.resize(3 * np);
+    for (int64_t e = e0; e < e1; ++e)
+      for (int gz = 0; gz < nq; ++gz)
+        for (int gy = 0; gy < nq; ++gy)
+          for (int gx = 0; gx < nq; ++gx) {
+            const int64_t k = ((e - e0) * npe + (gz * nq + gy) * nq + gx) * 3;
+            pts[k + 0] = c->h_x0[3 * e + 0] + c->h_h[3 * e + 0] * xg[gx];
+            pts[k + 1] = c->h_x0[3 * e + 1] + c->h_h[3 * e + 1] * xg[gy];
+            pts[k + 2] = c->h_x0[3 * e + 2] + c->h_h[3 * e + 2] * xg[gz];
+          }
+    for (int f = 0; f < 2; ++f) {
+      stm_field_fn fn = f == 0 ? E0 : H0;
+      if (!fn) continue;
+      fn(user, np, pts.data(), val.data());
+      for (int64_t e = e0; e < e1; ++e)
+        for (int cc = 0; cc < 3; ++cc) {
+          double* ue = &u[(e * 6 + f * 3 + cc) * N3];
+          const double hc = c->h_h[3 * e + cc];
+          for (int gz = 0; gz < nq; ++gz)
+            for (int gy = 0; gy < nq; ++gy)
+              for (int gx = 0; gx < nq; ++gx) {
+                const double v = val[((e - e0) * npe + (gz * nq + gy) * nq + gx) * 3 + cc] * hc * wg[gx] * wg[gy] * wg[gz];
+                for (int l = 0; l < N; ++l)
+                  for (int k = 0; k < N; ++k) {
+                    const double lk = Lg[gz * N + l] * Lg[gy * N + k] * v;
+                    for (int j = 0; j < N; ++j) ue[(l * N + k) * N + j] += lk * Lg[gx * N + j];
+                  }
+              }
+        }
+    }
+  }
+  return stm_set_state(c, t, u.data(), STM_MEM_HOST);
+}
+
+int32_t stm_energy(stm_ctx* c, double* energy) {
+  if (!c || !energy) return STM_EINVAL;
+  energy_brick(c->state, c->mass64, c->N3, c->n_state, c->red_partial, c->red_out, c->stream);
+  c->launches += 2;
+  STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  STM_CK(cudaStreamSynchronize(c->stream));
+  *energy = c->h_pinned[0];
+  return STM_OK;
+}
+
+int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
+  if (!c) return STM_EINVAL;
+  if (!(dt > 0)) return fail(c, STM_EINVAL, "dt must be positive");
+  if (c->opts.precision != STM_FP64) return fail(c, STM_EUNSUPPORTED, "mixed precision slab solve not built yet");
+  const int m = c->opts.restart;
+  const int64_t n = c->n_test;
+  const int64_t qn3 = (int64_t)c->Q * c->N3;
+  if (c->V_cols < m + 1) {
+    if (c->V) cudaFree(c->V);
+    if (c->z) cudaFree(c->z);
+    if (c->x) cudaFree(c->x);
+    c->V = c->z = c->x = nullptr;
+    c->V_cols = 0;
+    if (cudaMalloc(&c->V, (size_t)(m + 1) * n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->z, n * sizeof(double)) != cudaSuccess || cudaMalloc(&c->x, n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, STM_ENOMEM, "GMRES workspace allocation failed");
+    }
+    c->V_cols = m + 1;
+  }
+  double* V = c->V;
+  int rc;
+  // reference: ||R(U^(0))|| with all unknowns zero
+  STM_CK(cudaMemsetAsync(c->z, 0, n * sizeof(double), c->stream));
+  if ((rc = resid64(c, dt, c->z, V))) return rc;
+  double ref;
+  if ((rc = norm2(c, V, n, &ref))) return rc;
+  ref = std::sqrt(ref);
+  k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
+  c->launches += 1;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), yv(m);
+  int iters = 0, cycles = 0;
+  double rel = 0.0;
+  const double tol = c->opts.tol;
+  for (;;) {
+    if ((rc = resid64(c, dt, c->x, V))) return rc;
+    double beta2;
+    if ((rc = norm2(c, V, n, &beta2))) return rc;
+    const double beta = std::sqrt(beta2);
+    rel = ref > 0 ? beta / ref : beta;
+    if (!std::isfinite(rel)) return fail(c, STM_ENAN, "non-finite residual in slab solve");
+    if (rel <= tol || iters >= c->opts.max_it || beta == 0.0) break;
+    k_scale<<<grid1(n), 256, 0, c->stream>>>(V, -1.0 / beta, n);  // V0 = r / beta, r = -R
+    c->launches += 1;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* w = V + (size_t)(j + 1) * n;
+      precond_apply<double>(c->z, V + (size_t)j * n, c->mass64, qn3, n, c->stream);
+      c->launches += 1;
+      if ((rc = linop<double>(c, dt, c->z, w))) return rc;
+      // classical Gram-Schmidt with one conditional re-orthogonalisation
+      multidot<double>(w, V, n, j + 1, true, n, c->red_partial, c->red_out, c->stream);
+      c->launches += 3;  // two reduction kernels and the update below
+      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      multi_axpy<double>(w, V, n, j + 1, c->red_out, n, c->stream);
+      STM_CK(cudaStreamSynchronize(c->stream));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = c->h_pinned[i];
+      const double before = c->h_pinned[j + 1];
+      double after;
+      if ((rc = norm2(c, w, n, &after))) return rc;
+      if (after < 0.5 * before) {
+        multidot<double>(w, V, n, j + 1, false, n, c->red_partial, c->red_out, c->stream);
+        c->launches += 3;
+        STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        multi_axpy<double>(w, V, n, j + 1, c->red_out, n, c->stream);
+        STM_CK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i <= j; ++i) H[i * m + j] += c->h_pinned[i];
+        if ((rc = norm2(c, w, n, &after))) return rc;
+      }
+      const double hn = std::sqrt(after);
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0) {
+        k_scale<<<grid1(n), 256, 0, c->stream>>>(w, 1.0 / hn, n);
+        c->launches += 1;
+      }
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], b = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * b;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[j * m + j], b = H[(j + 1) * m + j];
+      const double r = std::hypot(a, b);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? b / r : 0.0;
+      H[j * m + j] = r;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * ref || iters >= c->opts.max_it || hn == 0.0) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * yv[l];
+      yv[i] = s / H[i * m + i];
+    }
+    Coef16 y{};
+    for (int i = 0; i < k; ++i) y.c[i] = yv[i];
+    precond_combine<double, double>(c->x, V, n, k, y, c->mass64, qn3, n, c->stream);
+    c->launches += 1;
+    ++cycles;
+  }
+  k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);
+  c->launches += 1;
+  STM_CK(cudaGetLastError());
+  c->t += dt;
+  double en = 0.0;
+  if ((rc = stm_energy(c, &en))) return rc;
+  if (rep) {
+    rep->iterations = iters;
+    rep->restarts = cycles;
+    rep->rel_residual = rel;
+    rep->energy = en;
+  }
+  return rel <= tol ? STM_OK : STM_ENOTCONV;
+}
+
+int32_t stm_launch_count(stm_ctx* c, int64_t* n) {
+  if (!c || !n) return STM_EINVAL;
+  *n = c->launches;
+  return STM_OK;
+}
+
+int32_t stm_profile_enable(stm_ctx* c, int32_t on) {
+  if (!c) return STM_EINVAL;
+  STM_CK(cudaStreamSynchronize(c->stream));
+  c->profiling = on != 0;
+  c->timed.clear();
+  c->ev_used = 0;
+  return STM_OK;
+}
+
+int32_t stm_profile_read(stm_ctx* c, double* ms, int64_t* count) {
+  if (!c || !ms || !count) return STM_EINVAL;
+  STM_CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = 0.0;
+    count[k] = 0;
+  }
+  for (const auto& t : c->timed) {
+    float a = 0.f, b = 0.f;
+    STM_CK(cudaEventElapsedTime(&a, t.a, t.b));
+    STM_CK(cudaEventElapsedTime(&b, t.b, t.c));
+    ms[2 * t.prec] += a;
+    ms[2 * t.prec + 1] += b;
+    count[2 * t.prec] += 1;
+    count[2 * t.prec + 1] += 1;
+  }
+  return STM_OK;
+}
+
+}  // extern "C"

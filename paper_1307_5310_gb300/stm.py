@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libstm.so (the C ABI declared in include/stm.h).
+
+Functions keep the C names; ``Slab`` bundles one context.  Arrays are either
+numpy arrays (host memory, copied inside the call) or CUDA torch tensors
+(device memory, used in place on the context stream).  Every step of the
+residual, the solve and the energy runs in the library's CUDA kernels; this
+module only marshals arguments.  Loading fails loudly when the library has
+not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstm.so")
+
+STM_OK = 0
+STM_EINVAL = -1
+STM_ENOMEM = -2
+STM_EDEVICE = -3
+STM_ETIMEOUT = -4
+STM_ENAN = -5
+STM_EUNSUPPORTED = -6
+STM_ENOTCONV = 1
+
+STM_GEOM_BRICK = 0
+STM_GEOM_TRILINEAR = 2
+STM_FP64 = 0
+STM_FP32 = 1
+STM_MIXED = 2
+STM_MEM_HOST = 0
+STM_MEM_DEVICE = 1
+
+# Every exported entry point of include/stm.h.
+EXPORTS = (
+    "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply",
+    "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
+    "stm_launch_count", "stm_profile_enable", "stm_profile_read",
+)
+
+
+class stm_mesh(C.Structure):
+    _fields_ = [
+        ("n_elem", C.c_int64), ("n_vert", C.c_int64),
+        ("vert", C.POINTER(C.c_double)), ("hex", C.POINTER(C.c_int64)), ("nbr", C.POINTER(C.c_int64)),
+        ("p", C.POINTER(C.c_uint8)), ("q", C.POINTER(C.c_uint8)),
+        ("eps", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
+        ("geometry", C.c_int32),
+    ]
+
+
+class stm_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32),
+                ("deterministic", C.c_int32), ("stream", C.c_int64)]
+
+
+class stm_solve_report(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("rel_residual", C.c_double),
+                ("energy", C.c_double)]
+
+
+FIELD_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double))
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libstm.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libstm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.stm_create.argtypes = [C.POINTER(vp), C.POINTER(stm_mesh), C.POINTER(stm_opts)]
+        L.stm_destroy.argtypes = [vp]
+        L.stm_last_error.argtypes = [vp]
+        L.stm_last_error.restype = C.c_char_p
+        L.stm_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        L.stm_residual_apply.argtypes = [vp, d, d, vp, vp, i32, i32]
+        L.stm_set_state.argtypes = [vp, d, vp, i32]
+        L.stm_get_state.argtypes = [vp, C.POINTER(d), vp, i32]
+        L.stm_set_initial.argtypes = [vp, d, FIELD_FN, FIELD_FN, vp]
+        L.stm_slab_solve.argtypes = [vp, d, C.POINTER(stm_solve_report)]
+        L.stm_energy.argtypes = [vp, C.POINTER(d)]
+        L.stm_launch_count.argtypes = [vp, C.POINTER(i64)]
+        L.stm_profile_enable.argtypes = [vp, i32]
+        L.stm_profile_read.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
+        for name in EXPORTS:
+            if name != "stm_last_error":
+                getattr(L, name).restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+class StmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"stm error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a, dtype=None):
+    """(pointer, mem kind, keep-alive) for a numpy array or a CUDA torch tensor."""
+    if isinstance(a, np.ndarray):
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data_as(C.c_void_p), STM_MEM_HOST, a
+    import torch
+
+    if isinstance(a, torch.Tensor):
+        if not a.is_cuda:
+            return _ptr(a.numpy(), dtype)
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(a.dtype).replace("torch.", "") != np.dtype(dtype).name:
+            raise TypeError(f"expected {dtype}, got {a.dtype}")
+        return C.c_void_p(a.data_ptr()), STM_MEM_DEVICE, a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Slab:
+    """One library context for a mesh (see include/stm.h)."""
+
+    def __init__(self, mesh: dict, precision=STM_FP64, tol=1e-12, restart=10, max_it=500,
+                 deterministic=True, stream=None):
+        L = lib()
+        self._keep = {}
+        ne = mesh["hex"].shape[0]
+        arr = {
+            "vert": np.ascontiguousarray(mesh["vert"], dtype=np.float64),
+            "hex": np.ascontiguousarray(mesh["hex"], dtype=np.int64),
+            "nbr": np.ascontiguousarray(mesh["nbr"], dtype=np.int64),
+            "p": np.ascontiguousarray(np.asarray(mesh["p"]).reshape(ne), dtype=np.uint8),
+            "q": np.ascontiguousarray(np.asarray(mesh["q"]).reshape(ne), dtype=np.uint8),
+            "eps": np.ascontiguousarray(mesh["eps"], dtype=np.float64),
+            "mu": np.ascontiguousarray(mesh["mu"], dtype=np.float64),
+        }
+        geom = {"brick": STM_GEOM_BRICK, "trilinear": STM_GEOM_TRILINEAR}[mesh.get("geometry", "brick")]
+        m = stm_mesh(ne, arr["vert"].shape[0],
+                     arr["vert"].ctypes.data_as(C.POINTER(C.c_double)),
+                     arr["hex"].ctypes.data_as(C.POINTER(C.c_int64)),
+                     arr["nbr"].ctypes.data_as(C.POINTER(C.c_int64)),
+                     arr["p"].ctypes.data_as(C.POINTER(C.c_uint8)),
+                     arr["q"].ctypes.data_as(C.POINTER(C.c_uint8)),
+                     arr["eps"].ctypes.data_as(C.POINTER(C.c_double)),
+                     arr["mu"].ctypes.data_as(C.POINTER(C.c_double)), geom)
+        if stream is None:
+            import torch
+
+            stream = torch.cuda.current_stream().cuda_stream
+        o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream))
+        h = C.c_void_p()
+        rc = L.stm_create(C.byref(h), C.byref(m), C.byref(o))
+        if rc != STM_OK:
+            raise StmError(rc, "stm_create failed (see stderr)")
+        self.ctx = h
+        nt, ns, nst = C.c_int64(), C.c_int64(), C.c_int64()
+        L.stm_sizes(h, C.byref(nt), C.byref(ns), C.byref(nst))
+        self.n_trial, self.n_test, self.n_state = nt.value, ns.value, nst.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().stm_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def _check(self, rc, ok=(STM_OK,)):
+        if rc not in ok:
+            raise StmError(rc, lib().stm_last_error(self.ctx).decode())
+        return rc
+
+    def residual_apply(self, U, R, t0: float, dt: float, prec=STM_FP64):
+        dt_ = np.float64 if prec == STM_FP64 else np.float32
+        pu, mu_, _ = _ptr(U, dt_)
+        pr, mr, _ = _ptr(R, dt_)
+        if mu_ != mr:
+            raise ValueError("U and R must both be host or both be device arrays")
+        return self._check(lib().stm_residual_apply(self.ctx, t0, dt, pu, pr, prec, mu_))
+
+    def set_state(self, u, t=0.0):
+        p, m, _ = _ptr(u, np.float64)
+        return self._check(lib().stm_set_state(self.ctx, t, p, m))
+
+    def get_state(self, out=None):
+        out = np.empty(self.n_state) if out is None else out
+        p, m, _ = _ptr(out, np.float64)
+        t = C.c_double()
+        self._check(lib().stm_get_state(self.ctx, C.byref(t), p, m))
+        return out, t.value
+
+    def set_initial(self, E0=None, H0=None, t=0.0):
+        def wrap(fn):
+            if fn is None:
+                return C.cast(None, FIELD_FN)
+
+            def cb(_user, n, x, out):
+                xs = np.ctypeslib.as_array(x, shape=(n, 3))
+                np.ctypeslib.as_array(out, shape=(n, 3))[:] = fn(xs)
+            return FIELD_FN(cb)
+        e, h = wrap(E0), wrap(H0)
+        self._keep["cb"] = (e, h)
+        return self._check(lib().stm_set_initial(self.ctx, t, e, h, None))
+
+    def slab_solve(self, dt: float):
+        rep = stm_solve_report()
+        rc = self._check(lib().stm_slab_solve(self.ctx, dt, C.byref(rep)), ok=(STM_OK, STM_ENOTCONV))
+        return rc, {"iterations": rep.iterations, "restarts": rep.restarts,
+                    "rel_residual": rep.rel_residual, "energy": rep.energy}
+
+    def energy(self) -> float:
+        e = C.c_double()
+        self._check(lib().stm_energy(self.ctx, C.byref(e)))
+        return e.value
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(lib().stm_launch_count(self.ctx, C.byref(n)))
+        return n.value
+
+    def profile(self, on: bool):
+        return self._check(lib().stm_profile_enable(self.ctx, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel: (total ms, launches)} for the residual kernels since profile(True)."""
+        ms = (C.c_double * 4)()
+        cnt = (C.c_int64 * 4)()
+        self._check(lib().stm_profile_read(self.ctx, ms, cnt))
+        names = ("k_prep_fp64", "k_apply_fp64", "k_prep_fp32", "k_apply_fp32")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(names)}

@@ -1,0 +1,146 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances: FP64 results are held to 1e-12 relative L2 (the target for the
+double-precision path).  FP32 residuals: inputs are rounded to float first
+(the oracle sees the same rounded values), and the bar is 2e-6 relative L2 --
+each residual entry sums at most a few dozen products of O(1) terms, so
+float rounding (u = 6e-8) with this amplification stays below 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import stdg
+from paper_1307_5310_gb300 import meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def stm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1307_5310_gb300 import stm as s
+
+    return s
+
+
+CASES = [
+    (2, 2, 2, 1, 1), (3, 2, 2, 2, 2), (2, 2, 3, 3, 3), (2, 2, 2, 4, 4), (3, 1, 1, 0, 1),
+    (2, 2, 2, 5, 2), (1, 1, 2, 7, 1), (2, 1, 2, 6, 3), (5, 3, 2, 2, 1), (2, 2, 2, 4, 3),
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,p,q", CASES)
+def test_residual_fp64(stm, nx, ny, nz, p, q):
+    m = meshgen.box_mesh(nx, ny, nz, hi=(1.0, 0.7, 1.3), p=p, q=q, order="morton")
+    meshgen.random_materials(m, 1, 2)
+    U = meshgen.random_coeffs(m, 3)
+    Ro = stdg.Oracle(m).residual(U, 0.2, 0.05)
+    s = stm.Slab(m)
+    R = np.empty(s.n_test)
+    s.residual_apply(U, R, 0.2, 0.05)
+    assert rel(R, Ro) < 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,nz,p,q", [(2, 2, 2, 2, 2), (3, 2, 2, 4, 3), (1, 2, 1, 7, 4)])
+def test_residual_fp32(stm, nx, ny, nz, p, q):
+    m = meshgen.box_mesh(nx, ny, nz, hi=(1.0, 0.7, 1.3), p=p, q=q)
+    meshgen.random_materials(m, 4, 5)
+    U32 = meshgen.random_coeffs(m, 6).astype(np.float32)
+    Ro = stdg.Oracle(m).residual(U32.astype(np.float64), 0.0, 0.03)
+    s = stm.Slab(m)
+    R = np.empty(s.n_test, np.float32)
+    s.residual_apply(U32, R, 0.0, 0.03, prec=stm.STM_FP32)
+    assert rel(R, Ro) < 2e-6
+
+
+def test_residual_device_memory(stm):
+    import torch
+
+    m = meshgen.box_mesh(3, 3, 2, p=3, q=2, order="morton")
+    meshgen.random_materials(m, 7, 8)
+    U = meshgen.random_coeffs(m, 9)
+    s = stm.Slab(m)
+    Rh = np.empty(s.n_test)
+    s.residual_apply(U, Rh, 0.0, 0.1)
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty(s.n_test, dtype=torch.float64, device="cuda")
+    s.residual_apply(Ud, Rd, 0.0, 0.1)
+    torch.cuda.synchronize()
+    assert np.array_equal(Rd.cpu().numpy(), Rh)  # same kernels, same order: bitwise
+
+
+def test_energy_and_projection(stm):
+    m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.5, 0.8), p=3, q=1)
+    meshgen.random_materials(m, 1, 9)
+    o = stdg.Oracle(m)
+    E0 = lambda x: np.stack([np.sin(x[:, 1]), x[:, 0] * x[:, 2], np.cos(3 * x[:, 0])], 1)
+    H0 = lambda x: np.stack([x[:, 2] ** 2, np.exp(x[:, 0]), 0 * x[:, 0] + 0.5], 1)
+    uo = o.project(E0, H0)
+    s = stm.Slab(m)
+    s.set_initial(E0, H0)
+    ug, _ = s.get_state()
+    assert rel(ug, uo) < 1e-12
+    assert abs(s.energy() - o.energy(uo)) < 1e-12 * o.energy(uo)
+
+
+def _cavity(x, t=0.0):
+    z = np.zeros(x.shape[0])
+    return np.stack([z, z, np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.cos(math.sqrt(2) * math.pi * t)], 1)
+
+
+def test_slab_solve_plain_config(stm):
+    """4^3 PEC cavity, p = 2, q = 1, 20 slabs of 0.05: GPU GMRES vs the oracle's direct solves."""
+    m = meshgen.box_mesh(4, p=2, q=1)
+    o = stdg.Oracle(m)
+    dt = 0.05
+    u = o.project(_cavity, None)
+    A_b = o.assemble(0.0, dt)
+    s = stm.Slab(m, tol=1e-14, restart=10, max_it=2000)
+    s.set_initial(_cavity, None)
+    for n in range(20):
+        u = o.end_state(o.slab_solve(u, n * dt, dt, A_b=A_b))
+        rc, rep = s.slab_solve(dt)
+        assert rc == stm.STM_OK, rep
+    ug, t = s.get_state()
+    assert abs(t - 1.0) < 1e-12
+    assert rel(ug, u) < 1e-12
+
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_slab_solve_higher_q(stm, q):
+    m = meshgen.box_mesh(2, 3, 2, hi=(0.5, 0.75, 0.5), p=2, q=q)
+    meshgen.random_materials(m, 2, 3)
+    o = stdg.Oracle(m)
+    rng = np.random.Generator(np.random.PCG64(5))
+    u0 = rng.uniform(-1, 1, o.ne * 6 * 27)
+    dt = 0.04
+    uo = o.end_state(o.slab_solve(u0, 0.0, dt))
+    s = stm.Slab(m, tol=1e-14, max_it=2000)
+    s.set_state(u0)
+    rc, rep = s.slab_solve(dt)
+    assert rc == stm.STM_OK, rep
+    ug, _ = s.get_state()
+    assert rel(ug, uo) < 1e-12
+
+
+def test_energy_conserved_100_slabs(stm):
+    """PEC cavity, random piecewise eps/mu, J = 0: energy constant to 1e-12 relative over 100 slabs."""
+    m = meshgen.box_mesh(4, p=3, q=2)
+    meshgen.random_materials(m, 11, 12)
+    s = stm.Slab(m, tol=1e-15, max_it=5000)
+    rng = np.random.Generator(np.random.PCG64(13))
+    s.set_state(rng.uniform(-1, 1, s.n_state))
+    e0 = s.energy()
+    drift = 0.0
+    for _ in range(100):
+        s.slab_solve(0.02)
+        drift = max(drift, abs(s.energy() - e0) / e0)
+    assert drift < 1e-12
