@@ -149,6 +149,32 @@ int32_t stm_launch_count(stm_ctx *ctx, int64_t *n);
 int32_t stm_profile_enable(stm_ctx *ctx, int32_t on);
 int32_t stm_profile_read(stm_ctx *ctx, double *ms, int64_t *count);
 
+/* Residual apply that allocates no device memory (the paper has no
+ * counterpart; this is a service for callers that cannot call cudaMalloc,
+ * e.g. code inside a CUDA graph being captured, or a host whose device memory
+ * all belongs to its own pool).  Same result as stm_residual_apply with
+ * prec = STM_FP64 on an STM_GEOM_BRICK mesh of uniform (p, q), with PEC and no
+ * sources, but without a context: every argument is a device pointer the
+ * caller owns.
+ *   nbr [n_elem][6] int32 face neighbours (as stm_mesh.nbr, -1 = boundary);
+ *   h   [n_elem][3] edge lengths of the axis-aligned boxes;
+ *   eps, mu [n_elem]; U trial layout, R test layout (both double).
+ * Scratch lives in one static device array of STM_NOALLOC_SCRATCH_BYTES,
+ * held by every GPU that loads the library until the process exits.  A call
+ * needs 8 (6 + 6 q (p+1)^3 + 24 q (p+1)^2) bytes per element (each of the three
+ * parts rounded up to 256 bytes); a larger request returns STM_EINVAL, with
+ * a message on stderr, and launches nothing.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array, so calls that overlap on the GPU (different streams, or other
+ * threads) race; calls ordered on one stream do not.  Everything the kernels
+ * read from the scratch is written by the same call first.  Work is queued on
+ * `stream` (0 = the default stream) and the call returns without waiting. */
+#define STM_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int32_t stm_residual_apply_noalloc(int64_t n_elem, int32_t p, int32_t q, double dt, const int32_t *nbr,
+                                   const double *h, const double *eps, const double *mu, const double *U,
+                                   double *R, int64_t stream);
+
 #ifdef __cplusplus
 }
 #endif

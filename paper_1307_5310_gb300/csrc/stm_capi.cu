@@ -77,6 +77,9 @@ Tables<T> make_tables(int P, int Q, double dt) {
   return t;
 }
 
+template Tables<double> make_tables<double>(int, int, double);
+template int launch_residual<double>(int, int, const ApplyArgs<double>&, cudaStream_t, int, const LaunchEvents&);
+
 // Gauss-Legendre rule on [0,1] by Newton's method on the Legendre polynomial.
 void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);

@@ -38,7 +38,7 @@ STM_MEM_DEVICE = 1
 EXPORTS = (
     "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply",
     "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
-    "stm_launch_count", "stm_profile_enable", "stm_profile_read",
+    "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
 )
 
 
@@ -89,11 +89,27 @@ def lib() -> C.CDLL:
         L.stm_launch_count.argtypes = [vp, C.POINTER(i64)]
         L.stm_profile_enable.argtypes = [vp, i32]
         L.stm_profile_read.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
+        L.stm_residual_apply_noalloc.argtypes = [i64, i32, i32, d, vp, vp, vp, vp, vp, vp, i64]
         for name in EXPORTS:
             if name != "stm_last_error":
                 getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
+
+
+def residual_apply_noalloc(n_elem, p, q, dt, nbr, h, eps, mu, U, R, stream=None) -> int:
+    """stm_residual_apply_noalloc with CUDA torch tensors (all device memory); returns the status."""
+    import torch
+
+    args = []
+    for t, dt_ in ((nbr, torch.int32), (h, torch.float64), (eps, torch.float64), (mu, torch.float64),
+                   (U, torch.float64), (R, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == dt_):
+            raise TypeError("residual_apply_noalloc takes contiguous CUDA tensors of the documented types")
+        args.append(C.c_void_p(t.data_ptr()))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    return lib().stm_residual_apply_noalloc(n_elem, p, q, dt, *args, int(stream))
 
 
 class StmError(RuntimeError):
