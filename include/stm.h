@@ -88,6 +88,8 @@ typedef struct {
   int32_t max_it;        /* iteration cap per slab                                */
   int32_t deterministic; /* 1: fixed-order reductions (bitwise reproducible)      */
   int64_t stream;        /* cudaStream_t as integer; 0 = the CUDA default stream  */
+  int32_t reorth;        /* 1: second Gram-Schmidt pass when the norm drops below
+                            1/sqrt(2) of its value (DGKS test); 0: never           */
 } stm_opts;
 
 typedef struct {

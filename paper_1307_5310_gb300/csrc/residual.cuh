@@ -71,6 +71,13 @@ __host__ __device__ constexpr bool b_nz(int i, int m) {
 // Nonzero pattern of D.
 __host__ __device__ constexpr bool d_nz(int a, int b) { return a < b && ((b - a) & 1); }
 
+// x with its sign bit xor-ed with m (m = 0 or 0x80000000): a negation on the
+// integer pipe, so the FP64 pipe only sees the products of the residual.
+__device__ __forceinline__ double flip_sign(double x, unsigned m) {
+  return __hiloint2double(__double2hiint(x) ^ (int)m, __double2loint(x));
+}
+__device__ __forceinline__ float flip_sign(float x, unsigned m) { return __int_as_float(__float_as_int(x) ^ (int)m); }
+
 // Line of the N^3 tensor along axis a at transverse position t (the spatial
 // index with the a-coordinate removed, order preserved).
 template <int N>
@@ -167,9 +174,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         const int f = r / 3;
         const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
         const int b = 3 - c - a;
-        // eps_{c a b}: +1 for cyclic (c, a, b)
-        const int cyc = ((a - c + 3) % 3 == 1) ? 1 : -1;
-        const T sgn = T((f == 0 ? -1 : 1) * cyc);
+        // eps_{c a b}: +1 for cyclic (c, a, b); the sign s_F eps_{cab} is applied by
+        // flipping sign bits of the inputs (integer pipe), not by multiplies
+        const bool cyc = ((a - c + 3) % 3 == 1);
+        const unsigned flip = ((f == 0) == cyc) ? 0x80000000u : 0u;
         const int fp = 1 - f;
         const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
         int base, stride;
@@ -187,18 +195,19 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         else jp = (fp == 0) ? xp + xp : T(0);
         if (em >= 0) jm = xm - A.tr[em * per_el + (so + 2 * Q) * N2 + t];
         else jm = (fp == 0) ? xm + xm : T(0);
-        const T sp = jp + jm, dm = jp - jm;
+        const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
         T yv[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) yv[j] = yl[j * stride];
+        for (int j = 0; j < N; ++j) yv[j] = flip_sign(yl[j * stride], flip);
         T* Rl = Rs + ((f * 3 + c) * Q + i) * N3 + base;
 #pragma unroll
         for (int al = 0; al < N; ++al) {
-          T acc = -A.tb.hf[al] * ((al & 1) ? sp : dm);
+          T r = Rl[al * stride];
+          r = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r);
 #pragma unroll
           for (int be = 0; be < N; ++be)
-            if (d_nz(al, be)) acc = fma(A.tb.Dt[al][be], yv[be], acc);
-          Rl[al * stride] = fma(sgn, acc, Rl[al * stride]);
+            if (d_nz(al, be)) r = fma(A.tb.Dt[al][be], yv[be], r);
+          Rl[al * stride] = r;
         }
       }
       __syncthreads();

@@ -160,11 +160,20 @@ struct stm_ctx {
   size_t tmp_in_bytes = 0;
   void* tmp_out = nullptr;
   size_t tmp_out_bytes = 0;
-  // GMRES workspace (FP64)
+  // inverse mass factors 1 / (eps G_c), 1 / (mu G_c): the preconditioner of Eq. preconditioner
+  double* inv64 = nullptr;
+  float* inv32 = nullptr;
+  // GMRES workspace: FP64 basis (plain path) or FP32 basis + FP64 residual (mixed path)
   double* V = nullptr;
+  int64_t V_len = 0;
   double* z = nullptr;
+  int64_t z_len = 0;
   double* x = nullptr;
-  int V_cols = 0;
+  int64_t x_len = 0;
+  float* V32 = nullptr;
+  int64_t V32_len = 0;
+  float* z32 = nullptr;
+  int64_t z32_len = 0;
   // instrumentation: kernel launch count, optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -311,19 +320,122 @@ __global__ void k_extract_end(double* state, const double* x, int64_t q, int64_t
   }
 }
 
-__global__ void k_scale(double* v, double a, int64_t n) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    v[j] *= a;
-}
-
 int grid1(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
-int norm2(stm_ctx* c, const double* v, int64_t n, double* out) {
-  multidot<double>(v, v, 0, 0, true, n, c->red_partial, c->red_out, c->stream);
+template <typename S>
+const S* inv_ptr(stm_ctx* c);
+template <>
+const double* inv_ptr<double>(stm_ctx* c) { return c->inv64; }
+template <>
+const float* inv_ptr<float>(stm_ctx* c) { return c->inv32; }
+
+// ||v||^2 (fixed-order reduction, FP64 accumulation).
+template <typename S>
+int norm2(stm_ctx* c, S* v, int64_t n, double* out) {
+  axpy_norm<S>(v, v, 0, 0, Coef16{}, n, c->red_partial, c->red_out, c->stream);
   c->launches += 2;
   STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   STM_CK(cudaStreamSynchronize(c->stream));
   *out = c->h_pinned[0];
+  return STM_OK;
+}
+
+// One restart cycle of right-preconditioned GMRES on the unknowns (Sec. 5.4),
+// with the basis kept unnormalised: v_i = V_i / alpha_i (alpha_i signed).
+// On entry V[0] holds the start vector with v_0 = V[0] / a0 the normalised
+// residual r / |r|, |a0| = |r|.  Classical Gram-Schmidt (one fused dot pass,
+// one fused update + norm pass), with an optional second pass when the norm
+// drops below 1/sqrt(2) of its value before the update.  Returns the number k
+// of basis vectors used and the coefficients yc[i] such that the correction
+// is P^{-1} sum_{i<k} yc[i] V[i]; *res is the residual norm estimate |g_k|.
+template <typename S>
+int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double tol_abs, int max_iters, int* k_out,
+                Coef16* yc, double* res, int* iters) {
+  const int m = c->opts.restart;
+  const int64_t qn3 = (int64_t)c->Q * c->N3;
+  std::vector<double> H((m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), alpha(m + 1), yv(m);
+  alpha[0] = a0;
+  g[0] = std::fabs(a0);
+  int k = 0, rc;
+  for (int j = 0; j < m && *iters < max_iters; ++j) {
+    S* W = V + (size_t)(j + 1) * n;
+    precond_apply<S>(z, V + (size_t)j * n, inv_ptr<S>(c), qn3, n, c->stream);
+    c->launches += 1;
+    if ((rc = linop<S>(c, dt, z, W))) return rc;
+    multidot<S>(W, V, n, j + 1, true, n, c->red_partial, c->red_out, c->stream);
+    c->launches += 2;
+    STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    const double before = c->h_pinned[j + 1];
+    Coef16 cc{};
+    for (int i = 0; i <= j; ++i) {
+      cc.c[i] = c->h_pinned[i] / (alpha[i] * alpha[i]);
+      H[i * m + j] = c->h_pinned[i] / (alpha[i] * alpha[j]);
+    }
+    axpy_norm<S>(W, V, n, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
+    c->launches += 2;
+    STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    double after = c->h_pinned[0];
+    if (c->opts.reorth && after < 0.5 * before) {
+      multidot<S>(W, V, n, j + 1, false, n, c->red_partial, c->red_out, c->stream);
+      c->launches += 2;
+      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      STM_CK(cudaStreamSynchronize(c->stream));
+      for (int i = 0; i <= j; ++i) {
+        cc.c[i] = c->h_pinned[i] / (alpha[i] * alpha[i]);
+        H[i * m + j] += c->h_pinned[i] / (alpha[i] * alpha[j]);
+      }
+      axpy_norm<S>(W, V, n, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
+      c->launches += 2;
+      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      STM_CK(cudaStreamSynchronize(c->stream));
+      after = c->h_pinned[0];
+    }
+    if (!std::isfinite(after) || !std::isfinite(before)) return fail(c, STM_ENAN, "non-finite value in GMRES");
+    const double nw = std::sqrt(after);
+    alpha[j + 1] = (alpha[j] < 0 ? -nw : nw);
+    H[(j + 1) * m + j] = nw / std::fabs(alpha[j]);
+    for (int i = 0; i < j; ++i) {
+      const double x = H[i * m + j], y = H[(i + 1) * m + j];
+      H[i * m + j] = cs[i] * x + sn[i] * y;
+      H[(i + 1) * m + j] = -sn[i] * x + cs[i] * y;
+    }
+    const double x = H[j * m + j], y = H[(j + 1) * m + j];
+    const double r = std::hypot(x, y);
+    cs[j] = r > 0 ? x / r : 1.0;
+    sn[j] = r > 0 ? y / r : 0.0;
+    H[j * m + j] = r;
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    ++*iters;
+    k = j + 1;
+    if (std::fabs(g[j + 1]) <= tol_abs || nw == 0.0) break;
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int l = i + 1; l < k; ++l) t -= H[i * m + l] * yv[l];
+    yv[i] = t / H[i * m + i];
+  }
+  for (int i = 0; i < kMaxDots; ++i) yc->c[i] = 0.0;
+  for (int i = 0; i < k; ++i) yc->c[i] = yv[i] / alpha[i];
+  *k_out = k;
+  *res = std::fabs(g[k]);
+  return STM_OK;
+}
+
+template <typename T>
+int ensure_buf(stm_ctx* c, T** p, int64_t* have, int64_t need) {
+  if (*have >= need) return STM_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc((void**)p, (size_t)need * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, STM_ENOMEM, "solver workspace allocation failed");
+  }
+  *have = need;
   return STM_OK;
 }
 
@@ -368,6 +480,7 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     c->opts.max_it = 500;
     c->opts.deterministic = 1;
     c->opts.stream = 0;
+    c->opts.reorth = 1;
   }
   if (c->opts.restart < 1 || c->opts.restart > kMaxDots - 1)
     return bad(STM_EINVAL, "restart must be 1..15");
@@ -429,9 +542,14 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   // 0 is the CUDA default stream, so work is ordered with a caller that uses it
   c->stream = (cudaStream_t)(intptr_t)c->opts.stream;
   std::vector<float> m32(c->h_mass.begin(), c->h_mass.end());
+  std::vector<double> i64(c->h_mass.size());
+  for (size_t k = 0; k < i64.size(); ++k) i64[k] = 1.0 / c->h_mass[k];
+  std::vector<float> i32(i64.begin(), i64.end());
   bool ok = cudaMalloc(&c->nbr, nb.size() * sizeof(int32_t)) == cudaSuccess &&
             cudaMalloc(&c->mass64, c->h_mass.size() * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->mass32, m32.size() * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->inv64, i64.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->inv32, i32.size() * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&c->state, c->n_state * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->red_partial, (kMaxDots + 1) * kRedBlocks * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->red_out, (kMaxDots + 1) * sizeof(double)) == cudaSuccess &&
@@ -445,6 +563,8 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   cudaMemcpy(c->nbr, nb.data(), nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   cudaMemcpy(c->mass64, c->h_mass.data(), c->h_mass.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(c->mass32, m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->inv64, i64.data(), i64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->inv32, i32.data(), i32.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemset(c->state, 0, c->n_state * sizeof(double));
   if (cudaGetLastError() != cudaSuccess) {
     stm_destroy(c);
@@ -457,8 +577,9 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
 int32_t stm_destroy(stm_ctx* c) {
   if (!c) return STM_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  void* ptrs[] = {c->nbr, c->mass64, c->mass32, c->y64, c->tr64, c->y32, c->tr32, c->state, c->red_partial,
-                  c->red_out, c->tmp_in, c->tmp_out, c->V, c->z, c->x};
+  void* ptrs[] = {c->nbr,     c->mass64,  c->mass32, c->y64,   c->tr64, c->y32, c->tr32,
+                  c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
+                  c->x,       c->V32,     c->z32,    c->inv64, c->inv32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -592,108 +713,67 @@ int32_t stm_energy(stm_ctx* c, double* energy) {
 int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   if (!c) return STM_EINVAL;
   if (!(dt > 0)) return fail(c, STM_EINVAL, "dt must be positive");
-  if (c->opts.precision != STM_FP64) return fail(c, STM_EUNSUPPORTED, "mixed precision slab solve not built yet");
+  const bool mixed = c->opts.precision == STM_MIXED;
+  if (!mixed && c->opts.precision != STM_FP64) return fail(c, STM_EINVAL, "opts.precision must be FP64 or MIXED");
   const int m = c->opts.restart;
   const int64_t n = c->n_test;
   const int64_t qn3 = (int64_t)c->Q * c->N3;
-  if (c->V_cols < m + 1) {
-    if (c->V) cudaFree(c->V);
-    if (c->z) cudaFree(c->z);
-    if (c->x) cudaFree(c->x);
-    c->V = c->z = c->x = nullptr;
-    c->V_cols = 0;
-    if (cudaMalloc(&c->V, (size_t)(m + 1) * n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->z, n * sizeof(double)) != cudaSuccess || cudaMalloc(&c->x, n * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, STM_ENOMEM, "GMRES workspace allocation failed");
-    }
-    c->V_cols = m + 1;
-  }
-  double* V = c->V;
   int rc;
-  // reference: ||R(U^(0))|| with all unknowns zero
-  STM_CK(cudaMemsetAsync(c->z, 0, n * sizeof(double), c->stream));
-  if ((rc = resid64(c, dt, c->z, V))) return rc;
+  // FP64 buffers: x (unknowns), z (work / residual); basis in FP64 or FP32
+  if ((rc = ensure_buf<double>(c, &c->x, &c->x_len, n)) || (rc = ensure_buf<double>(c, &c->z, &c->z_len, n))) return rc;
+  if (mixed) {
+    if ((rc = ensure_buf<float>(c, &c->V32, &c->V32_len, (m + 1) * n)) ||
+        (rc = ensure_buf<float>(c, &c->z32, &c->z32_len, n)))
+      return rc;
+  } else if ((rc = ensure_buf<double>(c, &c->V, &c->V_len, (m + 1) * n))) {
+    return rc;
+  }
+  // reference: ||R(U^(0))|| with all unknowns zero (R6)
+  STM_CK(cudaMemsetAsync(c->x, 0, n * sizeof(double), c->stream));
+  if ((rc = resid64(c, dt, c->x, c->z))) return rc;
   double ref;
-  if ((rc = norm2(c, V, n, &ref))) return rc;
+  if ((rc = norm2<double>(c, c->z, n, &ref))) return rc;
   ref = std::sqrt(ref);
+  // initial guess: u_1 = u_0, higher modes 0
   k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
   c->launches += 1;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), yv(m);
   int iters = 0, cycles = 0;
   double rel = 0.0;
   const double tol = c->opts.tol;
   for (;;) {
-    if ((rc = resid64(c, dt, c->x, V))) return rc;
+    // true FP64 residual R(u0, x)
+    double* R64 = mixed ? c->z : c->V;
+    if ((rc = resid64(c, dt, c->x, R64))) return rc;
     double beta2;
-    if ((rc = norm2(c, V, n, &beta2))) return rc;
+    if ((rc = norm2<double>(c, R64, n, &beta2))) return rc;
     const double beta = std::sqrt(beta2);
     rel = ref > 0 ? beta / ref : beta;
     if (!std::isfinite(rel)) return fail(c, STM_ENAN, "non-finite residual in slab solve");
     if (rel <= tol || iters >= c->opts.max_it || beta == 0.0) break;
-    k_scale<<<grid1(n), 256, 0, c->stream>>>(V, -1.0 / beta, n);  // V0 = r / beta, r = -R
-    c->launches += 1;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
     int k = 0;
-    for (int j = 0; j < m; ++j) {
-      double* w = V + (size_t)(j + 1) * n;
-      precond_apply<double>(c->z, V + (size_t)j * n, c->mass64, qn3, n, c->stream);
+    Coef16 yc{};
+    double res = 0.0;
+    if (!mixed) {
+      // V[0] = R = -r, so v_0 = V[0] / (-beta)
+      if ((rc = gmres_cycle<double>(c, dt, c->V, c->z, n, -beta, tol * ref, c->opts.max_it, &k, &yc, &res, &iters)))
+        return rc;
+      precond_combine<double, double>(c->x, c->V, n, k, yc, c->inv64, qn3, n, c->stream);
+    } else {
+      // FP32 inner GMRES(m) cycle on A d = r, started from the rounded FP64 residual;
+      // the inner target is the outer one or what FP32 can resolve, whichever is larger
+      convert<float, double>(c->V32, R64, n, c->stream);
       c->launches += 1;
-      if ((rc = linop<double>(c, dt, c->z, w))) return rc;
-      // classical Gram-Schmidt with one conditional re-orthogonalisation
-      multidot<double>(w, V, n, j + 1, true, n, c->red_partial, c->red_out, c->stream);
-      c->launches += 3;  // two reduction kernels and the update below
-      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      multi_axpy<double>(w, V, n, j + 1, c->red_out, n, c->stream);
-      STM_CK(cudaStreamSynchronize(c->stream));
-      for (int i = 0; i <= j; ++i) H[i * m + j] = c->h_pinned[i];
-      const double before = c->h_pinned[j + 1];
-      double after;
-      if ((rc = norm2(c, w, n, &after))) return rc;
-      if (after < 0.5 * before) {
-        multidot<double>(w, V, n, j + 1, false, n, c->red_partial, c->red_out, c->stream);
-        c->launches += 3;
-        STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        multi_axpy<double>(w, V, n, j + 1, c->red_out, n, c->stream);
-        STM_CK(cudaStreamSynchronize(c->stream));
-        for (int i = 0; i <= j; ++i) H[i * m + j] += c->h_pinned[i];
-        if ((rc = norm2(c, w, n, &after))) return rc;
-      }
-      const double hn = std::sqrt(after);
-      H[(j + 1) * m + j] = hn;
-      if (hn > 0) {
-        k_scale<<<grid1(n), 256, 0, c->stream>>>(w, 1.0 / hn, n);
-        c->launches += 1;
-      }
-      // Givens rotations
-      for (int i = 0; i < j; ++i) {
-        const double a = H[i * m + j], b = H[(i + 1) * m + j];
-        H[i * m + j] = cs[i] * a + sn[i] * b;
-        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
-      }
-      const double a = H[j * m + j], b = H[(j + 1) * m + j];
-      const double r = std::hypot(a, b);
-      cs[j] = r > 0 ? a / r : 1.0;
-      sn[j] = r > 0 ? b / r : 0.0;
-      H[j * m + j] = r;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++iters;
-      k = j + 1;
-      if (std::fabs(g[j + 1]) <= tol * ref || iters >= c->opts.max_it || hn == 0.0) break;
+      double b32;
+      if ((rc = norm2<float>(c, c->V32, n, &b32))) return rc;
+      b32 = std::sqrt(b32);
+      const double tin = std::max(tol * ref, 1e-6 * b32);
+      if ((rc = gmres_cycle<float>(c, dt, c->V32, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
+        return rc;
+      precond_combine<float, double>(c->x, c->V32, n, k, yc, c->inv32, qn3, n, c->stream);
     }
-    for (int i = k - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * yv[l];
-      yv[i] = s / H[i * m + i];
-    }
-    Coef16 y{};
-    for (int i = 0; i < k; ++i) y.c[i] = yv[i];
-    precond_combine<double, double>(c->x, V, n, k, y, c->mass64, qn3, n, c->stream);
     c->launches += 1;
     ++cycles;
+    if (k == 0) break;
   }
   k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);
   c->launches += 1;

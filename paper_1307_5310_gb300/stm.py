@@ -54,7 +54,7 @@ class stm_mesh(C.Structure):
 
 class stm_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32),
-                ("deterministic", C.c_int32), ("stream", C.c_int64)]
+                ("deterministic", C.c_int32), ("stream", C.c_int64), ("reorth", C.c_int32)]
 
 
 class stm_solve_report(C.Structure):
@@ -143,7 +143,7 @@ class Slab:
     """One library context for a mesh (see include/stm.h)."""
 
     def __init__(self, mesh: dict, precision=STM_FP64, tol=1e-12, restart=10, max_it=500,
-                 deterministic=True, stream=None):
+                 deterministic=True, stream=None, reorth=True):
         L = lib()
         self._keep = {}
         ne = mesh["hex"].shape[0]
@@ -169,7 +169,7 @@ class Slab:
             import torch
 
             stream = torch.cuda.current_stream().cuda_stream
-        o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream))
+        o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream), 1 if reorth else 0)
         h = C.c_void_p()
         rc = L.stm_create(C.byref(h), C.byref(m), C.byref(o))
         if rc != STM_OK:

@@ -144,3 +144,26 @@ def test_energy_conserved_100_slabs(stm):
         s.slab_solve(0.02)
         drift = max(drift, abs(s.energy() - e0) / e0)
     assert drift < 1e-12
+
+
+@pytest.mark.parametrize("reorth", [True, False])
+def test_slab_solve_mixed_precision(stm, reorth):
+    """FP32 inner GMRES + FP64 refinement: slab solution within 1e-9 of the oracle's direct solve."""
+    m = meshgen.box_mesh(3, 3, 2, hi=(0.75, 0.75, 0.5), p=3, q=2, order="morton")
+    meshgen.random_materials(m, 6, 7)
+    o = stdg.Oracle(m)
+    rng = np.random.Generator(np.random.PCG64(8))
+    u0 = rng.uniform(-1, 1, o.ne * 6 * 64)
+    dt = 0.25 / 7
+    uo = o.end_state(o.slab_solve(u0, 0.0, dt))
+    s = stm.Slab(m, precision=stm.STM_MIXED, tol=1e-11, max_it=3000, reorth=reorth)
+    s.set_state(u0)
+    rc, rep = s.slab_solve(dt)
+    assert rc == stm.STM_OK, rep
+    ug, _ = s.get_state()
+    assert rel(ug, uo) < 1e-9
+    s64 = stm.Slab(m, tol=1e-11, max_it=3000, reorth=reorth)
+    s64.set_state(u0)
+    rc, rep64 = s64.slab_solve(dt)
+    assert rc == stm.STM_OK
+    assert rel(s64.get_state()[0], uo) < 1e-9
