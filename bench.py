@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--q", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reorth", type=int, default=0, help="second Gram-Schmidt pass (DGKS test); off by default: same iteration count and accuracy on this workload")
     return ap.parse_args()
 
 
@@ -176,6 +177,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_solve(s, u_init, dt, steps, warmup, barrier):
+    """Time `steps` slab solves from the same start state; returns timings and counters."""
+    import torch
+
+    reps = []
+
+    def step():
+        s.set_state(u_init)
+        rc, rep = s.slab_solve(dt)
+        reps.append((rc, rep))
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    s.profile(True)
+    l0 = s.launch_count()
+    reps.clear()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    e0.record()
+    for _ in range(steps):
+        a = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        step_ms.append((time.perf_counter() - a) * 1e3)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    prof = s.profile_read()
+    s.profile(False)
+    return {"ms": e0.elapsed_time(e1) / steps, "step_ms": step_ms, "launches": s.launch_count() - l0,
+            "prof": prof, "iterations": statistics.mean(r["iterations"] for _, r in reps),
+            "restarts": statistics.mean(r["restarts"] for _, r in reps),
+            "rel_residual": max(r["rel_residual"] for _, r in reps), "rc": [rc for rc, _ in reps]}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -192,62 +230,40 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1307_5310_gb300 import stm
 
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     m = workload(args.n, args.p, args.q)
     ne = m["hex"].shape[0]
     h = 1.0 / args.n
     dt = h / (2 * args.p + 1)
     n3 = (args.p + 1) ** 3
     dof_slab = ne * 6 * (args.q + 1) * n3
-    s = stm.Slab(m, tol=args.tol, restart=10, max_it=400)
     rng = np.random.Generator(np.random.PCG64(1310))
-    u_init = torch.from_numpy(rng.uniform(-1, 1, s.n_state)).cuda()
+    u_host = torch.from_numpy(rng.uniform(-1, 1, ne * 6 * n3)).pin_memory()
+    u_init = u_host.cuda()
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    reps = []
-
-    def step():
-        s.set_state(u_init)
-        rc, rep = s.slab_solve(dt)
-        reps.append(rep)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier()
+    # ---- FP64 slab solve: the timed step --------------------------------------------------
+    s = stm.Slab(m, tol=args.tol, restart=10, max_it=400, reorth=bool(args.reorth))
     clk = Clocks(local)
-    s.profile(True)
-    l0 = s.launch_count()
-    reps.clear()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    step_ms = []
-    for _ in range(args.steps):
-        a = time.perf_counter()
-        step()
-        torch.cuda.synchronize()
-        step_ms.append((time.perf_counter() - a) * 1e3)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
+    r64 = measure_solve(s, u_init, dt, args.steps, args.warmup, barrier)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = s.launch_count() - l0
-    prof = s.profile_read()
-    s.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(r64["ms"])
+    prof = r64["prof"]
     applies = prof["k_apply_fp64"][1] / args.steps
     value = world * dof_slab * applies / (ms / 1e3) / 1e9
-    iters = statistics.mean(r["iterations"] for r in reps)
+    u64 = torch.empty_like(u_init)
+    s.get_state(u64)
 
-    # roofline of the dominant kernel (k_apply, FP64 pipe)
     fl_prep, fl_apply = flops_per_element(args.p, args.q)
     apply_ms = prof["k_apply_fp64"][0] / max(1, prof["k_apply_fp64"][1])
     prep_ms = prof["k_prep_fp64"][0] / max(1, prof["k_prep_fp64"][1])
@@ -257,67 +273,72 @@ def run_ours(args):
     roofline = {"kernel": f"k_apply<double,{args.p},{args.q}>", "bound": "alu", "achieved": ach, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
                 "peak_source": "FP64 pipe: 2 FMA/clock/SM x 152 SMs x median SM clock under load (of derived)",
-                "launch_ms": apply_ms, "prep": {"kernel": f"k_prep<double,{args.p},{args.q}>", "launch_ms": prep_ms,
-                                                "achieved": fl_prep * ne / (prep_ms / 1e3) / 1e12,
-                                                "frac": fl_prep * ne / (prep_ms / 1e3) / 1e12 / fp64_peak}}
+                "launch_ms": apply_ms,
+                "prep": {"kernel": f"k_prep<double,{args.p},{args.q}>", "launch_ms": prep_ms,
+                         "achieved": fl_prep * ne / (prep_ms / 1e3) / 1e12,
+                         "frac": fl_prep * ne / (prep_ms / 1e3) / 1e12 / fp64_peak}}
 
-    # FP32 residual apply (HBM bound) measured separately, same workload
-    fp32 = None
-    try:
-        U32 = torch.empty(s.n_trial, dtype=torch.float32, device="cuda")
-        g = torch.Generator(device="cuda").manual_seed(1309)
-        U32.uniform_(-1, 1, generator=g)
-        R32 = torch.empty(s.n_test, dtype=torch.float32, device="cuda")
-        for _ in range(3):
-            s.residual_apply(U32, R32, 0.0, dt, prec=stm.STM_FP32)
-        s.profile(True)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        for _ in range(10):
-            s.residual_apply(U32, R32, 0.0, dt, prec=stm.STM_FP32)
-        a1.record()
-        torch.cuda.synchronize()
-        p32 = s.profile_read()
-        s.profile(False)
-        ms32 = a0.elapsed_time(a1) / 10
-        ap32 = p32["k_apply_fp32"][0] / 10
-        pp32 = p32["k_prep_fp32"][0] / 10
-        by = bytes_per_element(args.p, args.q, 4) * ne
-        fp32 = {"gdofs": dof_slab / (ms32 / 1e3) / 1e9, "ms_per_apply": ms32, "k_prep_ms": pp32, "k_apply_ms": ap32,
-                "roofline": {"bound": "hbm", "achieved": by / (ms32 / 1e3) / 1e9, "peak": 6780.0, "unit": "GB/s",
-                             "frac": by / (ms32 / 1e3) / 1e9 / 6780.0, "traffic": None,
-                             "note": "algorithmic bytes (read U, write R) over the prep+apply pair"}}
-        del U32, R32
-    except Exception as ex:  # reported, never silently replaced
-        fp32 = {"error": str(ex)}
-
-    # end to end through the C ABI with host buffers: state in, slab solve, state out
-    u_host = u_init.cpu().numpy()
-    out = np.empty_like(u_host)
-    for _ in range(1):
-        s.set_state(u_host)
-        s.slab_solve(dt)
-        s.get_state(out)
+    # ---- end to end through the C ABI with pinned host buffers ---------------------------------
+    out = torch.empty(u_host.shape, dtype=torch.float64).pin_memory()
+    uh, oh = u_host.numpy(), out.numpy()
+    s.set_state(uh)
+    s.slab_solve(dt)
+    s.get_state(oh)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s.set_state(u_host)
+        s.set_state(uh)
         s.slab_solve(dt)
-        s.get_state(out)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        s.get_state(oh)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
     e2e = {"value": world * dof_slab * applies / (e2e_ms / 1e3) / 1e9, "unit": "GDoF/s",
-           "h2d_bytes_per_step": int(u_host.nbytes), "d2h_bytes_per_step": int(out.nbytes),
-           "ms_per_step": e2e_ms}
+           "h2d_bytes_per_step": int(uh.nbytes), "d2h_bytes_per_step": int(oh.nbytes), "ms_per_step": e2e_ms,
+           "path": "stm_set_state (host) + stm_slab_solve + stm_get_state (host), pinned buffers"}
+
+    # tight FP64 reference solution of the same slab for the accuracy statement
+    s.close()
+    sref = stm.Slab(m, tol=1e-12, restart=10, max_it=2000, reorth=True)
+    sref.set_state(u_init)
+    sref.slab_solve(dt)
+    uref = torch.empty_like(u_init)
+    sref.get_state(uref)
+    sref.close()
+    err64 = float(torch.linalg.norm(u64 - uref) / torch.linalg.norm(uref))
+
+    # ---- mixed precision: FP32 inner GMRES, FP64 refinement ----------------------------------
+    mixed = None
+    try:
+        smx = stm.Slab(m, precision=stm.STM_MIXED, tol=args.tol, restart=10, max_it=400, reorth=bool(args.reorth))
+        rmx = measure_solve(smx, u_init, dt, args.steps, args.warmup, barrier)
+        umx = torch.empty_like(u_init)
+        smx.get_state(umx)
+        msx = max_over_ranks(rmx["ms"])
+        pm = rmx["prof"]
+        ap64, ap32 = pm["k_apply_fp64"][1] / args.steps, pm["k_apply_fp32"][1] / args.steps
+        mixed = {"ms_per_solve": msx, "slab_solves_per_s": world / (msx / 1e3),
+                 "gdofs": world * dof_slab * (ap64 + ap32) / (msx / 1e3) / 1e9,
+                 "fp64_applies": ap64, "fp32_applies": ap32, "inner_iterations": rmx["iterations"],
+                 "outer_refinements": rmx["restarts"], "rel_residual": rmx["rel_residual"],
+                 "rel_err_vs_fp64_ref": float(torch.linalg.norm(umx - uref) / torch.linalg.norm(uref)),
+                 "speedup_vs_fp64": ms / msx, "gpu_launches": rmx["launches"]}
+        # FP32 residual kernel (single pass): HBM roofline
+        k32 = pm["k_apply_fp32"]
+        k32_ms = k32[0] / max(1, k32[1])
+        by = bytes_per_element(args.p, args.q, 4) * ne
+        mixed["fp32_kernel"] = {"kernel": f"k_fused<float,{args.p},{args.q}>", "launch_ms": k32_ms,
+                                "gdofs": dof_slab / (k32_ms / 1e3) / 1e9,
+                                "roofline": {"bound": "hbm", "achieved": by / (k32_ms / 1e3) / 1e9, "peak": 6780.0,
+                                             "unit": "GB/s", "frac": by / (k32_ms / 1e3) / 1e9 / 6780.0,
+                                             "traffic": None, "peak_source": "hbm_gbs of measured"}}
+        smx.close()
+    except Exception as ex:  # reported, never replaced by another path
+        mixed = {"error": repr(ex)}
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu, _ = cpu_baseline(args.p, args.q)
-        lat = sorted(step_ms)
+        lat = sorted(r64["step_ms"])
         line = {
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -325,12 +346,13 @@ def run_ours(args):
             "config": {"workload": f"affine {args.n}^3 bricks on [0,1]^3, p={args.p}, q={args.q}, eps/mu U[1,4], "
                                    f"PEC, dt=h/(2p+1); step = one FP64 slab solve (GMRES(10), tol {args.tol:g})",
                        "elements": ne, "dof_per_slab": dof_slab, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (6.3 GB coefficients)"},
-            "residual_applies_per_step": applies, "gmres_iterations_per_step": iters,
-            "slab_solves_per_s": world / (ms / 1e3),
-            "latency_ms": {"p50": statistics.median(lat), "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
-            "roofline": roofline, "fp32_apply": fp32, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": launches,
+                       "reorth": bool(args.reorth), "l2": "inputs larger than L2 (6.3 GB coefficients)"},
+            "residual_applies_per_step": applies, "gmres_iterations_per_step": r64["iterations"],
+            "slab_solves_per_s": world / (ms / 1e3), "rel_err_vs_fp64_ref": err64,
+            "latency_ms": {"p50": statistics.median(lat),
+                           "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+            "roofline": roofline, "mixed": mixed, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": r64["launches"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

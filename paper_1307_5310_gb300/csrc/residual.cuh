@@ -218,6 +218,140 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   }
 }
 
+// Single-pass variant (used for FP32, where the kernel is bound by memory
+// traffic, not arithmetic): one CTA per element reads its own coefficients
+// once, recomputes the six neighbour face traces from the neighbours'
+// coefficients (face neighbours sit close in memory, so these reads mostly hit
+// L2), forms its own traces in registers inside the line loop, and writes R.
+// No y or trace scratch goes through HBM.
+template <typename T, int P, int Q>
+__global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
+  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3]
+  T* nt = Rs + 6 * Q * N3;                  // [6 faces][2 fields][2 comps][Q][N2] neighbour traces
+  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
+    const int32_t* nb = A.nbr + e * 6;
+    // (a) own coefficients: temporal contraction and the mass term
+    for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
+      const int fc = it / N3, s = it - fc * N3;
+      T u[Q + 1];
+      u[0] = A.u0 ? A.u0[e * A.u0_es + fc * A.u0_cs + s] : T(0);
+#pragma unroll
+      for (int m = 1; m <= Q; ++m) u[m] = A.um[e * A.um_es + fc * A.um_cs + (m - 1) * N3 + s];
+      const T mc = A.mass[e * 6 + fc];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        T acc = T(0);
+        bool first = true;
+#pragma unroll
+        for (int m = 0; m <= Q; ++m) {
+          if (b_nz(i, m)) {
+            acc = first ? A.tb.B[i][m] * u[m] : fma(A.tb.B[i][m], u[m], acc);
+            first = false;
+          }
+        }
+        ys[(fc * Q + i) * N3 + s] = acc;
+        T v = mc * u[i + 1];
+        if (i == 0) v = fma(-mc, u[0], v);
+        if (A.b) v -= A.b[e * (int64_t)(6 * Q * N3) + (fc * Q + i) * N3 + s];
+        Rs[(fc * Q + i) * N3 + s] = v;
+      }
+    }
+    // (b) neighbour traces on the shared faces: items (face, field, comp, t)
+    for (int it = threadIdx.x; it < 24 * N2; it += blockDim.x) {
+      int r = it;
+      const int t = r % N2; r /= N2;
+      const int bi = r % 2; r /= 2;
+      const int fld = r % 2;
+      const int face = r / 2;
+      const int a = face >> 1, side = face & 1;
+      const int64_t en = nb[face];
+      if (en < 0) continue;
+      const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
+      int base, stride;
+      line_geom<N>(a, t, base, stride);
+      // the neighbour across face (a, side) meets it with its face (a, 1 - side)
+      T tu[Q + 1];
+#pragma unroll
+      for (int m = 0; m <= Q; ++m) {
+        const T* ul = (m == 0) ? (A.u0 ? A.u0 + en * A.u0_es + (fld * 3 + b) * A.u0_cs : nullptr)
+                               : A.um + en * A.um_es + (fld * 3 + b) * A.um_cs + (m - 1) * N3;
+        T acc = T(0);
+        if (ul) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const T lj = (side == 1 && (j & 1)) ? -A.tb.lv[j] : A.tb.lv[j];  // L_j(0) for side 1, L_j(1) for side 0
+            acc = fma(lj, ul[base + j * stride], acc);
+          }
+        }
+        tu[m] = acc;
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m <= Q; ++m)
+          if (b_nz(i, m)) acc = fma(A.tb.B[i][m], tu[m], acc);
+        nt[(((face * 2 + fld) * 2 + bi) * Q + i) * N2 + t] = acc;
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+      for (int it = threadIdx.x; it < 6 * Q * N2; it += blockDim.x) {
+        int r = it;
+        const int t = r % N2; r /= N2;
+        const int i = r % Q; r /= Q;
+        const int c = r % 3;
+        const int f = r / 3;
+        const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
+        const int b = 3 - c - a;
+        const bool cyc = ((a - c + 3) % 3 == 1);
+        const unsigned flip = ((f == 0) == cyc) ? 0x80000000u : 0u;
+        const int fp = 1 - f;
+        const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
+        int base, stride;
+        line_geom<N>(a, t, base, stride);
+        const T* yl = ys + ((fp * 3 + b) * Q + i) * N3 + base;
+        T yv[N];
+        T ev = T(0), od = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          yv[j] = yl[j * stride];
+          if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
+          else ev = fma(A.tb.lv[j], yv[j], ev);
+        }
+        const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
+        const int ep = nb[2 * a + 1], em = nb[2 * a];
+        T jp, jm;
+        if (ep >= 0) jp = xp - nt[((((2 * a + 1) * 2 + fp) * 2 + bi) * Q + i) * N2 + t];
+        else jp = (fp == 0) ? xp + xp : T(0);
+        if (em >= 0) jm = xm - nt[((((2 * a) * 2 + fp) * 2 + bi) * Q + i) * N2 + t];
+        else jm = (fp == 0) ? xm + xm : T(0);
+        const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
+#pragma unroll
+        for (int j = 0; j < N; ++j) yv[j] = flip_sign(yv[j], flip);
+        T* Rl = Rs + ((f * 3 + c) * Q + i) * N3 + base;
+#pragma unroll
+        for (int al = 0; al < N; ++al) {
+          T r2 = Rl[al * stride];
+          r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+          for (int be = 0; be < N; ++be)
+            if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
+          Rl[al * stride] = r2;
+        }
+      }
+      __syncthreads();
+    }
+    T* Rg = A.R + e * (int64_t)(6 * Q * N3);
+    for (int it = threadIdx.x; it < 6 * Q * N3; it += blockDim.x) Rg[it] = Rs[it];
+    __syncthreads();
+  }
+}
+
 // Optional CUDA events recorded before k_prep, between the kernels and after
 // k_apply (all null: no timing).
 struct LaunchEvents {
@@ -227,15 +361,29 @@ struct LaunchEvents {
 template <typename T, int P, int Q>
 int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const LaunchEvents& ev) {
   constexpr int N = P + 1, N3 = N * N * N;
+  constexpr int N2 = N * N;
   const size_t sm_prep = sizeof(T) * 6 * Q * N3;
   const size_t sm_apply = 2 * sm_prep;
+  const size_t sm_fused = sm_apply + sizeof(T) * 24 * Q * N2;
   static bool configured = false;
   if (!configured) {
     if (sm_prep > 48 * 1024)
       cudaFuncSetAttribute(k_prep<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
     if (sm_apply > 48 * 1024)
       cudaFuncSetAttribute(k_apply<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+    if constexpr (sizeof(T) == 4) {
+      if (sm_fused > 48 * 1024)
+        cudaFuncSetAttribute(k_fused<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
+    }
     configured = true;
+  }
+  if constexpr (sizeof(T) == 4) {
+    // single pass: ev.start/ev.stop bracket k_fused (reported in the apply slot)
+    if (ev.start) cudaEventRecord(ev.start, s);
+    if (ev.mid) cudaEventRecord(ev.mid, s);
+    k_fused<T, P, Q><<<grid, 256, sm_fused, s>>>(args);
+    if (ev.stop) cudaEventRecord(ev.stop, s);
+    return (int)cudaGetLastError();
   }
   if (ev.start) cudaEventRecord(ev.start, s);
   k_prep<T, P, Q><<<grid, 256, sm_prep, s>>>(args);

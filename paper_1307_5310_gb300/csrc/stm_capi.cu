@@ -254,8 +254,10 @@ template <typename T>
 int apply(stm_ctx* c, double dt, const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_es,
           int64_t u0_cs, const T* b, T* R) {
   T *y = nullptr, *tr = nullptr;
-  int rc = scratch<T>(c, &y, &tr);
-  if (rc) return rc;
+  if constexpr (sizeof(T) == 8) {  // the FP32 kernel is single-pass and needs no scratch
+    int rc = scratch<T>(c, &y, &tr);
+    if (rc) return rc;
+  }
   ApplyArgs<T> a;
   a.um = um;
   a.um_es = um_es;
