@@ -53,7 +53,9 @@ extern "C" {
 #define STM_ENOTCONV 1        /* solver stopped at max_it; best iterate kept     */
 
 #define STM_GEOM_BRICK 0     /* axis-aligned boxes (affine, diagonal DF)          */
-#define STM_GEOM_TRILINEAR 2 /* trilinear maps from the 8 vertices (curved)       */
+#define STM_GEOM_TRILINEAR 2 /* trilinear maps from the 8 vertices (curved); face 2d+1
+                                of e and face 2d of its neighbour must have the same
+                                four vertex ids in the same reference order         */
 
 #define STM_FP64 0  /* residual apply / solve in double precision             */
 #define STM_FP32 1  /* residual apply in single precision (float arrays)       */
@@ -75,7 +77,7 @@ typedef struct {
                           x^_d = 1), -1 on the boundary; face 2d+1 of e must meet
                           face 2d of nbr                                          */
   const uint8_t *p;    /* [n_elem] spatial degree (isotropic), 0..7              */
-  const uint8_t *q;    /* [n_elem] temporal degree, 1..4                         */
+  const uint8_t *q;    /* [n_elem] temporal degree, 1..6                         */
   const double *eps;   /* [n_elem] permittivity, > 0                             */
   const double *mu;    /* [n_elem] permeability, > 0                             */
   int32_t geometry;    /* STM_GEOM_*                                              */
@@ -126,10 +128,32 @@ int32_t stm_get_state(stm_ctx *ctx, double *t, void *u, int32_t mem);
 
 /* L2 projection of E0(x), H0(x) onto the covariant spatial spaces (initial
  * data of Eq. maxwell), evaluated by the callback at p+2 Gauss points per
- * direction; becomes the state at time t.  Either callback may be NULL (0). */
+ * direction; becomes the state at time t.  Either callback may be NULL (0).
+ * Built for STM_GEOM_BRICK; curved meshes return STM_EUNSUPPORTED (set the
+ * state directly). */
 typedef void (*stm_field_fn)(void *user, int64_t npts, const double *x /*[npts][3]*/,
                              double *out /*[npts][3]*/);
 int32_t stm_set_initial(stm_ctx *ctx, double t, stm_field_fn E0, stm_field_fn H0, void *user);
+
+/* Current density J of Eq. maxwell as a sum of Gaussian pulses (at most 8):
+ *   J(x, t) = sum_k amp_k dir_k exp(-|x - centre_k|^2 / (2 sigma_x^2)) exp(-(t - t0_k)^2 / (2 sigma_t^2)).
+ * It enters the load l_E(v) = (J, v) of Eq. bilinearform:C, integrated on the
+ * device with p+2 Gauss points per direction and q+2 in time.  n_src = 0
+ * removes all sources.  The array is copied. */
+typedef struct {
+  double centre[3], dir[3];
+  double sigma_x, t0, sigma_t, amp;
+} stm_gauss_src;
+int32_t stm_set_source_gauss(stm_ctx *ctx, const stm_gauss_src *src, int32_t n_src);
+
+/* Boundary data g of Eq. maxwell (n x E = n x g): l_H(w) = -<n x g, w> on the
+ * boundary faces (Eq. bilinearform:C).  The callback gets npts space-time
+ * points x[k] = (x, y, z, t) and writes g there; it is called on the host once
+ * per slab (p+2 Gauss points per face direction, q+2 in time).  NULL = PEC
+ * (g = 0). */
+typedef void (*stm_st_field_fn)(void *user, int64_t npts, const double *xt /*[npts][4]*/,
+                                double *out /*[npts][3]*/);
+int32_t stm_set_boundary(stm_ctx *ctx, stm_st_field_fn g, void *user);
 
 /* Solve one slab (Sec. 5.4): find modes 1..q of U with R_h(U) = 0 by GMRES
  * (restart opts.restart, right preconditioned by the time-derivative terms of

@@ -38,7 +38,7 @@
 namespace stm {
 
 constexpr int kMaxN = 8;   // p <= 7
-constexpr int kMaxQ = 4;   // q <= 4
+constexpr int kMaxQ = 6;   // q <= 6
 
 template <typename T>
 struct Tables {
@@ -59,7 +59,8 @@ struct ApplyArgs {
   T* tr;                  // [ne][2][3 axes][2 sides][2 comps][q][N2] scratch: face traces
   T* R;                   // [ne][2][3][q][N3] residual (test layout)
   const int32_t* nbr;     // [ne][6]
-  const T* mass;          // [ne][2][3]: eps G_c (E rows), mu G_c (H rows)
+  const T* mass;          // [ne][2][3]: eps G_c (E rows), mu G_c (H rows); nullptr: R already
+                          //   holds the mass term (curved elements, written by k_mass_curved)
   int64_t n_elem;
   Tables<T> tb;
 };
@@ -147,74 +148,83 @@ template <typename T, int P, int Q>
 __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
-  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3]
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [3][Q][N3]: y of the other field
+  T* Rs = ys + 3 * Q * N3;                  // [3][Q][N3]: residual rows of this field
   for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
-    const T* yg = A.y + e * (int64_t)(6 * Q * N3);
-    for (int it = threadIdx.x; it < 6 * Q * N3; it += blockDim.x) {
-      ys[it] = yg[it];
-      const int fc = it / (Q * N3);
-      const int r = it - fc * (Q * N3);
-      const int i = r / N3, s = r - i * N3;
-      const T mc = A.mass[e * 6 + fc];
-      T v = mc * A.um[e * A.um_es + fc * A.um_cs + i * N3 + s];
-      if (i == 0 && A.u0) v = fma(-mc, A.u0[e * A.u0_es + fc * A.u0_cs + s], v);
-      if (A.b) v -= A.b[e * (int64_t)(6 * Q * N3) + it];
-      Rs[it] = v;
-    }
-    __syncthreads();
     const int32_t* nb = A.nbr + e * 6;
 #pragma unroll 1
-    for (int k = 0; k < 2; ++k) {
-      for (int it = threadIdx.x; it < 6 * Q * N2; it += blockDim.x) {
-        int r = it;
-        const int t = r % N2; r /= N2;
-        const int i = r % Q; r /= Q;
-        const int c = r % 3;
-        const int f = r / 3;
-        const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
-        const int b = 3 - c - a;
-        // eps_{c a b}: +1 for cyclic (c, a, b); the sign s_F eps_{cab} is applied by
-        // flipping sign bits of the inputs (integer pipe), not by multiplies
-        const bool cyc = ((a - c + 3) % 3 == 1);
-        const unsigned flip = ((f == 0) == cyc) ? 0x80000000u : 0u;
-        const int fp = 1 - f;
-        const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
-        int base, stride;
-        line_geom<N>(a, t, base, stride);
-        const T* yl = ys + ((fp * 3 + b) * Q + i) * N3 + base;
-        // jumps of the tangential component b of field fp on the faces normal to a
-        const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * Q + i;  // side-0 slot within an element
-        constexpr int64_t per_el = 2 * 3 * 2 * 2 * (int64_t)Q * N2;
-        const T* tre = A.tr + e * per_el;
-        const T xm = tre[so * N2 + t];
-        const T xp = tre[(so + 2 * Q) * N2 + t];
-        const int ep = nb[2 * a + 1], em = nb[2 * a];
-        T jp, jm;
-        if (ep >= 0) jp = xp - A.tr[ep * per_el + so * N2 + t];
-        else jp = (fp == 0) ? xp + xp : T(0);
-        if (em >= 0) jm = xm - A.tr[em * per_el + (so + 2 * Q) * N2 + t];
-        else jm = (fp == 0) ? xm + xm : T(0);
-        const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
-        T yv[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) yv[j] = flip_sign(yl[j * stride], flip);
-        T* Rl = Rs + ((f * 3 + c) * Q + i) * N3 + base;
-#pragma unroll
-        for (int al = 0; al < N; ++al) {
-          T r = Rl[al * stride];
-          r = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r);
-#pragma unroll
-          for (int be = 0; be < N; ++be)
-            if (d_nz(al, be)) r = fma(A.tb.Dt[al][be], yv[be], r);
-          Rl[al * stride] = r;
+    for (int f = 0; f < 2; ++f) {
+      const int fp = 1 - f;
+      const T* yg = A.y + (e * 2 + fp) * (int64_t)(3 * Q * N3);
+      T* Rg = A.R + (e * 2 + f) * (int64_t)(3 * Q * N3);
+      const T* bg = A.b ? A.b + (e * 2 + f) * (int64_t)(3 * Q * N3) : nullptr;
+      for (int it = threadIdx.x; it < 3 * Q * N3; it += blockDim.x) {
+        ys[it] = yg[it];
+        const int cc = it / (Q * N3);
+        const int r = it - cc * (Q * N3);
+        const int i = r / N3, s = r - i * N3;
+        const int fc = f * 3 + cc;
+        T v;
+        if (A.mass) {
+          const T mc = A.mass[e * 6 + fc];
+          v = mc * A.um[e * A.um_es + fc * A.um_cs + i * N3 + s];
+          if (i == 0 && A.u0) v = fma(-mc, A.u0[e * A.u0_es + fc * A.u0_cs + s], v);
+        } else {
+          v = Rg[it];
         }
+        if (bg) v -= bg[it];
+        Rs[it] = v;
       }
       __syncthreads();
+#pragma unroll 1
+      for (int k = 0; k < 2; ++k) {
+        for (int it = threadIdx.x; it < 3 * Q * N2; it += blockDim.x) {
+          int r = it;
+          const int t = r % N2; r /= N2;
+          const int i = r % Q;
+          const int c = r / Q;
+          const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
+          const int b = 3 - c - a;
+          // eps_{c a b}: +1 for cyclic (c, a, b); the sign s_F eps_{cab} is applied by
+          // flipping sign bits of the inputs (integer pipe), not by multiplies
+          const bool cyc = ((a - c + 3) % 3 == 1);
+          const unsigned flip = ((f == 0) == cyc) ? 0x80000000u : 0u;
+          const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
+          int base, stride;
+          line_geom<N>(a, t, base, stride);
+          const T* yl = ys + (b * Q + i) * N3 + base;
+          // jumps of the tangential component b of field fp on the faces normal to a
+          const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * Q + i;  // side-0 slot within an element
+          constexpr int64_t per_el = 2 * 3 * 2 * 2 * (int64_t)Q * N2;
+          const T* tre = A.tr + e * per_el;
+          const T xm = tre[so * N2 + t];
+          const T xp = tre[(so + 2 * Q) * N2 + t];
+          const int ep = nb[2 * a + 1], em = nb[2 * a];
+          T jp, jm;
+          if (ep >= 0) jp = xp - A.tr[ep * per_el + so * N2 + t];
+          else jp = (fp == 0) ? xp + xp : T(0);
+          if (em >= 0) jm = xm - A.tr[em * per_el + (so + 2 * Q) * N2 + t];
+          else jm = (fp == 0) ? xm + xm : T(0);
+          const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
+          T yv[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) yv[j] = flip_sign(yl[j * stride], flip);
+          T* Rl = Rs + (c * Q + i) * N3 + base;
+#pragma unroll
+          for (int al = 0; al < N; ++al) {
+            T r2 = Rl[al * stride];
+            r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+            for (int be = 0; be < N; ++be)
+              if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
+            Rl[al * stride] = r2;
+          }
+        }
+        __syncthreads();
+      }
+      for (int it = threadIdx.x; it < 3 * Q * N3; it += blockDim.x) Rg[it] = Rs[it];
+      __syncthreads();
     }
-    T* Rg = A.R + e * (int64_t)(6 * Q * N3);
-    for (int it = threadIdx.x; it < 6 * Q * N3; it += blockDim.x) Rg[it] = Rs[it];
-    __syncthreads();
   }
 }
 
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
       u[0] = A.u0 ? A.u0[e * A.u0_es + fc * A.u0_cs + s] : T(0);
 #pragma unroll
       for (int m = 1; m <= Q; ++m) u[m] = A.um[e * A.um_es + fc * A.um_cs + (m - 1) * N3 + s];
-      const T mc = A.mass[e * 6 + fc];
+      const T mc = A.mass ? A.mass[e * 6 + fc] : T(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         T acc = T(0);
@@ -253,8 +263,13 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
           }
         }
         ys[(fc * Q + i) * N3 + s] = acc;
-        T v = mc * u[i + 1];
-        if (i == 0) v = fma(-mc, u[0], v);
+        T v;
+        if (A.mass) {
+          v = mc * u[i + 1];
+          if (i == 0) v = fma(-mc, u[0], v);
+        } else {
+          v = A.R[e * (int64_t)(6 * Q * N3) + (fc * Q + i) * N3 + s];
+        }
         if (A.b) v -= A.b[e * (int64_t)(6 * Q * N3) + (fc * Q + i) * N3 + s];
         Rs[(fc * Q + i) * N3 + s] = v;
       }
@@ -363,8 +378,8 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   constexpr int N = P + 1, N3 = N * N * N;
   constexpr int N2 = N * N;
   const size_t sm_prep = sizeof(T) * 6 * Q * N3;
-  const size_t sm_apply = 2 * sm_prep;
-  const size_t sm_fused = sm_apply + sizeof(T) * 24 * Q * N2;
+  const size_t sm_apply = sm_prep;
+  const size_t sm_fused = 2 * sm_prep + sizeof(T) * 24 * Q * N2;
   static bool configured = false;
   if (!configured) {
     if (sm_prep > 48 * 1024)

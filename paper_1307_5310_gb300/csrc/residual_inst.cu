@@ -1,5 +1,5 @@
 // One translation unit per spatial degree P (compiled with -DSTM_P=<P>):
-// instantiates the residual kernels of residual.cuh for q = 1..4 and both
+// instantiates the residual kernels of residual.cuh for q = 1..6 and both
 // precisions, so the build can compile the degrees in parallel.
 #include "residual.cuh"
 
@@ -22,6 +22,8 @@ int STM_CAT(launch_residual_p, STM_P)(int Q, const ApplyArgs<T>& a, cudaStream_t
     case 2: return launch_residual_pq<T, STM_P, 2>(a, s, grid, ev);
     case 3: return launch_residual_pq<T, STM_P, 3>(a, s, grid, ev);
     case 4: return launch_residual_pq<T, STM_P, 4>(a, s, grid, ev);
+    case 5: return launch_residual_pq<T, STM_P, 5>(a, s, grid, ev);
+    case 6: return launch_residual_pq<T, STM_P, 6>(a, s, grid, ev);
     default: return -1;
   }
 }

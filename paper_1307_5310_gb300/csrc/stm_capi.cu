@@ -13,7 +13,9 @@
 #include <string>
 #include <vector>
 
+#include "curved.cuh"
 #include "krylov.cuh"
+#include "load.cuh"
 #include "residual.cuh"
 #include "stm.h"
 
@@ -174,6 +176,26 @@ struct stm_ctx {
   int64_t V32_len = 0;
   float* z32 = nullptr;
   int64_t z32_len = 0;
+  // geometry: vertices of every element; curved metric
+  std::vector<double> h_X8;  // [ne][8][3]
+  std::vector<int32_t> h_nbr;  // [ne][6]
+  double* X8 = nullptr;
+  double *eps64 = nullptr, *mu64 = nullptr;
+  float *eps32 = nullptr, *mu32 = nullptr;
+  double* Gw64 = nullptr;  // [ne][6][(p+2)^3]
+  float* Gw32 = nullptr;
+  double* Pinv64 = nullptr;  // [ne][2][9]
+  float* Pinv32 = nullptr;
+  double* el = nullptr;      // per-element energies (curved)
+  CurvedTables ct{};
+  // load vector L (Gaussian currents, boundary data g), cached per (t0, dt)
+  std::vector<stm_gauss_src> srcs;
+  stm_st_field_fn gfn = nullptr;
+  void* guser = nullptr;
+  double* load64 = nullptr;
+  float* load32 = nullptr;
+  bool load_valid = false;
+  double load_t0 = 0.0, load_dt = 0.0;
   // instrumentation: kernel launch count, optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -231,6 +253,20 @@ const double* mass_ptr<double>(stm_ctx* c) { return c->mass64; }
 template <>
 const float* mass_ptr<float>(stm_ctx* c) { return c->mass32; }
 
+// curved element data in the working precision: 0 = w G at the Gauss points, 1 = eps, 2 = mu, 3 = Pinv
+template <typename T>
+const T* curved_ptr(stm_ctx* c, int which);
+template <>
+const double* curved_ptr<double>(stm_ctx* c, int which) {
+  const double* p[4] = {c->Gw64, c->eps64, c->mu64, c->Pinv64};
+  return p[which];
+}
+template <>
+const float* curved_ptr<float>(stm_ctx* c, int which) {
+  const float* p[4] = {c->Gw32, c->eps32, c->mu32, c->Pinv32};
+  return p[which];
+}
+
 template <typename T>
 int scratch(stm_ctx* c, T** y, T** tr);
 template <>
@@ -271,6 +307,14 @@ int apply(stm_ctx* c, double dt, const T* um, int64_t um_es, int64_t um_cs, cons
   a.R = R;
   a.nbr = c->nbr;
   a.mass = mass_ptr<T>(c);
+  if (c->geometry == STM_GEOM_TRILINEAR) {
+    // curved: the metric-dependent mass term goes first into R; the residual kernels add the rest
+    const int em = launch_mass_curved<T>(c->P, c->Q, um, um_es, um_cs, u0, u0_es, u0_cs, curved_ptr<T>(c, 0),
+                                         curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne, R, c->stream);
+    c->launches += 1;
+    if (em) return fail(c, STM_EDEVICE, std::string("curved mass launch: ") + cudaGetErrorString((cudaError_t)em));
+    a.mass = nullptr;
+  }
   a.n_elem = c->ne;
   a.tb = make_tables<T>(c->P, c->Q, dt);
   const int grid = (int)std::min<int64_t>(c->ne, 1 << 30);
@@ -300,10 +344,178 @@ int linop(stm_ctx* c, double dt, const T* xin, T* out) {
   return apply<T>(c, dt, xin, es, cs, nullptr, 0, 0, nullptr, out);
 }
 
-// R(U) with mode 0 = state (FP64) and modes 1..q = xin.
-int resid64(stm_ctx* c, double dt, const double* xin, double* out) {
+// R(U) = A U - b with mode 0 = state (FP64), modes 1..q = xin and the load b (or none).
+int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* out) {
   const int64_t es = 6LL * c->Q * c->N3, cs = (int64_t)c->Q * c->N3;
-  return apply<double>(c, dt, xin, es, cs, c->state, 6LL * c->N3, c->N3, nullptr, out);
+  return apply<double>(c, dt, xin, es, cs, c->state, 6LL * c->N3, c->N3, b, out);
+}
+
+// Load vector b = L on the slab (t0, t0 + dt] (Eq. bilinearform:C): Gaussian
+// currents on the device, boundary data g on the host.  Returns null when no
+// source and no boundary data are set (L = 0).  Cached per (t0, dt).
+int build_load(stm_ctx* c, double t0, double dt, const double** out) {
+  *out = nullptr;
+  if (c->srcs.empty() && !c->gfn) return STM_OK;
+  if (c->load_valid && c->load_t0 == t0 && c->load_dt == dt) {
+    *out = c->load64;
+    return STM_OK;
+  }
+  const int64_t n = c->n_test;
+  if (!c->load64) {
+    if (cudaMalloc(&c->load64, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->load32, n * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, STM_ENOMEM, "load vector allocation failed");
+    }
+  }
+  const int P = c->P, Q = c->Q, N = c->N, N3 = c->N3, nq = P + 2, nt = Q + 2;
+  std::vector<double> xq, wq, xt, wt;
+  gauss01(nq, xq, wq);
+  gauss01(nt, xt, wt);
+  std::vector<double> Lq(nq * N), Lt(nt * Q > 0 ? nt * kMaxQ : 1);
+  for (int g = 0; g < nq; ++g) legendre01(N, xq[g], &Lq[g * N]);
+  for (int g = 0; g < nt; ++g) legendre01(Q, xt[g], &Lt[g * kMaxQ]);
+  if (c->gfn) {
+    // l_H(w) = -<n x g, w> on boundary faces; in the reference face (Nanson, covariant
+    // transform) <n x g, w> = dt int int (n^ x g^) . w^ with g^ = DF^T g.
+    std::vector<double> hb(n, 0.0);
+    std::vector<int64_t> faces;
+    for (int64_t e = 0; e < c->ne; ++e)
+      for (int f = 0; f < 6; ++f)
+        if (c->h_nbr[6 * e + f] < 0) faces.push_back(6 * e + f);
+    const int64_t per_face = (int64_t)nt * nq * nq;
+    const int64_t chunk = std::max<int64_t>(1, (1 << 20) / per_face);
+    std::vector<double> xtp, gv, DFs;
+    std::vector<double> L0(N), L1(N);
+    legendre01(N, 0.0, L0.data());
+    legendre01(N, 1.0, L1.data());
+    for (size_t f0 = 0; f0 < faces.size(); f0 += chunk) {
+      const size_t f1 = std::min(faces.size(), f0 + chunk);
+      const int64_t np = (int64_t)(f1 - f0) * per_face;
+      xtp.resize(4 * np);
+      gv.resize(3 * np);
+      DFs.resize(9 * (f1 - f0) * nq * nq);
+      for (size_t fi = f0; fi < f1; ++fi) {
+        const int64_t e = faces[fi] / 6;
+        const int f = (int)(faces[fi] % 6), d = f / 2, sd = f % 2;
+        const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+        const double* X = &c->h_X8[24 * e];
+        for (int u = 0; u < nq; ++u)
+          for (int v = 0; v < nq; ++v) {
+            double xh[3];
+            xh[d] = sd;
+            xh[a1] = xq[u];
+            xh[a2] = xq[v];
+            double x[3] = {0, 0, 0};
+            double* DF = &DFs[(((fi - f0) * nq + u) * nq + v) * 9];
+            for (int k = 0; k < 9; ++k) DF[k] = 0.0;
+            for (int vv = 0; vv < 8; ++vv) {
+              const int bit[3] = {vv & 1, (vv >> 1) & 1, (vv >> 2) & 1};
+              double fa[3], dfa[3];
+              for (int a = 0; a < 3; ++a) {
+                fa[a] = bit[a] ? xh[a] : 1.0 - xh[a];
+                dfa[a] = bit[a] ? 1.0 : -1.0;
+              }
+              const double Nv = fa[0] * fa[1] * fa[2];
+              const double dN[3] = {dfa[0] * fa[1] * fa[2], fa[0] * dfa[1] * fa[2], fa[0] * fa[1] * dfa[2]};
+              for (int i = 0; i < 3; ++i) {
+                x[i] += Nv * X[3 * vv + i];
+                for (int j = 0; j < 3; ++j) DF[3 * i + j] += X[3 * vv + i] * dN[j];
+              }
+            }
+            for (int tq = 0; tq < nt; ++tq) {
+              const int64_t k = (((int64_t)(fi - f0) * nt + tq) * nq + u) * nq + v;
+              xtp[4 * k] = x[0];
+              xtp[4 * k + 1] = x[1];
+              xtp[4 * k + 2] = x[2];
+              xtp[4 * k + 3] = t0 + dt * xt[tq];
+            }
+          }
+      }
+      c->gfn(c->guser, np, xtp.data(), gv.data());
+      for (size_t fi = f0; fi < f1; ++fi) {
+        const int64_t e = faces[fi] / 6;
+        const int f = (int)(faces[fi] % 6), d = f / 2, sd = f % 2;
+        const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+        const double sgn = sd ? 1.0 : -1.0;  // n^ = sgn e_d
+        const double* Lside = sd ? L1.data() : L0.data();
+        for (int tq = 0; tq < nt; ++tq)
+          for (int u = 0; u < nq; ++u)
+            for (int v = 0; v < nq; ++v) {
+              const int64_t k = (((int64_t)(fi - f0) * nt + tq) * nq + u) * nq + v;
+              const double* DF = &DFs[(((fi - f0) * nq + u) * nq + v) * 9];
+              const double* g = &gv[3 * k];
+              double gh[3];
+              for (int cc = 0; cc < 3; ++cc) gh[cc] = DF[0 * 3 + cc] * g[0] + DF[1 * 3 + cc] * g[1] + DF[2 * 3 + cc] * g[2];
+              double ng[3];  // n^ x g^
+              const double nv[3] = {d == 0 ? sgn : 0.0, d == 1 ? sgn : 0.0, d == 2 ? sgn : 0.0};
+              ng[0] = nv[1] * gh[2] - nv[2] * gh[1];
+              ng[1] = nv[2] * gh[0] - nv[0] * gh[2];
+              ng[2] = nv[0] * gh[1] - nv[1] * gh[0];
+              const double w = dt * wt[tq] * wq[u] * wq[v];
+              for (int cc = 0; cc < 3; ++cc) {
+                if (ng[cc] == 0.0) continue;
+                for (int i = 0; i < Q; ++i) {
+                  const double wi = -w * Lt[tq * kMaxQ + i] * ng[cc];
+                  double* row = &hb[((e * 2 + 1) * 3 + cc) * (int64_t)Q * N3 + (int64_t)i * N3];
+                  for (int al = 0; al < N; ++al)
+                    for (int j1 = 0; j1 < N; ++j1)
+                      for (int j2 = 0; j2 < N; ++j2) {
+                        int idx[3];
+                        idx[d] = al;
+                        idx[a1] = j1;
+                        idx[a2] = j2;
+                        row[(idx[2] * N + idx[1]) * N + idx[0]] +=
+                            wi * Lside[al] * Lq[u * N + j1] * Lq[v * N + j2];
+                      }
+                }
+              }
+            }
+      }
+    }
+    STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+  } else {
+    STM_CK(cudaMemsetAsync(c->load64, 0, n * sizeof(double), c->stream));
+  }
+  if (!c->srcs.empty()) {
+    GaussParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.n_src = (int)c->srcs.size();
+    gp.Q = Q;
+    for (int g = 0; g < nq; ++g) {
+      gp.xq[g] = xq[g];
+      gp.wq[g] = wq[g];
+      for (int j = 0; j < N; ++j) gp.Lq[j][g] = Lq[g * N + j];
+    }
+    for (int k = 0; k < gp.n_src; ++k) {
+      const stm_gauss_src& sr = c->srcs[k];
+      for (int i = 0; i < 3; ++i) {
+        gp.c[k][i] = sr.centre[i];
+        gp.d[k][i] = sr.dir[i];
+      }
+      gp.inv2sx2[k] = 1.0 / (2.0 * sr.sigma_x * sr.sigma_x);
+      gp.amp[k] = sr.amp;
+      for (int i = 0; i < Q; ++i) {
+        double acc = 0.0;
+        for (int tq = 0; tq < nt; ++tq) {
+          const double t = t0 + dt * xt[tq] - sr.t0;
+          acc += wt[tq] * Lt[tq * kMaxQ + i] * std::exp(-t * t / (2.0 * sr.sigma_t * sr.sigma_t));
+        }
+        gp.tf[k][i] = dt * acc;
+      }
+    }
+    const int e = launch_load_gauss(P, c->X8, c->ne, gp, c->load64, c->stream);
+    c->launches += 1;
+    if (e) return fail(c, STM_EDEVICE, std::string("load kernel: ") + cudaGetErrorString((cudaError_t)e));
+  }
+  convert<float, double>(c->load32, c->load64, n, c->stream);
+  c->launches += 1;
+  c->load_valid = true;
+  c->load_t0 = t0;
+  c->load_dt = dt;
+  *out = c->load64;
+  return STM_OK;
 }
 
 __global__ void k_init_guess(double* x, const double* state, int64_t q, int64_t n3, int64_t n) {
@@ -361,7 +573,10 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double 
   int k = 0, rc;
   for (int j = 0; j < m && *iters < max_iters; ++j) {
     S* W = V + (size_t)(j + 1) * n;
-    precond_apply<S>(z, V + (size_t)j * n, inv_ptr<S>(c), qn3, n, c->stream);
+    if (c->geometry == STM_GEOM_TRILINEAR)
+      precond_curved<S, S>(z, V + (size_t)j * n, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream);
+    else
+      precond_apply<S>(z, V + (size_t)j * n, inv_ptr<S>(c), qn3, n, c->stream);
     c->launches += 1;
     if ((rc = linop<S>(c, dt, z, W))) return rc;
     multidot<S>(W, V, n, j + 1, true, n, c->red_partial, c->red_out, c->stream);
@@ -465,8 +680,9 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     if (m->p[e] != c->P || m->q[e] != c->Q)
       return bad(STM_EUNSUPPORTED, "elements of different (p, q) are not handled by this build");
   if (c->P > 7) return bad(STM_EINVAL, "p must be 0..7");
-  if (c->Q < 1 || c->Q > 4) return bad(STM_EINVAL, "q must be 1..4");
-  if (m->geometry != STM_GEOM_BRICK) return bad(STM_EUNSUPPORTED, "only axis-aligned brick elements are handled");
+  if (c->Q < 1 || c->Q > kMaxQ) return bad(STM_EINVAL, "q must be 1..6");
+  if (m->geometry != STM_GEOM_BRICK && m->geometry != STM_GEOM_TRILINEAR) return bad(STM_EINVAL, "unknown geometry");
+  const bool curved = m->geometry == STM_GEOM_TRILINEAR;
   c->geometry = m->geometry;
   c->N = c->P + 1;
   c->N2 = c->N * c->N;
@@ -486,30 +702,41 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   }
   if (c->opts.restart < 1 || c->opts.restart > kMaxDots - 1)
     return bad(STM_EINVAL, "restart must be 1..15");
-  // element geometry: axis-aligned boxes
+  // element geometry: vertices of every element; bricks must be axis-aligned boxes
   c->h_x0.resize(3 * c->ne);
   c->h_h.resize(3 * c->ne);
   c->h_mass.resize(6 * c->ne);
+  c->h_X8.resize(24 * c->ne);
   for (int64_t e = 0; e < c->ne; ++e) {
     const int64_t* hv = m->hex + 8 * e;
-    for (int v = 0; v < 8; ++v)
+    for (int v = 0; v < 8; ++v) {
       if (hv[v] < 0 || hv[v] >= m->n_vert) return bad(STM_EINVAL, "vertex id out of range");
+      for (int d = 0; d < 3; ++d) c->h_X8[24 * e + 3 * v + d] = m->vert[3 * hv[v] + d];
+    }
+    if (!(m->eps[e] > 0) || !(m->mu[e] > 0)) return bad(STM_EINVAL, "eps and mu must be positive");
     const double* v0 = m->vert + 3 * hv[0];
     const double* v7 = m->vert + 3 * hv[7];
     double h[3];
-    for (int d = 0; d < 3; ++d) {
-      h[d] = v7[d] - v0[d];
-      if (!(h[d] > 0)) return bad(STM_EINVAL, "element with non-positive extent (vertex order)");
+    for (int d = 0; d < 3; ++d) h[d] = v7[d] - v0[d];
+    if (curved) {
+      for (int d = 0; d < 3; ++d) {
+        c->h_x0[3 * e + d] = v0[d];
+        c->h_h[3 * e + d] = h[d];
+        c->h_mass[6 * e + d] = 1.0;
+        c->h_mass[6 * e + 3 + d] = 1.0;
+      }
+      continue;
     }
+    for (int d = 0; d < 3; ++d)
+      if (!(h[d] > 0)) return bad(STM_EINVAL, "element with non-positive extent (vertex order)");
     const double tol = 1e-10 * std::max(h[0], std::max(h[1], h[2]));
     for (int v = 0; v < 8; ++v) {
       const double* x = m->vert + 3 * hv[v];
       const int bit[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
       for (int d = 0; d < 3; ++d)
         if (std::fabs(x[d] - (v0[d] + bit[d] * h[d])) > tol)
-          return bad(STM_EUNSUPPORTED, "element is not an axis-aligned box");
+          return bad(STM_EUNSUPPORTED, "element is not an axis-aligned box (use STM_GEOM_TRILINEAR)");
     }
-    if (!(m->eps[e] > 0) || !(m->mu[e] > 0)) return bad(STM_EINVAL, "eps and mu must be positive");
     const double G[3] = {h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2]};
     for (int d = 0; d < 3; ++d) {
       c->h_x0[3 * e + d] = v0[d];
@@ -526,20 +753,37 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       if (e2 >= 0) {
         const int d = f / 2, s = f % 2;
         if (m->nbr[6 * e2 + (2 * d + 1 - s)] != e) return bad(STM_EINVAL, "neighbour lists are not symmetric");
-        // conforming: the two boxes share the whole face
-        const double tol = 1e-10 * c->h_h[3 * e + d];
-        const double face = c->h_x0[3 * e + d] + (s ? c->h_h[3 * e + d] : 0.0);
-        const double face2 = c->h_x0[3 * e2 + d] + (s ? 0.0 : c->h_h[3 * e2 + d]);
-        bool ok = std::fabs(face - face2) <= tol;
-        for (int t = 0; t < 3; ++t)
-          if (t != d)
-            ok = ok && std::fabs(c->h_x0[3 * e + t] - c->h_x0[3 * e2 + t]) <= tol &&
-                 std::fabs(c->h_h[3 * e + t] - c->h_h[3 * e2 + t]) <= tol;
+        bool ok = true;
+        if (curved) {
+          // conforming, same parametrisation: face (d, s) of e and face (d, 1-s) of e2 have the
+          // same four vertices in the same reference order
+          int k1 = 0;
+          int64_t va[4], vb[4];
+          for (int v = 0; v < 8; ++v) {
+            if (((v >> d) & 1) == s) va[k1++] = m->hex[8 * e + v];
+          }
+          int k2 = 0;
+          for (int v = 0; v < 8; ++v) {
+            if (((v >> d) & 1) == 1 - s) vb[k2++] = m->hex[8 * e2 + v];
+          }
+          for (int k = 0; k < 4; ++k) ok = ok && va[k] == vb[k];
+        } else {
+          // conforming: the two boxes share the whole face
+          const double tol = 1e-10 * c->h_h[3 * e + d];
+          const double face = c->h_x0[3 * e + d] + (s ? c->h_h[3 * e + d] : 0.0);
+          const double face2 = c->h_x0[3 * e2 + d] + (s ? 0.0 : c->h_h[3 * e2 + d]);
+          ok = std::fabs(face - face2) <= tol;
+          for (int t = 0; t < 3; ++t)
+            if (t != d)
+              ok = ok && std::fabs(c->h_x0[3 * e + t] - c->h_x0[3 * e2 + t]) <= tol &&
+                   std::fabs(c->h_h[3 * e + t] - c->h_h[3 * e2 + t]) <= tol;
+        }
         if (!ok) return bad(STM_EUNSUPPORTED, "non-conforming face (hanging nodes) are not handled");
       }
       nb[6 * e + f] = (int32_t)e2;
     }
   }
+  c->h_nbr = nb;
   if (cudaGetDevice(&c->device) != cudaSuccess) return bad(STM_EDEVICE, "no CUDA device");
   // 0 is the CUDA default stream, so work is ordered with a caller that uses it
   c->stream = (cudaStream_t)(intptr_t)c->opts.stream;
@@ -568,9 +812,64 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   cudaMemcpy(c->inv64, i64.data(), i64.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(c->inv32, i32.data(), i32.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemset(c->state, 0, c->n_state * sizeof(double));
-  if (cudaGetLastError() != cudaSuccess) {
+  // vertices (load kernel, curved metric) and, for curved elements, the metric at the Gauss points
+  ok = cudaMalloc(&c->X8, c->h_X8.size() * sizeof(double)) == cudaSuccess;
+  if (ok) cudaMemcpy(c->X8, c->h_X8.data(), c->h_X8.size() * sizeof(double), cudaMemcpyHostToDevice);
+  {
+    std::vector<double> xq, wq;
+    gauss01(c->P + 2, xq, wq);
+    for (int g = 0; g < c->P + 2; ++g) {
+      c->ct.xq[g] = xq[g];
+      c->ct.wq[g] = wq[g];
+      double L[kMaxN];
+      legendre01(c->N, xq[g], L);
+      for (int j = 0; j < c->N; ++j) c->ct.Lq[j][g] = L[j];
+    }
+  }
+  if (ok && curved) {
+    const int64_t nq3 = (int64_t)(c->P + 2) * (c->P + 2) * (c->P + 2);
+    std::vector<float> e32(m->eps, m->eps + c->ne), m32b(m->mu, m->mu + c->ne);
+    int* bad_d = nullptr;
+    ok = cudaMalloc(&c->eps64, c->ne * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->mu64, c->ne * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->eps32, c->ne * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->mu32, c->ne * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->Gw64, c->ne * 6 * nq3 * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->Gw32, c->ne * 6 * nq3 * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->Pinv64, c->ne * 18 * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->Pinv32, c->ne * 18 * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->el, c->ne * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&bad_d, sizeof(int)) == cudaSuccess;
+    if (ok) {
+      cudaMemcpy(c->eps64, m->eps, c->ne * sizeof(double), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->mu64, m->mu, c->ne * sizeof(double), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->eps32, e32.data(), c->ne * sizeof(float), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->mu32, m32b.data(), c->ne * sizeof(float), cudaMemcpyHostToDevice);
+      cudaMemset(bad_d, 0, sizeof(int));
+      launch_metric(c->P, c->X8, c->eps64, c->mu64, c->ne, c->ct, c->Gw64, c->Pinv64, bad_d, 0);
+      convert<float, double>(c->Gw32, c->Gw64, c->ne * 6 * nq3, 0);
+      convert<float, double>(c->Pinv32, c->Pinv64, c->ne * 18, 0);
+      int bad_h = 0;
+      cudaMemcpy(&bad_h, bad_d, sizeof(int), cudaMemcpyDeviceToHost);
+      cudaFree(bad_d);
+      if (bad_h) {
+        stm_destroy(c);
+        fprintf(stderr, "stm_create: an element map has a non-positive Jacobian\n");
+        return STM_EINVAL;
+      }
+    }
+  }
+  if (!ok || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
     stm_destroy(c);
-    return STM_EDEVICE;
+    fprintf(stderr, "stm_create: device setup failed\n");
+    return ok ? STM_EDEVICE : STM_ENOMEM;
+  }
+  if (curved) {  // the diagonal brick factors do not apply
+    cudaFree(c->mass64);
+    cudaFree(c->mass32);
+    c->mass64 = nullptr;
+    c->mass32 = nullptr;
   }
   *out = c;
   return STM_OK;
@@ -581,7 +880,8 @@ int32_t stm_destroy(stm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->nbr,     c->mass64,  c->mass32, c->y64,   c->tr64, c->y32, c->tr32,
                   c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
-                  c->x,       c->V32,     c->z32,    c->inv64, c->inv32};
+                  c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
+                  c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -600,7 +900,6 @@ int32_t stm_sizes(stm_ctx* c, int64_t* n_trial, int64_t* n_test, int64_t* n_stat
 }
 
 int32_t stm_residual_apply(stm_ctx* c, double t0, double dt, const void* U, void* R, int32_t prec, int32_t mem) {
-  (void)t0;
   if (!c || !U || !R) return STM_EINVAL;
   if (!(dt > 0)) return fail(c, STM_EINVAL, "dt must be positive");
   if (prec != STM_FP64 && prec != STM_FP32) return fail(c, STM_EINVAL, "prec must be STM_FP64 or STM_FP32");
@@ -617,13 +916,15 @@ int32_t stm_residual_apply(stm_ctx* c, double t0, double dt, const void* U, void
     Rd = c->tmp_out;
   }
   const int64_t tes = 6LL * (c->Q + 1) * c->N3, tcs = (int64_t)(c->Q + 1) * c->N3;
-  int rc;
+  const double* b = nullptr;
+  int rc = build_load(c, t0, dt, &b);
+  if (rc) return rc;
   if (prec == STM_FP64) {
     const double* u = (const double*)Ud;
-    rc = apply<double>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, nullptr, (double*)Rd);
+    rc = apply<double>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, b, (double*)Rd);
   } else {
     const float* u = (const float*)Ud;
-    rc = apply<float>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, nullptr, (float*)Rd);
+    rc = apply<float>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, b ? c->load32 : nullptr, (float*)Rd);
   }
   if (rc) return rc;
   if (mem == STM_MEM_HOST) {
@@ -656,6 +957,8 @@ int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, 
   // Covariant L2 projection on a brick: u_c[s] = h_c int_K^ phi_s (F_c o F_K) dx^,
   // by the tensor Gauss rule with p+2 points per direction.
   if (!c) return STM_EINVAL;
+  if (c->geometry == STM_GEOM_TRILINEAR)
+    return fail(c, STM_EUNSUPPORTED, "L2 projection on curved elements is not built; use stm_set_state");
   const int nq = c->P + 2, N = c->N, N3 = c->N3;
   std::vector<double> xg, wg;
   gauss01(nq, xg, wg);
@@ -704,6 +1007,18 @@ int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, 
 
 int32_t stm_energy(stm_ctx* c, double* energy) {
   if (!c || !energy) return STM_EINVAL;
+  if (c->geometry == STM_GEOM_TRILINEAR) {
+    const int e = launch_energy_curved(c->P, c->state, c->Gw64, c->eps64, c->mu64, c->ct, c->ne, c->el, c->stream);
+    c->launches += 1;
+    if (e) return fail(c, STM_EDEVICE, "curved energy launch failed");
+    std::vector<double> el(c->ne);
+    STM_CK(cudaMemcpyAsync(el.data(), c->el, c->ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    double sum = 0.0;
+    for (double v : el) sum += v;  // fixed order
+    *energy = sum;
+    return STM_OK;
+  }
   energy_brick(c->state, c->mass64, c->N3, c->n_state, c->red_partial, c->red_out, c->stream);
   c->launches += 2;
   STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -730,9 +1045,12 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   } else if ((rc = ensure_buf<double>(c, &c->V, &c->V_len, (m + 1) * n))) {
     return rc;
   }
+  const double* b = nullptr;
+  if ((rc = build_load(c, c->t, dt, &b))) return rc;
+  const bool curved = c->geometry == STM_GEOM_TRILINEAR;
   // reference: ||R(U^(0))|| with all unknowns zero (R6)
   STM_CK(cudaMemsetAsync(c->x, 0, n * sizeof(double), c->stream));
-  if ((rc = resid64(c, dt, c->x, c->z))) return rc;
+  if ((rc = resid64(c, dt, c->x, b, c->z))) return rc;
   double ref;
   if ((rc = norm2<double>(c, c->z, n, &ref))) return rc;
   ref = std::sqrt(ref);
@@ -745,7 +1063,7 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   for (;;) {
     // true FP64 residual R(u0, x)
     double* R64 = mixed ? c->z : c->V;
-    if ((rc = resid64(c, dt, c->x, R64))) return rc;
+    if ((rc = resid64(c, dt, c->x, b, R64))) return rc;
     double beta2;
     if ((rc = norm2<double>(c, R64, n, &beta2))) return rc;
     const double beta = std::sqrt(beta2);
@@ -759,7 +1077,8 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       // V[0] = R = -r, so v_0 = V[0] / (-beta)
       if ((rc = gmres_cycle<double>(c, dt, c->V, c->z, n, -beta, tol * ref, c->opts.max_it, &k, &yc, &res, &iters)))
         return rc;
-      precond_combine<double, double>(c->x, c->V, n, k, yc, c->inv64, qn3, n, c->stream);
+      if (curved) precond_curved<double, double>(c->x, c->V, n, k, yc.c, c->Pinv64, qn3, c->ne, true, c->stream);
+      else precond_combine<double, double>(c->x, c->V, n, k, yc, c->inv64, qn3, n, c->stream);
     } else {
       // FP32 inner GMRES(m) cycle on A d = r, started from the rounded FP64 residual;
       // the inner target is the outer one or what FP32 can resolve, whichever is larger
@@ -771,7 +1090,8 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       const double tin = std::max(tol * ref, 1e-6 * b32);
       if ((rc = gmres_cycle<float>(c, dt, c->V32, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
         return rc;
-      precond_combine<float, double>(c->x, c->V32, n, k, yc, c->inv32, qn3, n, c->stream);
+      if (curved) precond_curved<float, double>(c->x, c->V32, n, k, yc.c, c->Pinv32, qn3, c->ne, true, c->stream);
+      else precond_combine<float, double>(c->x, c->V32, n, k, yc, c->inv32, qn3, n, c->stream);
     }
     c->launches += 1;
     ++cycles;
@@ -790,6 +1110,23 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
     rep->energy = en;
   }
   return rel <= tol ? STM_OK : STM_ENOTCONV;
+}
+
+int32_t stm_set_source_gauss(stm_ctx* c, const stm_gauss_src* src, int32_t n_src) {
+  if (!c || n_src < 0 || n_src > kMaxSrc || (n_src > 0 && !src)) return STM_EINVAL;
+  for (int k = 0; k < n_src; ++k)
+    if (!(src[k].sigma_x > 0) || !(src[k].sigma_t > 0)) return fail(c, STM_EINVAL, "source widths must be positive");
+  c->srcs.assign(src, src + n_src);
+  c->load_valid = false;
+  return STM_OK;
+}
+
+int32_t stm_set_boundary(stm_ctx* c, stm_st_field_fn g, void* user) {
+  if (!c) return STM_EINVAL;
+  c->gfn = g;
+  c->guser = user;
+  c->load_valid = false;
+  return STM_OK;
 }
 
 int32_t stm_launch_count(stm_ctx* c, int64_t* n) {

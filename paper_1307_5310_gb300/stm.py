@@ -39,6 +39,7 @@ EXPORTS = (
     "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply",
     "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
+    "stm_set_source_gauss", "stm_set_boundary",
 )
 
 
@@ -62,7 +63,13 @@ class stm_solve_report(C.Structure):
                 ("energy", C.c_double)]
 
 
+class stm_gauss_src(C.Structure):
+    _fields_ = [("centre", C.c_double * 3), ("dir", C.c_double * 3), ("sigma_x", C.c_double), ("t0", C.c_double),
+                ("sigma_t", C.c_double), ("amp", C.c_double)]
+
+
 FIELD_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double))
+ST_FIELD_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double))
 
 _lib = None
 
@@ -90,6 +97,8 @@ def lib() -> C.CDLL:
         L.stm_profile_enable.argtypes = [vp, i32]
         L.stm_profile_read.argtypes = [vp, C.POINTER(d), C.POINTER(i64)]
         L.stm_residual_apply_noalloc.argtypes = [i64, i32, i32, d, vp, vp, vp, vp, vp, vp, i64]
+        L.stm_set_source_gauss.argtypes = [vp, C.POINTER(stm_gauss_src), i32]
+        L.stm_set_boundary.argtypes = [vp, ST_FIELD_FN, vp]
         for name in EXPORTS:
             if name != "stm_last_error":
                 getattr(L, name).restype = C.c_int32
@@ -249,3 +258,26 @@ class Slab:
         self._check(lib().stm_profile_read(self.ctx, ms, cnt))
         names = ("k_prep_fp64", "k_apply_fp64", "k_prep_fp32", "k_apply_fp32")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(names)}
+
+    def set_source_gauss(self, sources):
+        """sources: list of dicts with centre, dir, sigma_x, t0, sigma_t, amp (at most 8)."""
+        arr = (stm_gauss_src * max(1, len(sources)))()
+        for k, sd in enumerate(sources):
+            arr[k].centre[:] = list(sd["centre"])
+            arr[k].dir[:] = list(sd["dir"])
+            arr[k].sigma_x, arr[k].t0 = sd["sigma_x"], sd["t0"]
+            arr[k].sigma_t, arr[k].amp = sd["sigma_t"], sd["amp"]
+        return self._check(lib().stm_set_source_gauss(self.ctx, arr, len(sources)))
+
+    def set_boundary(self, g=None):
+        """g(x [n,3], t [n]) -> [n,3] boundary data of n x E = n x g; None = PEC."""
+        if g is None:
+            self._keep.pop("g", None)
+            return self._check(lib().stm_set_boundary(self.ctx, C.cast(None, ST_FIELD_FN), None))
+
+        def cb(_user, n, xt, out):
+            a = np.ctypeslib.as_array(xt, shape=(n, 4))
+            np.ctypeslib.as_array(out, shape=(n, 3))[:] = g(a[:, :3], a[:, 3])
+        f = ST_FIELD_FN(cb)
+        self._keep["g"] = f
+        return self._check(lib().stm_set_boundary(self.ctx, f, None))

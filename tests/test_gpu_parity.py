@@ -34,6 +34,7 @@ def stm():
 CASES = [
     (2, 2, 2, 1, 1), (3, 2, 2, 2, 2), (2, 2, 3, 3, 3), (2, 2, 2, 4, 4), (3, 1, 1, 0, 1),
     (2, 2, 2, 5, 2), (1, 1, 2, 7, 1), (2, 1, 2, 6, 3), (5, 3, 2, 2, 1), (2, 2, 2, 4, 3),
+    (2, 1, 1, 2, 5), (1, 1, 2, 3, 6),
 ]
 
 
