@@ -1,0 +1,131 @@
+#include "hp.cuh"
+
+namespace stm {
+
+namespace {
+
+__device__ __forceinline__ void degrees(const uint8_t* pq, int64_t e, int& n3, int& q) {
+  const int v = pq[e];
+  const int n = (v & 15) + 1;
+  n3 = n * n * n;
+  q = v >> 4;
+}
+
+template <typename S>
+__global__ void k_precond_hp(S* __restrict__ z, const S* __restrict__ v, const S* __restrict__ inv,
+                             const int64_t* __restrict__ off, const uint8_t* __restrict__ pq, int64_t ne) {
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    int n3, q;
+    degrees(pq, e, n3, q);
+    const int blk = q * n3;
+    const int64_t o = off[e];
+    for (int it = threadIdx.x; it < 6 * blk; it += blockDim.x) z[o + it] = v[o + it] * inv[e * 6 + it / blk];
+  }
+}
+
+template <typename S, typename X>
+__global__ void k_combine_hp(X* __restrict__ x, const S* __restrict__ V, int64_t ldv, int k, Coef16 y,
+                             const S* __restrict__ inv, const int64_t* __restrict__ off,
+                             const uint8_t* __restrict__ pq, int64_t ne) {
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    int n3, q;
+    degrees(pq, e, n3, q);
+    const int blk = q * n3;
+    const int64_t o = off[e];
+    for (int it = threadIdx.x; it < 6 * blk; it += blockDim.x) {
+      S acc = S(0);
+      for (int j = 0; j < k; ++j) acc = fma((S)y.c[j], V[j * ldv + o + it], acc);
+      x[o + it] = (X)x[o + it] + (X)(acc * inv[e * 6 + it / blk]);
+    }
+  }
+}
+
+__global__ void k_init_hp(double* __restrict__ x, const double* __restrict__ st, const int64_t* __restrict__ ot,
+                          const int64_t* __restrict__ os, const uint8_t* __restrict__ pq, int64_t ne) {
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    int n3, q;
+    degrees(pq, e, n3, q);
+    for (int it = threadIdx.x; it < 6 * q * n3; it += blockDim.x) {
+      const int fc = it / (q * n3), r = it - fc * q * n3, i = r / n3, s = r - i * n3;
+      x[ot[e] + it] = (i == 0) ? st[os[e] + fc * n3 + s] : 0.0;
+    }
+  }
+}
+
+__global__ void k_extract_hp(double* __restrict__ st, const double* __restrict__ x, const int64_t* __restrict__ ot,
+                             const int64_t* __restrict__ os, const uint8_t* __restrict__ pq, int64_t ne) {
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    int n3, q;
+    degrees(pq, e, n3, q);
+    for (int it = threadIdx.x; it < 6 * n3; it += blockDim.x) {
+      const int fc = it / n3, s = it - fc * n3;
+      st[os[e] + it] = x[ot[e] + fc * q * n3 + s];
+    }
+  }
+}
+
+__global__ void k_energy_hp(const double* __restrict__ u, const double* __restrict__ mass,
+                            const int64_t* __restrict__ os, const uint8_t* __restrict__ pq, int64_t ne,
+                            double* __restrict__ el) {
+  __shared__ double red[32];
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    int n3, q;
+    degrees(pq, e, n3, q);
+    double acc = 0.0;
+    for (int it = threadIdx.x; it < 6 * n3; it += blockDim.x) {
+      const double v = u[os[e] + it];
+      acc = fma(mass[e * 6 + it / n3] * v, v, acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+      el[e] = 0.5 * sum;
+    }
+    __syncthreads();
+  }
+}
+
+inline int egrid(int64_t ne) { return (int)(ne < 65536 ? ne : 65536); }
+
+}  // namespace
+
+template <typename S>
+void precond_hp(S* z, const S* v, const S* inv, const int64_t* off_test, const uint8_t* pq, int64_t ne,
+                cudaStream_t s) {
+  k_precond_hp<S><<<egrid(ne), 256, 0, s>>>(z, v, inv, off_test, pq, ne);
+}
+
+template <typename S, typename X>
+void combine_hp(X* x, const S* V, int64_t ldv, int k, const Coef16& y, const S* inv, const int64_t* off_test,
+                const uint8_t* pq, int64_t ne, cudaStream_t s) {
+  k_combine_hp<S, X><<<egrid(ne), 256, 0, s>>>(x, V, ldv, k, y, inv, off_test, pq, ne);
+}
+
+void init_guess_hp(double* x, const double* state, const int64_t* off_test, const int64_t* off_state,
+                   const uint8_t* pq, int64_t ne, cudaStream_t s) {
+  k_init_hp<<<egrid(ne), 256, 0, s>>>(x, state, off_test, off_state, pq, ne);
+}
+
+void extract_end_hp(double* state, const double* x, const int64_t* off_test, const int64_t* off_state,
+                    const uint8_t* pq, int64_t ne, cudaStream_t s) {
+  k_extract_hp<<<egrid(ne), 256, 0, s>>>(state, x, off_test, off_state, pq, ne);
+}
+
+void energy_hp(const double* u, const double* mass, const int64_t* off_state, const uint8_t* pq, int64_t ne,
+               double* el, cudaStream_t s) {
+  k_energy_hp<<<egrid(ne), 256, 0, s>>>(u, mass, off_state, pq, ne, el);
+}
+
+template void precond_hp<double>(double*, const double*, const double*, const int64_t*, const uint8_t*, int64_t,
+                                 cudaStream_t);
+template void precond_hp<float>(float*, const float*, const float*, const int64_t*, const uint8_t*, int64_t,
+                                cudaStream_t);
+template void combine_hp<double, double>(double*, const double*, int64_t, int, const Coef16&, const double*,
+                                         const int64_t*, const uint8_t*, int64_t, cudaStream_t);
+template void combine_hp<float, double>(double*, const float*, int64_t, int, const Coef16&, const float*,
+                                        const int64_t*, const uint8_t*, int64_t, cudaStream_t);
+
+}  // namespace stm

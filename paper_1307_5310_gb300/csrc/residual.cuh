@@ -63,6 +63,42 @@ struct ApplyArgs {
                           //   holds the mass term (curved elements, written by k_mass_curved)
   int64_t n_elem;
   Tables<T> tb;
+  // uneven (p, q): elements of one class are listed in elist; every per-element
+  // block is found through offset arrays, and neighbours may belong to other classes
+  const int32_t* elist = nullptr;   // [n_elem] element ids of this class (null: uniform mesh)
+  const int64_t* off_um = nullptr;  // um block of element e starts at off_um[e] (+ N3 if um_trial)
+  const int64_t* off_u0 = nullptr;  // u0 block of element e starts at off_u0[e]
+  const int64_t* off_R = nullptr;   // test-layout offsets (R, y, b)
+  const int64_t* off_tr = nullptr;  // trace-buffer offsets
+  const uint8_t* pq = nullptr;      // per element: p | q << 4
+  int um_trial = 0;                 // 1: um is in the trial layout (modes 0..q per component)
+  int u0_state = 0;                 // 1: u0 is a state vector ([f][c][s]); 0: trial layout
+};
+
+// Element-local addressing of one element of class (P, Q).
+template <typename T, int P, int Q, bool HP>
+struct ElemAddr {
+  static constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  int64_t e, um, um_cs, u0, u0_cs, R, tr;
+  __device__ __forceinline__ ElemAddr(const ApplyArgs<T>& A, int64_t blk) {
+    if (HP) {
+      e = A.elist[blk];
+      um = A.off_um[e] + (A.um_trial ? N3 : 0);
+      um_cs = A.um_trial ? (Q + 1) * N3 : Q * N3;
+      u0 = A.u0 ? A.off_u0[e] : 0;
+      u0_cs = A.u0_state ? N3 : (Q + 1) * N3;
+      R = A.off_R[e];
+      tr = A.off_tr[e];
+    } else {
+      e = blk;
+      um = e * A.um_es;
+      um_cs = A.um_cs;
+      u0 = e * A.u0_es;
+      u0_cs = A.u0_cs;
+      R = e * (int64_t)(6 * Q * N3);
+      tr = e * (int64_t)(24 * Q * N2);
+    }
+  }
 };
 
 // Nonzero pattern of B (banded): columns 0,1 meet rows 0,1; column m >= 2 meets rows m-2 and m.
@@ -88,19 +124,20 @@ __device__ __forceinline__ void line_geom(int a, int t, int& base, int& stride) 
   else { base = t; stride = N * N; }
 }
 
-template <typename T, int P, int Q>
+template <typename T, int P, int Q, bool HP>
 __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
-  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
+  for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
+    const ElemAddr<T, P, Q, HP> ad(A, blk);
     for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
       const int fc = it / N3, s = it - fc * N3;
       T u[Q + 1];
-      u[0] = A.u0 ? A.u0[e * A.u0_es + fc * A.u0_cs + s] : T(0);
+      u[0] = A.u0 ? A.u0[ad.u0 + fc * ad.u0_cs + s] : T(0);
 #pragma unroll
-      for (int m = 1; m <= Q; ++m) u[m] = A.um[e * A.um_es + fc * A.um_cs + (m - 1) * N3 + s];
-      T* yg = A.y + (e * 6 + fc) * (int64_t)(Q * N3) + s;
+      for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (m - 1) * N3 + s];
+      T* yg = A.y + ad.R + fc * (int64_t)(Q * N3) + s;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         T acc = T(0);
@@ -136,28 +173,52 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
         if (j & 1) od = fma(A.tb.lv[j], v, od);
         else ev = fma(A.tb.lv[j], v, ev);
       }
-      const int64_t o = ((((e * 2 + f) * 3 + a) * 2 + 0) * 2 + bi) * (int64_t)Q + i;
-      A.tr[o * N2 + t] = ev - od;                 // face x^_a = 0
-      A.tr[(o + 2 * Q) * N2 + t] = ev + od;       // face x^_a = 1
+      const int64_t o = ((((int64_t)f * 3 + a) * 2 + 0) * 2 + bi) * Q + i;
+      A.tr[ad.tr + o * N2 + t] = ev - od;                 // face x^_a = 0
+      A.tr[ad.tr + (o + 2 * Q) * N2 + t] = ev + od;       // face x^_a = 1
     }
     __syncthreads();
   }
 }
 
-template <typename T, int P, int Q>
+// Trace of the neighbour en across face (a, side of the element), component
+// slot bi of field fp, temporal test mode i, at the element's transverse
+// position t (N x N).  With uneven degrees the neighbour's orthonormal face
+// modes are truncated or zero-padded and its temporal modes cut at
+// min(q, q') (the projection onto the common temporal test space of
+// Eq. bilinearform:S).
+template <typename T, int N, int Q, bool HP>
+__device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int nside, int fp, int a, int bi, int i,
+                                       int t) {
+  if (!HP) {
+    constexpr int N2 = N * N;
+    const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * Q + i;
+    return A.tr[en * (int64_t)(24 * Q * N2) + so * N2 + t];
+  }
+  const int pq = A.pq[en];
+  const int Nn = (pq & 15) + 1, qn = pq >> 4;
+  const int slow = t / N, fast = t - slow * N;
+  if (i >= qn || slow >= Nn || fast >= Nn) return T(0);
+  const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qn + i;
+  return A.tr[A.off_tr[en] + so * (Nn * Nn) + slow * Nn + fast];
+}
+
+template <typename T, int P, int Q, bool HP>
 __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [3][Q][N3]: y of the other field
   T* Rs = ys + 3 * Q * N3;                  // [3][Q][N3]: residual rows of this field
-  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
+  for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
+    const ElemAddr<T, P, Q, HP> ad(A, blk);
+    const int64_t e = ad.e;
     const int32_t* nb = A.nbr + e * 6;
 #pragma unroll 1
     for (int f = 0; f < 2; ++f) {
       const int fp = 1 - f;
-      const T* yg = A.y + (e * 2 + fp) * (int64_t)(3 * Q * N3);
-      T* Rg = A.R + (e * 2 + f) * (int64_t)(3 * Q * N3);
-      const T* bg = A.b ? A.b + (e * 2 + f) * (int64_t)(3 * Q * N3) : nullptr;
+      const T* yg = A.y + ad.R + fp * (int64_t)(3 * Q * N3);
+      T* Rg = A.R + ad.R + f * (int64_t)(3 * Q * N3);
+      const T* bg = A.b ? A.b + ad.R + f * (int64_t)(3 * Q * N3) : nullptr;
       for (int it = threadIdx.x; it < 3 * Q * N3; it += blockDim.x) {
         ys[it] = yg[it];
         const int cc = it / (Q * N3);
@@ -167,8 +228,8 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         T v;
         if (A.mass) {
           const T mc = A.mass[e * 6 + fc];
-          v = mc * A.um[e * A.um_es + fc * A.um_cs + i * N3 + s];
-          if (i == 0 && A.u0) v = fma(-mc, A.u0[e * A.u0_es + fc * A.u0_cs + s], v);
+          v = mc * A.um[ad.um + fc * ad.um_cs + i * N3 + s];
+          if (i == 0 && A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
         } else {
           v = Rg[it];
         }
@@ -195,15 +256,14 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           const T* yl = ys + (b * Q + i) * N3 + base;
           // jumps of the tangential component b of field fp on the faces normal to a
           const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * Q + i;  // side-0 slot within an element
-          constexpr int64_t per_el = 2 * 3 * 2 * 2 * (int64_t)Q * N2;
-          const T* tre = A.tr + e * per_el;
+          const T* tre = A.tr + ad.tr;
           const T xm = tre[so * N2 + t];
           const T xp = tre[(so + 2 * Q) * N2 + t];
           const int ep = nb[2 * a + 1], em = nb[2 * a];
           T jp, jm;
-          if (ep >= 0) jp = xp - A.tr[ep * per_el + so * N2 + t];
+          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP>(A, ep, 0, fp, a, bi, i, t);
           else jp = (fp == 0) ? xp + xp : T(0);
-          if (em >= 0) jm = xm - A.tr[em * per_el + (so + 2 * Q) * N2 + t];
+          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP>(A, em, 1, fp, a, bi, i, t);
           else jm = (fp == 0) ? xm + xm : T(0);
           const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
           T yv[N];
@@ -374,7 +434,8 @@ struct LaunchEvents {
 };
 
 template <typename T, int P, int Q>
-int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const LaunchEvents& ev) {
+int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const LaunchEvents& ev, int phase = 0,
+                       int block = 256) {
   constexpr int N = P + 1, N3 = N * N * N;
   constexpr int N2 = N * N;
   const size_t sm_prep = sizeof(T) * 6 * Q * N3;
@@ -382,29 +443,42 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   const size_t sm_fused = 2 * sm_prep + sizeof(T) * 24 * Q * N2;
   static bool configured = false;
   if (!configured) {
-    if (sm_prep > 48 * 1024)
-      cudaFuncSetAttribute(k_prep<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
-    if (sm_apply > 48 * 1024)
-      cudaFuncSetAttribute(k_apply<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+    if (sm_prep > 48 * 1024) {
+      cudaFuncSetAttribute(k_prep<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+      cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+    }
+    if (sm_apply > 48 * 1024) {
+      cudaFuncSetAttribute(k_apply<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+      cudaFuncSetAttribute(k_apply<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+    }
     if constexpr (sizeof(T) == 4) {
       if (sm_fused > 48 * 1024)
         cudaFuncSetAttribute(k_fused<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
     }
     configured = true;
   }
+  const bool hp = args.elist != nullptr;
   if constexpr (sizeof(T) == 4) {
-    // single pass: ev.start/ev.stop bracket k_fused (reported in the apply slot)
-    if (ev.start) cudaEventRecord(ev.start, s);
-    if (ev.mid) cudaEventRecord(ev.mid, s);
-    k_fused<T, P, Q><<<grid, 256, sm_fused, s>>>(args);
-    if (ev.stop) cudaEventRecord(ev.stop, s);
-    return (int)cudaGetLastError();
+    if (!hp) {
+      // single pass: ev.start/ev.stop bracket k_fused (reported in the apply slot)
+      if (ev.start) cudaEventRecord(ev.start, s);
+      if (ev.mid) cudaEventRecord(ev.mid, s);
+      k_fused<T, P, Q><<<grid, block, sm_fused, s>>>(args);
+      if (ev.stop) cudaEventRecord(ev.stop, s);
+      return (int)cudaGetLastError();
+    }
   }
-  if (ev.start) cudaEventRecord(ev.start, s);
-  k_prep<T, P, Q><<<grid, 256, sm_prep, s>>>(args);
-  if (ev.mid) cudaEventRecord(ev.mid, s);
-  k_apply<T, P, Q><<<grid, 256, sm_apply, s>>>(args);
-  if (ev.stop) cudaEventRecord(ev.stop, s);
+  if (phase != 2) {
+    if (ev.start) cudaEventRecord(ev.start, s);
+    if (hp) k_prep<T, P, Q, true><<<grid, block, sm_prep, s>>>(args);
+    else k_prep<T, P, Q, false><<<grid, block, sm_prep, s>>>(args);
+    if (ev.mid) cudaEventRecord(ev.mid, s);
+  }
+  if (phase != 1) {
+    if (hp) k_apply<T, P, Q, true><<<grid, block, sm_apply, s>>>(args);
+    else k_apply<T, P, Q, false><<<grid, block, sm_apply, s>>>(args);
+    if (ev.stop) cudaEventRecord(ev.stop, s);
+  }
   return (int)cudaGetLastError();
 }
 

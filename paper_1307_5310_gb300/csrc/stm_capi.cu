@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "curved.cuh"
+#include "hp.cuh"
 #include "krylov.cuh"
 #include "load.cuh"
 #include "residual.cuh"
@@ -22,7 +23,8 @@
 namespace stm {
 #define STM_DECL_P(k)                                                                                  \
   template <typename T>                                                                                \
-  int launch_residual_p##k(int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev);
+  int launch_residual_p##k(int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev, \
+                           int phase, int block);
 STM_DECL_P(0)
 STM_DECL_P(1)
 STM_DECL_P(2)
@@ -33,19 +35,27 @@ STM_DECL_P(6)
 STM_DECL_P(7)
 #undef STM_DECL_P
 
+// phase: 0 = both kernels, 1 = k_prep only, 2 = k_apply only (uneven-degree meshes run
+// every class's k_prep before any k_apply, which reads neighbour traces of other classes)
 template <typename T>
-int launch_residual(int P, int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev) {
+int launch_residual_ph(int P, int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev,
+                       int phase, int block) {
   switch (P) {
-    case 0: return launch_residual_p0<T>(Q, a, s, grid, ev);
-    case 1: return launch_residual_p1<T>(Q, a, s, grid, ev);
-    case 2: return launch_residual_p2<T>(Q, a, s, grid, ev);
-    case 3: return launch_residual_p3<T>(Q, a, s, grid, ev);
-    case 4: return launch_residual_p4<T>(Q, a, s, grid, ev);
-    case 5: return launch_residual_p5<T>(Q, a, s, grid, ev);
-    case 6: return launch_residual_p6<T>(Q, a, s, grid, ev);
-    case 7: return launch_residual_p7<T>(Q, a, s, grid, ev);
+    case 0: return launch_residual_p0<T>(Q, a, s, grid, ev, phase, block);
+    case 1: return launch_residual_p1<T>(Q, a, s, grid, ev, phase, block);
+    case 2: return launch_residual_p2<T>(Q, a, s, grid, ev, phase, block);
+    case 3: return launch_residual_p3<T>(Q, a, s, grid, ev, phase, block);
+    case 4: return launch_residual_p4<T>(Q, a, s, grid, ev, phase, block);
+    case 5: return launch_residual_p5<T>(Q, a, s, grid, ev, phase, block);
+    case 6: return launch_residual_p6<T>(Q, a, s, grid, ev, phase, block);
+    case 7: return launch_residual_p7<T>(Q, a, s, grid, ev, phase, block);
     default: return -1;
   }
+}
+
+template <typename T>
+int launch_residual(int P, int Q, const ApplyArgs<T>& a, cudaStream_t s, int grid, const LaunchEvents& ev) {
+  return launch_residual_ph<T>(P, Q, a, s, grid, ev, 0, 256);
 }
 
 // 1-D tables from their closed forms (Sec. 5.1-5.2): B_im = int L_i l_m with
@@ -179,6 +189,20 @@ struct stm_ctx {
   // geometry: vertices of every element; curved metric
   std::vector<double> h_X8;  // [ne][8][3]
   std::vector<int32_t> h_nbr;  // [ne][6]
+  // uneven (p, q): per-element degrees, block offsets and the (p, q) classes
+  bool hp = false;
+  std::vector<int> h_p, h_q;
+  std::vector<int64_t> h_off_trial, h_off_test, h_off_state, h_off_tr;
+  uint8_t* pq = nullptr;
+  int64_t *off_trial = nullptr, *off_test = nullptr, *off_state = nullptr, *off_tr = nullptr;
+  struct Class {
+    int P, Q;
+    int64_t count;
+    int32_t* elist;
+    int block;
+  };
+  std::vector<Class> classes;
+  int64_t n_tr = 0;
   double* X8 = nullptr;
   double *eps64 = nullptr, *mu64 = nullptr;
   float *eps32 = nullptr, *mu32 = nullptr;
@@ -237,8 +261,8 @@ int ensure(stm_ctx* c, void** p, size_t* have, size_t need) {
 template <typename T>
 int ensure_scratch(stm_ctx* c, T** y, T** tr) {
   if (*y) return STM_OK;
-  const size_t ny = (size_t)c->ne * 6 * c->Q * c->N3;
-  const size_t nt = (size_t)c->ne * 24 * c->Q * c->N2;
+  const size_t ny = (size_t)c->n_test;
+  const size_t nt = (size_t)c->n_tr;
   if (cudaMalloc((void**)y, ny * sizeof(T)) != cudaSuccess || cudaMalloc((void**)tr, nt * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, STM_ENOMEM, "scratch allocation failed");
@@ -284,33 +308,85 @@ int scratch<float>(stm_ctx* c, float** y, float** tr) {
   return rc;
 }
 
-// R = A(um; u0) - b on the context stream.  um holds modes 1..q with element
-// stride um_es and (field, component) stride um_cs; u0 is mode 0 or null.
+enum Layout { L_TRIAL = 0, L_TEST = 1, L_STATE = 2 };
+
 template <typename T>
-int apply(stm_ctx* c, double dt, const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_es,
-          int64_t u0_cs, const T* b, T* R) {
+int record_events(stm_ctx* c, LaunchEvents& ev) {
+  if (!c->profiling) return STM_OK;
+  while (c->ev_pool.size() < c->ev_used + 3) {
+    cudaEvent_t x;
+    if (cudaEventCreate(&x) != cudaSuccess) return fail(c, STM_EDEVICE, "event creation failed");
+    c->ev_pool.push_back(x);
+  }
+  ev.start = c->ev_pool[c->ev_used];
+  ev.mid = c->ev_pool[c->ev_used + 1];
+  ev.stop = c->ev_pool[c->ev_used + 2];
+  c->ev_used += 3;
+  c->timed.push_back({ev.start, ev.mid, ev.stop, sizeof(T) == 8 ? 0 : 1});
+  return STM_OK;
+}
+
+// R = A(um; u0) - b on the context stream.  um holds the unknown modes 1..q, in
+// the trial layout (um_layout = L_TRIAL, mode 0 skipped) or the test layout;
+// u0 is mode 0 (trial layout or a state vector) or null; b is the load or null.
+template <typename T>
+int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R) {
   T *y = nullptr, *tr = nullptr;
-  if constexpr (sizeof(T) == 8) {  // the FP32 kernel is single-pass and needs no scratch
+  if (sizeof(T) == 8 || c->hp) {  // the uniform FP32 kernel is single-pass and needs no scratch
     int rc = scratch<T>(c, &y, &tr);
     if (rc) return rc;
   }
   ApplyArgs<T> a;
-  a.um = um;
-  a.um_es = um_es;
-  a.um_cs = um_cs;
-  a.u0 = u0;
-  a.u0_es = u0_es;
-  a.u0_cs = u0_cs;
   a.b = b;
   a.y = y;
   a.tr = tr;
   a.R = R;
   a.nbr = c->nbr;
   a.mass = mass_ptr<T>(c);
+  const int N3 = c->N3, Q = c->Q;
+  if (c->hp) {
+    a.um = um;
+    a.u0 = u0;
+    a.off_um = um_layout == L_TRIAL ? c->off_trial : c->off_test;
+    a.um_trial = um_layout == L_TRIAL;
+    a.off_u0 = u0_layout == L_STATE ? c->off_state : c->off_trial;
+    a.u0_state = u0_layout == L_STATE;
+    a.off_R = c->off_test;
+    a.off_tr = c->off_tr;
+    a.pq = c->pq;
+    LaunchEvents ev, none;
+    int rc = record_events<T>(c, ev);
+    if (rc) return rc;
+    for (int phase = 1; phase <= 2; ++phase) {
+      for (size_t k = 0; k < c->classes.size(); ++k) {
+        const auto& cl = c->classes[k];
+        a.elist = cl.elist;
+        a.n_elem = cl.count;
+        a.tb = make_tables<T>(cl.P, kMaxQ, dt);
+        LaunchEvents e2 = none;
+        if (phase == 1 && k == 0) e2.start = ev.start;
+        if (phase == 1 && k + 1 == c->classes.size()) e2.mid = ev.mid;
+        if (phase == 2 && k + 1 == c->classes.size()) e2.stop = ev.stop;
+        const int grid = (int)std::min<int64_t>(cl.count, 1 << 30);
+        const int e = launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, e2, phase, cl.block);
+        c->launches += 1;
+        if (e) return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
+      }
+    }
+    return STM_OK;
+  }
+  // uniform mesh: strides
+  a.um = um_layout == L_TRIAL ? um + N3 : um;
+  a.um_es = um_layout == L_TRIAL ? 6LL * (Q + 1) * N3 : 6LL * Q * N3;
+  a.um_cs = um_layout == L_TRIAL ? (int64_t)(Q + 1) * N3 : (int64_t)Q * N3;
+  a.u0 = u0;
+  a.u0_es = u0_layout == L_STATE ? 6LL * N3 : 6LL * (Q + 1) * N3;
+  a.u0_cs = u0_layout == L_STATE ? (int64_t)N3 : (int64_t)(Q + 1) * N3;
   if (c->geometry == STM_GEOM_TRILINEAR) {
     // curved: the metric-dependent mass term goes first into R; the residual kernels add the rest
-    const int em = launch_mass_curved<T>(c->P, c->Q, um, um_es, um_cs, u0, u0_es, u0_cs, curved_ptr<T>(c, 0),
-                                         curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne, R, c->stream);
+    const int em = launch_mass_curved<T>(c->P, c->Q, a.um, a.um_es, a.um_cs, a.u0, a.u0_es, a.u0_cs,
+                                         curved_ptr<T>(c, 0), curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne,
+                                         R, c->stream);
     c->launches += 1;
     if (em) return fail(c, STM_EDEVICE, std::string("curved mass launch: ") + cudaGetErrorString((cudaError_t)em));
     a.mass = nullptr;
@@ -319,18 +395,8 @@ int apply(stm_ctx* c, double dt, const T* um, int64_t um_es, int64_t um_cs, cons
   a.tb = make_tables<T>(c->P, c->Q, dt);
   const int grid = (int)std::min<int64_t>(c->ne, 1 << 30);
   LaunchEvents ev;
-  if (c->profiling) {
-    while (c->ev_pool.size() < c->ev_used + 3) {
-      cudaEvent_t x;
-      if (cudaEventCreate(&x) != cudaSuccess) return fail(c, STM_EDEVICE, "event creation failed");
-      c->ev_pool.push_back(x);
-    }
-    ev.start = c->ev_pool[c->ev_used];
-    ev.mid = c->ev_pool[c->ev_used + 1];
-    ev.stop = c->ev_pool[c->ev_used + 2];
-    c->ev_used += 3;
-    c->timed.push_back({ev.start, ev.mid, ev.stop, sizeof(T) == 8 ? 0 : 1});
-  }
+  int rc = record_events<T>(c, ev);
+  if (rc) return rc;
   c->launches += 2;
   const int e = launch_residual<T>(c->P, c->Q, a, c->stream, grid, ev);
   if (e) return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
@@ -340,14 +406,12 @@ int apply(stm_ctx* c, double dt, const T* um, int64_t um_es, int64_t um_cs, cons
 // Linear operator on the unknowns (Krylov layout, modes 1..q), no u0, no load.
 template <typename T>
 int linop(stm_ctx* c, double dt, const T* xin, T* out) {
-  const int64_t es = 6LL * c->Q * c->N3, cs = (int64_t)c->Q * c->N3;
-  return apply<T>(c, dt, xin, es, cs, nullptr, 0, 0, nullptr, out);
+  return apply<T>(c, dt, xin, L_TEST, nullptr, L_STATE, nullptr, out);
 }
 
 // R(U) = A U - b with mode 0 = state (FP64), modes 1..q = xin and the load b (or none).
 int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* out) {
-  const int64_t es = 6LL * c->Q * c->N3, cs = (int64_t)c->Q * c->N3;
-  return apply<double>(c, dt, xin, es, cs, c->state, 6LL * c->N3, c->N3, b, out);
+  return apply<double>(c, dt, xin, L_TEST, c->state, L_STATE, b, out);
 }
 
 // Load vector b = L on the slab (t0, t0 + dt] (Eq. bilinearform:C): Gaussian
@@ -356,6 +420,7 @@ int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* o
 int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   *out = nullptr;
   if (c->srcs.empty() && !c->gfn) return STM_OK;
+  if (c->hp) return fail(c, STM_EUNSUPPORTED, "sources and boundary data are handled on uniform (p, q) meshes only");
   if (c->load_valid && c->load_t0 == t0 && c->load_dt == dt) {
     *out = c->load64;
     return STM_OK;
@@ -575,6 +640,8 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double 
     S* W = V + (size_t)(j + 1) * n;
     if (c->geometry == STM_GEOM_TRILINEAR)
       precond_curved<S, S>(z, V + (size_t)j * n, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream);
+    else if (c->hp)
+      precond_hp<S>(z, V + (size_t)j * n, inv_ptr<S>(c), c->off_test, c->pq, c->ne, c->stream);
     else
       precond_apply<S>(z, V + (size_t)j * n, inv_ptr<S>(c), qn3, n, c->stream);
     c->launches += 1;
@@ -676,20 +743,41 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   c->ne = m->n_elem;
   c->P = m->p[0];
   c->Q = m->q[0];
-  for (int64_t e = 0; e < c->ne; ++e)
-    if (m->p[e] != c->P || m->q[e] != c->Q)
-      return bad(STM_EUNSUPPORTED, "elements of different (p, q) are not handled by this build");
-  if (c->P > 7) return bad(STM_EINVAL, "p must be 0..7");
-  if (c->Q < 1 || c->Q > kMaxQ) return bad(STM_EINVAL, "q must be 1..6");
+  c->h_p.resize(c->ne);
+  c->h_q.resize(c->ne);
+  for (int64_t e = 0; e < c->ne; ++e) {
+    c->h_p[e] = m->p[e];
+    c->h_q[e] = m->q[e];
+    if (m->p[e] > 7) return bad(STM_EINVAL, "p must be 0..7");
+    if (m->q[e] < 1 || m->q[e] > kMaxQ) return bad(STM_EINVAL, "q must be 1..6");
+    if (m->p[e] != c->P || m->q[e] != c->Q) c->hp = true;
+  }
+  if (c->hp && m->geometry != STM_GEOM_BRICK)
+    return bad(STM_EUNSUPPORTED, "uneven (p, q) is handled on brick meshes only");
   if (m->geometry != STM_GEOM_BRICK && m->geometry != STM_GEOM_TRILINEAR) return bad(STM_EINVAL, "unknown geometry");
   const bool curved = m->geometry == STM_GEOM_TRILINEAR;
   c->geometry = m->geometry;
   c->N = c->P + 1;
   c->N2 = c->N * c->N;
   c->N3 = c->N2 * c->N;
-  c->n_trial = c->ne * 6LL * (c->Q + 1) * c->N3;
-  c->n_test = c->ne * 6LL * c->Q * c->N3;
-  c->n_state = c->ne * 6LL * c->N3;
+  {
+    // per-element block offsets of the trial, test, state and trace layouts
+    c->h_off_trial.assign(c->ne + 1, 0);
+    c->h_off_test.assign(c->ne + 1, 0);
+    c->h_off_state.assign(c->ne + 1, 0);
+    c->h_off_tr.assign(c->ne + 1, 0);
+    for (int64_t e = 0; e < c->ne; ++e) {
+      const int64_t n = c->h_p[e] + 1, n2 = n * n, n3 = n2 * n, q = c->h_q[e];
+      c->h_off_trial[e + 1] = c->h_off_trial[e] + 6 * (q + 1) * n3;
+      c->h_off_test[e + 1] = c->h_off_test[e] + 6 * q * n3;
+      c->h_off_state[e + 1] = c->h_off_state[e] + 6 * n3;
+      c->h_off_tr[e + 1] = c->h_off_tr[e] + 24 * q * n2;
+    }
+  }
+  c->n_trial = c->h_off_trial[c->ne];
+  c->n_test = c->h_off_test[c->ne];
+  c->n_state = c->h_off_state[c->ne];
+  c->n_tr = c->h_off_tr[c->ne];
   if (o) c->opts = *o;
   else {
     c->opts.precision = STM_FP64;
@@ -865,6 +953,41 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     fprintf(stderr, "stm_create: device setup failed\n");
     return ok ? STM_EDEVICE : STM_ENOMEM;
   }
+  if (c->hp) {
+    std::vector<uint8_t> pq(c->ne);
+    for (int64_t e = 0; e < c->ne; ++e) pq[e] = (uint8_t)(c->h_p[e] | (c->h_q[e] << 4));
+    bool okh = cudaMalloc(&c->pq, c->ne) == cudaSuccess &&
+               cudaMalloc(&c->off_trial, (c->ne + 1) * sizeof(int64_t)) == cudaSuccess &&
+               cudaMalloc(&c->off_test, (c->ne + 1) * sizeof(int64_t)) == cudaSuccess &&
+               cudaMalloc(&c->off_state, (c->ne + 1) * sizeof(int64_t)) == cudaSuccess &&
+               cudaMalloc(&c->off_tr, (c->ne + 1) * sizeof(int64_t)) == cudaSuccess &&
+               cudaMalloc(&c->el, c->ne * sizeof(double)) == cudaSuccess;
+    // (p, q) classes, element lists in mesh order
+    std::vector<std::vector<int32_t>> lists(8 * (kMaxQ + 1));
+    for (int64_t e = 0; e < c->ne; ++e) lists[c->h_p[e] * (kMaxQ + 1) + c->h_q[e]].push_back((int32_t)e);
+    for (int pp = 0; pp < 8 && okh; ++pp)
+      for (int qq = 1; qq <= kMaxQ && okh; ++qq) {
+        const auto& L = lists[pp * (kMaxQ + 1) + qq];
+        if (L.empty()) continue;
+        stm_ctx::Class cl{pp, qq, (int64_t)L.size(), nullptr, 256};
+        okh = cudaMalloc(&cl.elist, L.size() * sizeof(int32_t)) == cudaSuccess;
+        if (okh) cudaMemcpy(cl.elist, L.data(), L.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        c->classes.push_back(cl);
+      }
+    if (okh) {
+      cudaMemcpy(c->pq, pq.data(), c->ne, cudaMemcpyHostToDevice);
+      cudaMemcpy(c->off_trial, c->h_off_trial.data(), (c->ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->off_test, c->h_off_test.data(), (c->ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->off_state, c->h_off_state.data(), (c->ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+      cudaMemcpy(c->off_tr, c->h_off_tr.data(), (c->ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    }
+    if (!okh || cudaGetLastError() != cudaSuccess) {
+      cudaGetLastError();
+      stm_destroy(c);
+      fprintf(stderr, "stm_create: device setup of the (p, q) classes failed\n");
+      return STM_ENOMEM;
+    }
+  }
   if (curved) {  // the diagonal brick factors do not apply
     cudaFree(c->mass64);
     cudaFree(c->mass32);
@@ -885,6 +1008,11 @@ int32_t stm_destroy(stm_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  void* hp_ptrs[] = {c->pq, c->off_trial, c->off_test, c->off_state, c->off_tr};
+  for (void* p : hp_ptrs)
+    if (p) cudaFree(p);
+  for (auto& k : c->classes)
+    if (k.elist) cudaFree(k.elist);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -915,16 +1043,15 @@ int32_t stm_residual_apply(stm_ctx* c, double t0, double dt, const void* U, void
     Ud = c->tmp_in;
     Rd = c->tmp_out;
   }
-  const int64_t tes = 6LL * (c->Q + 1) * c->N3, tcs = (int64_t)(c->Q + 1) * c->N3;
   const double* b = nullptr;
   int rc = build_load(c, t0, dt, &b);
   if (rc) return rc;
   if (prec == STM_FP64) {
     const double* u = (const double*)Ud;
-    rc = apply<double>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, b, (double*)Rd);
+    rc = apply<double>(c, dt, u, L_TRIAL, u, L_TRIAL, b, (double*)Rd);
   } else {
     const float* u = (const float*)Ud;
-    rc = apply<float>(c, dt, u + c->N3, tes, tcs, u, tes, tcs, b ? c->load32 : nullptr, (float*)Rd);
+    rc = apply<float>(c, dt, u, L_TRIAL, u, L_TRIAL, b ? c->load32 : nullptr, (float*)Rd);
   }
   if (rc) return rc;
   if (mem == STM_MEM_HOST) {
@@ -955,62 +1082,82 @@ int32_t stm_get_state(stm_ctx* c, double* t, void* u, int32_t mem) {
 
 int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, void* user) {
   // Covariant L2 projection on a brick: u_c[s] = h_c int_K^ phi_s (F_c o F_K) dx^,
-  // by the tensor Gauss rule with p+2 points per direction.
+  // by the tensor Gauss rule with p+2 points per direction (per element degree).
   if (!c) return STM_EINVAL;
   if (c->geometry == STM_GEOM_TRILINEAR)
     return fail(c, STM_EUNSUPPORTED, "L2 projection on curved elements is not built; use stm_set_state");
-  const int nq = c->P + 2, N = c->N, N3 = c->N3;
-  std::vector<double> xg, wg;
-  gauss01(nq, xg, wg);
-  std::vector<double> Lg(nq * N);
-  for (int g = 0; g < nq; ++g) legendre01(N, xg[g], &Lg[g * N]);
-  const int64_t npe = (int64_t)nq * nq * nq;
-  const int64_t chunk = std::max<int64_t>(1, (1 << 20) / npe);
+  std::vector<std::vector<double>> xg(9), wg(9), Lg(9);
+  for (int P = 0; P <= 7; ++P) {
+    const int nq = P + 2, N = P + 1;
+    gauss01(nq, xg[P], wg[P]);
+    Lg[P].resize(nq * N);
+    for (int g = 0; g < nq; ++g) legendre01(N, xg[P][g], &Lg[P][g * N]);
+  }
   std::vector<double> u(c->n_state, 0.0), pts, val;
-  for (int64_t e0 = 0; e0 < c->ne; e0 += chunk) {
-    const int64_t e1 = std::min(c->ne, e0 + chunk);
-    const int64_t np = (e1 - e0) * npe;
+  std::vector<int64_t> pstart;
+  int64_t e0 = 0;
+  while (e0 < c->ne) {
+    // a chunk of elements with about 2^20 quadrature points
+    int64_t e1 = e0, np = 0;
+    pstart.clear();
+    while (e1 < c->ne && (np == 0 || np < (1 << 20))) {
+      const int nq = c->h_p[e1] + 2;
+      pstart.push_back(np);
+      np += (int64_t)nq * nq * nq;
+      ++e1;
+    }
     pts.resize(3 * np);
     val.resize(3 * np);
-    for (int64_t e = e0; e < e1; ++e)
+    for (int64_t e = e0; e < e1; ++e) {
+      const int P = c->h_p[e], nq = P + 2;
       for (int gz = 0; gz < nq; ++gz)
         for (int gy = 0; gy < nq; ++gy)
           for (int gx = 0; gx < nq; ++gx) {
-            const int64_t k = ((e - e0) * npe + (gz * nq + gy) * nq + gx) * 3;
-            pts[k + 0] = c->h_x0[3 * e + 0] + c->h_h[3 * e + 0] * xg[gx];
-            pts[k + 1] = c->h_x0[3 * e + 1] + c->h_h[3 * e + 1] * xg[gy];
-            pts[k + 2] = c->h_x0[3 * e + 2] + c->h_h[3 * e + 2] * xg[gz];
+            const int64_t k = (pstart[e - e0] + (gz * nq + gy) * nq + gx) * 3;
+            pts[k + 0] = c->h_x0[3 * e + 0] + c->h_h[3 * e + 0] * xg[P][gx];
+            pts[k + 1] = c->h_x0[3 * e + 1] + c->h_h[3 * e + 1] * xg[P][gy];
+            pts[k + 2] = c->h_x0[3 * e + 2] + c->h_h[3 * e + 2] * xg[P][gz];
           }
+    }
     for (int f = 0; f < 2; ++f) {
       stm_field_fn fn = f == 0 ? E0 : H0;
       if (!fn) continue;
       fn(user, np, pts.data(), val.data());
-      for (int64_t e = e0; e < e1; ++e)
+      for (int64_t e = e0; e < e1; ++e) {
+        const int P = c->h_p[e], nq = P + 2, N = P + 1, N3 = N * N * N;
+        const double* L = Lg[P].data();
         for (int cc = 0; cc < 3; ++cc) {
-          double* ue = &u[(e * 6 + f * 3 + cc) * N3];
+          double* ue = &u[c->h_off_state[e] + (f * 3 + cc) * N3];
           const double hc = c->h_h[3 * e + cc];
           for (int gz = 0; gz < nq; ++gz)
             for (int gy = 0; gy < nq; ++gy)
               for (int gx = 0; gx < nq; ++gx) {
-                const double v = val[((e - e0) * npe + (gz * nq + gy) * nq + gx) * 3 + cc] * hc * wg[gx] * wg[gy] * wg[gz];
+                const double v = val[(pstart[e - e0] + (gz * nq + gy) * nq + gx) * 3 + cc] * hc * wg[P][gx] *
+                                 wg[P][gy] * wg[P][gz];
                 for (int l = 0; l < N; ++l)
                   for (int k = 0; k < N; ++k) {
-                    const double lk = Lg[gz * N + l] * Lg[gy * N + k] * v;
-                    for (int j = 0; j < N; ++j) ue[(l * N + k) * N + j] += lk * Lg[gx * N + j];
+                    const double lk = L[gz * N + l] * L[gy * N + k] * v;
+                    for (int j = 0; j < N; ++j) ue[(l * N + k) * N + j] += lk * L[gx * N + j];
                   }
               }
         }
+      }
     }
+    e0 = e1;
   }
   return stm_set_state(c, t, u.data(), STM_MEM_HOST);
 }
 
 int32_t stm_energy(stm_ctx* c, double* energy) {
   if (!c || !energy) return STM_EINVAL;
-  if (c->geometry == STM_GEOM_TRILINEAR) {
-    const int e = launch_energy_curved(c->P, c->state, c->Gw64, c->eps64, c->mu64, c->ct, c->ne, c->el, c->stream);
+  if (c->geometry == STM_GEOM_TRILINEAR || c->hp) {
+    if (c->hp) {
+      energy_hp(c->state, c->mass64, c->off_state, c->pq, c->ne, c->el, c->stream);
+    } else {
+      const int e = launch_energy_curved(c->P, c->state, c->Gw64, c->eps64, c->mu64, c->ct, c->ne, c->el, c->stream);
+      if (e) return fail(c, STM_EDEVICE, "curved energy launch failed");
+    }
     c->launches += 1;
-    if (e) return fail(c, STM_EDEVICE, "curved energy launch failed");
     std::vector<double> el(c->ne);
     STM_CK(cudaMemcpyAsync(el.data(), c->el, c->ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
@@ -1055,7 +1202,8 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   if ((rc = norm2<double>(c, c->z, n, &ref))) return rc;
   ref = std::sqrt(ref);
   // initial guess: u_1 = u_0, higher modes 0
-  k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
+  if (c->hp) init_guess_hp(c->x, c->state, c->off_test, c->off_state, c->pq, c->ne, c->stream);
+  else k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
   c->launches += 1;
   int iters = 0, cycles = 0;
   double rel = 0.0;
@@ -1078,6 +1226,7 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       if ((rc = gmres_cycle<double>(c, dt, c->V, c->z, n, -beta, tol * ref, c->opts.max_it, &k, &yc, &res, &iters)))
         return rc;
       if (curved) precond_curved<double, double>(c->x, c->V, n, k, yc.c, c->Pinv64, qn3, c->ne, true, c->stream);
+      else if (c->hp) combine_hp<double, double>(c->x, c->V, n, k, yc, c->inv64, c->off_test, c->pq, c->ne, c->stream);
       else precond_combine<double, double>(c->x, c->V, n, k, yc, c->inv64, qn3, n, c->stream);
     } else {
       // FP32 inner GMRES(m) cycle on A d = r, started from the rounded FP64 residual;
@@ -1091,13 +1240,15 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       if ((rc = gmres_cycle<float>(c, dt, c->V32, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
         return rc;
       if (curved) precond_curved<float, double>(c->x, c->V32, n, k, yc.c, c->Pinv32, qn3, c->ne, true, c->stream);
+      else if (c->hp) combine_hp<float, double>(c->x, c->V32, n, k, yc, c->inv32, c->off_test, c->pq, c->ne, c->stream);
       else precond_combine<float, double>(c->x, c->V32, n, k, yc, c->inv32, qn3, n, c->stream);
     }
     c->launches += 1;
     ++cycles;
     if (k == 0) break;
   }
-  k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);
+  if (c->hp) extract_end_hp(c->state, c->x, c->off_test, c->off_state, c->pq, c->ne, c->stream);
+  else k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);
   c->launches += 1;
   STM_CK(cudaGetLastError());
   c->t += dt;
