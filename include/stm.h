@@ -50,6 +50,7 @@ extern "C" {
 #define STM_ETIMEOUT (-4)     /* a bounded device wait ran out                   */
 #define STM_ENAN (-5)         /* non-finite value detected                       */
 #define STM_EUNSUPPORTED (-6) /* mesh or option outside what this build handles */
+#define STM_ECANCELLED (-7)   /* request cancelled (server destroyed while queued)  */
 #define STM_ENOTCONV 1        /* solver stopped at max_it; best iterate kept     */
 
 #define STM_GEOM_BRICK 0     /* axis-aligned boxes (affine, diagonal DF)          */
@@ -174,6 +175,67 @@ int32_t stm_launch_count(stm_ctx *ctx, int64_t *n);
  * k_prep FP32, k_apply FP32] (arrays of 4). */
 int32_t stm_profile_enable(stm_ctx *ctx, int32_t on);
 int32_t stm_profile_read(stm_ctx *ctx, double *ms, int64_t *count);
+
+/* ---- Request server (continuous batching of slab-solve requests) ----------
+ * The paper solves one problem; serving many is this library's addition.  A
+ * request describes a problem on the unit cube: an n^3 mesh of bricks
+ * (elements numbered with x fastest), degrees p and q, eps/mu of the first
+ * material box containing an element's centre (background 1), Gaussian
+ * current pulses, and either cavity initial data (kind 0: E0 = (0, 0,
+ * sin pi x sin pi y), H0 = 0, the TM_11 mode of Sec. 6.1.1) or a field at
+ * rest (kind 1, driven by the sources); PEC walls.  It asks for n_slabs slab
+ * solves of size dt.  Requests queue FIFO; `workers` threads each admit the
+ * head request when its estimated device footprint fits the remaining
+ * hbm_budget_bytes (a request larger than the budget starts alone), run it on
+ * their own CUDA stream (so admitted requests overlap on the device), keep
+ * its fields and Krylov state on the device, and free it when done.  Results
+ * are identical whether a request runs alone or among others (fixed-order
+ * reductions, independent contexts).  The server is thread-safe. */
+typedef struct stm_server stm_server;
+typedef struct {
+  int32_t workers;          /* concurrent requests (1..64)                          */
+  int64_t hbm_budget_bytes; /* admission budget; <= 0: 80% of free device memory   */
+  int32_t precision;        /* STM_FP64 | STM_MIXED                                 */
+  double tol;               /* relative residual per slab                           */
+  int32_t restart, max_it;
+} stm_server_opts;
+typedef struct {
+  int32_t n, p, q, n_slabs;
+  double dt;
+  int32_t kind;             /* 0 cavity, 1 scattering (zero initial field)          */
+  int32_t n_boxes;          /* material boxes, at most 4                            */
+  double boxes[4][8];       /* lo x,y,z, hi x,y,z, eps, mu                          */
+  int32_t n_src;            /* Gaussian current pulses, at most 8                   */
+  stm_gauss_src src[8];
+} stm_request;
+typedef struct {
+  int32_t status;           /* 0 done, 1 queued, 2 running, ENOTCONV (>0) done with
+                               warning, < 0 failed (others are unaffected)           */
+  int32_t iterations;       /* GMRES iterations over all slabs                      */
+  double energy;            /* discrete energy at the final time                    */
+  double t_final;
+  double latency_ms;        /* submission to completion                             */
+  double queue_ms;          /* submission to admission                              */
+  double max_rel_residual;
+  int64_t n_state;          /* length of the final state                            */
+  int64_t footprint_bytes;  /* device footprint estimated at admission              */
+} stm_result;
+typedef struct {
+  int64_t submitted, completed, failed, running, queued;
+  int64_t peak_admitted_bytes, hbm_budget_bytes;
+  double p50_ms, p99_ms;    /* latency percentiles of completed requests            */
+  double solves_per_s;      /* slab solves completed per second since the first submission */
+  double wall_s;
+} stm_stats;
+int32_t stm_server_create(stm_server **srv, const stm_server_opts *opts);
+int32_t stm_server_submit(stm_server *srv, const stm_request *req, int64_t *ticket);
+/* Current result of a ticket; once done, state_out (host, n_state doubles) may
+ * receive the final state.  stm_server_wait blocks until the ticket is done. */
+int32_t stm_server_poll(stm_server *srv, int64_t ticket, stm_result *res, double *state_out);
+int32_t stm_server_wait(stm_server *srv, int64_t ticket, stm_result *res, double *state_out);
+int32_t stm_server_stats(stm_server *srv, stm_stats *st);
+/* Cancels queued requests, waits for running ones, frees everything. */
+int32_t stm_server_destroy(stm_server *srv);
 
 /* Residual apply that allocates no device memory (the paper has no
  * counterpart; this is a service for callers that cannot call cudaMalloc,

@@ -295,11 +295,11 @@ int mass_pq(const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_e
             const T* eps, const T* mu, const CurvedTables& ct, int64_t ne, T* R, cudaStream_t s) {
   constexpr int NQ3 = (P + 2) * (P + 2) * (P + 2);
   const size_t sm = sizeof(T) * 12 * NQ3;
-  static bool configured = false;
-  if (!configured) {
+  static const bool configured = [&] {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_mass_curved<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   const int grid = (int)(ne < (1 << 30) ? ne : (1 << 30));
   k_mass_curved<T, P, Q><<<grid, 256, sm, s>>>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, ctab<T>(ct), ne, R);
   return (int)cudaGetLastError();

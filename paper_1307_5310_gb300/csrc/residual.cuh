@@ -441,8 +441,8 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   const size_t sm_prep = sizeof(T) * 6 * Q * N3;
   const size_t sm_apply = sm_prep;
   const size_t sm_fused = 2 * sm_prep + sizeof(T) * 24 * Q * N2;
-  static bool configured = false;
-  if (!configured) {
+  // thread-safe one-time set-up (function-local static initialisation)
+  static const bool configured = [&] {
     if (sm_prep > 48 * 1024) {
       cudaFuncSetAttribute(k_prep<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
       cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
@@ -455,8 +455,9 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       if (sm_fused > 48 * 1024)
         cudaFuncSetAttribute(k_fused<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
     }
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   const bool hp = args.elist != nullptr;
   if constexpr (sizeof(T) == 4) {
     if (!hp) {

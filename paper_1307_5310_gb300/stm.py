@@ -40,6 +40,8 @@ EXPORTS = (
     "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
     "stm_set_source_gauss", "stm_set_boundary",
+    "stm_server_create", "stm_server_submit", "stm_server_poll", "stm_server_wait", "stm_server_stats",
+    "stm_server_destroy",
 )
 
 
@@ -66,6 +68,29 @@ class stm_solve_report(C.Structure):
 class stm_gauss_src(C.Structure):
     _fields_ = [("centre", C.c_double * 3), ("dir", C.c_double * 3), ("sigma_x", C.c_double), ("t0", C.c_double),
                 ("sigma_t", C.c_double), ("amp", C.c_double)]
+
+
+class stm_server_opts(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("precision", C.c_int32),
+                ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32)]
+
+
+class stm_request(C.Structure):
+    _fields_ = [("n", C.c_int32), ("p", C.c_int32), ("q", C.c_int32), ("n_slabs", C.c_int32), ("dt", C.c_double),
+                ("kind", C.c_int32), ("n_boxes", C.c_int32), ("boxes", (C.c_double * 8) * 4),
+                ("n_src", C.c_int32), ("src", stm_gauss_src * 8)]
+
+
+class stm_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("energy", C.c_double), ("t_final", C.c_double),
+                ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("max_rel_residual", C.c_double),
+                ("n_state", C.c_int64), ("footprint_bytes", C.c_int64)]
+
+
+class stm_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("running", C.c_int64),
+                ("queued", C.c_int64), ("peak_admitted_bytes", C.c_int64), ("hbm_budget_bytes", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("solves_per_s", C.c_double), ("wall_s", C.c_double)]
 
 
 FIELD_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double))
@@ -99,6 +124,12 @@ def lib() -> C.CDLL:
         L.stm_residual_apply_noalloc.argtypes = [i64, i32, i32, d, vp, vp, vp, vp, vp, vp, i64]
         L.stm_set_source_gauss.argtypes = [vp, C.POINTER(stm_gauss_src), i32]
         L.stm_set_boundary.argtypes = [vp, ST_FIELD_FN, vp]
+        L.stm_server_create.argtypes = [C.POINTER(vp), C.POINTER(stm_server_opts)]
+        L.stm_server_submit.argtypes = [vp, C.POINTER(stm_request), C.POINTER(i64)]
+        L.stm_server_poll.argtypes = [vp, i64, C.POINTER(stm_result), vp]
+        L.stm_server_wait.argtypes = [vp, i64, C.POINTER(stm_result), vp]
+        L.stm_server_stats.argtypes = [vp, C.POINTER(stm_stats)]
+        L.stm_server_destroy.argtypes = [vp]
         for name in EXPORTS:
             if name != "stm_last_error":
                 getattr(L, name).restype = C.c_int32
@@ -281,3 +312,58 @@ class Slab:
         f = ST_FIELD_FN(cb)
         self._keep["g"] = f
         return self._check(lib().stm_set_boundary(self.ctx, f, None))
+
+
+def _result_dict(r):
+    return {k: getattr(r, k) for k, _ in stm_result._fields_}
+
+
+class Server:
+    """Request server of the C ABI (continuous batching of slab-solve requests)."""
+
+    def __init__(self, workers=4, hbm_budget_bytes=0, precision=STM_FP64, tol=1e-9, restart=10, max_it=2000):
+        o = stm_server_opts(workers, hbm_budget_bytes, precision, tol, restart, max_it)
+        h = C.c_void_p()
+        rc = lib().stm_server_create(C.byref(h), C.byref(o))
+        if rc != STM_OK:
+            raise StmError(rc, "stm_server_create failed")
+        self.h = h
+
+    def submit(self, n, p, q, n_slabs, dt, kind=0, boxes=(), sources=()) -> int:
+        r = stm_request()
+        r.n, r.p, r.q, r.n_slabs, r.dt, r.kind = n, p, q, n_slabs, dt, kind
+        r.n_boxes = len(boxes)
+        for k, b in enumerate(boxes):
+            r.boxes[k][:] = list(b)
+        r.n_src = len(sources)
+        for k, sd in enumerate(sources):
+            r.src[k].centre[:] = list(sd["centre"])
+            r.src[k].dir[:] = list(sd["dir"])
+            r.src[k].sigma_x, r.src[k].t0 = sd["sigma_x"], sd["t0"]
+            r.src[k].sigma_t, r.src[k].amp = sd["sigma_t"], sd["amp"]
+        t = C.c_int64()
+        rc = lib().stm_server_submit(self.h, C.byref(r), C.byref(t))
+        if rc != STM_OK:
+            raise StmError(rc, "stm_server_submit failed")
+        return t.value
+
+    def wait(self, ticket, with_state=False):
+        r = stm_result()
+        lib().stm_server_wait(self.h, ticket, C.byref(r), None)
+        state = None
+        if with_state and r.n_state > 0 and r.status >= 0:
+            state = np.empty(r.n_state)
+            lib().stm_server_poll(self.h, ticket, C.byref(r), state.ctypes.data_as(C.c_void_p))
+        return _result_dict(r), state
+
+    def stats(self):
+        st = stm_stats()
+        lib().stm_server_stats(self.h, C.byref(st))
+        return {k: getattr(st, k) for k, _ in stm_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().stm_server_destroy(self.h)
+            self.h = None
+
+    __del__ = close
