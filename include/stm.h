@@ -75,8 +75,15 @@ typedef struct {
   const int64_t *hex;  /* [n_elem][8] vertex ids, vertex v at reference corner
                           (v&1, v>>1&1, v>>2&1)                                   */
   const int64_t *nbr;  /* [n_elem][6] element across face 2d+s (axis d, s = 1 at
-                          x^_d = 1), -1 on the boundary; face 2d+1 of e must meet
-                          face 2d of nbr                                          */
+                          x^_d = 1), -1 on the boundary, -2 on either side of a
+                          2:1 face (see hang); face 2d+1 of e must meet face 2d
+                          of nbr                                                  */
+  int64_t n_hang;      /* rows of hang (0 = conforming mesh)                       */
+  const int64_t *hang; /* [n_hang][6] 2:1 faces of brick meshes: coarse element,
+                          coarse face, fine element, fine face, u, v -- the fine
+                          face is the quarter (u, v) of the coarse face, u along
+                          the lower and v along the higher tangential axis; every
+                          coarse face of this kind has four rows               */
   const uint8_t *p;    /* [n_elem] spatial degree (isotropic), 0..7              */
   const uint8_t *q;    /* [n_elem] temporal degree, 1..6                         */
   const double *eps;   /* [n_elem] permittivity, > 0                             */

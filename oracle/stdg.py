@@ -215,6 +215,7 @@ class Oracle:
         self.eps = np.asarray(mesh["eps"], dtype=np.float64).reshape(self.ne)
         self.mu = np.asarray(mesh["mu"], dtype=np.float64).reshape(self.ne)
         self.nbr = face_neighbours(self.hex)
+        self.pieces = self._face_pieces()
         n3 = (self.p + 1) ** 3
         self.trial_sz = 6 * (self.q + 1) * n3
         self.test_sz = 6 * self.q * n3
@@ -248,6 +249,80 @@ class Oracle:
             self._vol_cache[key] = hit
         return _Pts(hit.xh, geometry.map_points(X8, xh), hit.DF, hit.DFinv, hit.J, hit.phi, hit.gphi)
 
+    # -- face topology -----------------------------------------------------------
+    def _locate(self, x, exclude):
+        """Element (other than ``exclude``) whose closed reference cube contains point x, or -1."""
+        if not hasattr(self, "_bbox"):
+            X = self.vert[self.hex]  # [ne, 8, 3]
+            lo, hi = X.min(axis=1), X.max(axis=1)
+            self._bbox = (lo, hi)
+            # bucket grid with cells as large as the largest element
+            self._h = float(np.max(hi - lo))
+            self._o = lo.min(axis=0)
+            buckets = {}
+            i0 = np.floor((lo - self._o) / self._h).astype(np.int64)
+            i1 = np.floor((hi - self._o) / self._h).astype(np.int64)
+            for e in range(self.ne):
+                for i in range(i0[e, 0], i1[e, 0] + 1):
+                    for j in range(i0[e, 1], i1[e, 1] + 1):
+                        for k in range(i0[e, 2], i1[e, 2] + 1):
+                            buckets.setdefault((i, j, k), []).append(e)
+            self._buckets = {k: np.array(v) for k, v in buckets.items()}
+            self._tol = 1e-9 * max(1.0, float(np.max(np.abs(self.vert))))
+        lo, hi = self._bbox
+        tol = self._tol
+        key = tuple(np.floor((x - self._o) / self._h).astype(np.int64))
+        pool = self._buckets.get(key, np.zeros(0, dtype=np.int64))
+        cand = pool[np.all((x >= lo[pool] - tol) & (x <= hi[pool] + tol), axis=1)]
+        for e2 in cand:
+            if e2 == exclude:
+                continue
+            xh = geometry.inverse_map(self.X8(e2), x[None, :])[0]
+            if np.all(xh > -1e-9) and np.all(xh < 1 + 1e-9):
+                return int(e2)
+        return -1
+
+    def _face_pieces(self):
+        """Per element face: a list of (neighbour or -1, (u0, u1, v0, v1)) pieces.
+
+        The rectangle is a part of the element's reference face in its two
+        tangential coordinates (lower axis first).  Faces matched by shared
+        vertices are one piece; other faces are probed just outside their
+        centre: no element there means boundary, a larger element means this
+        face is a quarter of that element's face (one piece), smaller elements
+        mean four quarter pieces, each with the element found outside its
+        centre.
+        """
+        pieces = [[None] * 6 for _ in range(self.ne)]
+        dN = geometry.shape_grad(np.full((1, 3), 0.5))[0]  # [8, 3]
+        vol = np.abs(np.linalg.det(np.einsum("evi,vj->eij", self.vert[self.hex], dN)))
+        for e in range(self.ne):
+            for f in range(6):
+                if self.nbr[e, f, 0] >= 0:
+                    pieces[e][f] = [(int(self.nbr[e, f, 0]), (0.0, 1.0, 0.0, 1.0))]
+                    continue
+                d, s = divmod(f, 2)
+
+                def probe(u, v):
+                    xh = np.full((1, 3), 0.5)
+                    a1, a2 = [a for a in range(3) if a != d]
+                    xh[0, d] = s
+                    xh[0, a1], xh[0, a2] = u, v
+                    x = geometry.map_points(self.X8(e), xh)[0]
+                    DF = geometry.jacobian(self.X8(e), xh)[0]
+                    out = DF[:, d] * (1.0 if s == 1 else -1.0)
+                    return self._locate(x + 1e-4 * out, e)
+
+                e2 = probe(0.5, 0.5)
+                if e2 < 0:
+                    pieces[e][f] = []
+                elif vol[e2] > 1.5 * vol[e] or vol[e2] > 0.75 * vol[e] and probe(0.25, 0.25) == e2:
+                    pieces[e][f] = [(e2, (0.0, 1.0, 0.0, 1.0))]
+                else:
+                    pieces[e][f] = [(probe(0.25 + 0.5 * u, 0.25 + 0.5 * v), (0.5 * u, 0.5 * u + 0.5, 0.5 * v, 0.5 * v + 0.5))
+                                    for v in (0, 1) for u in (0, 1)]
+        return pieces
+
     # -- volume terms ----------------------------------------------------------
     def _volume(self, e, uE, uH, dt, t0, src):
         """Volume part of R for element e: [B, 2, 3, q, N3]."""
@@ -270,21 +345,26 @@ class Oracle:
         return np.stack([RE, RH], axis=1)
 
     # -- face terms ------------------------------------------------------------
-    def _face(self, e, f, uE, uH, vE, vH, dt, t0, g):
-        """Face (e, f) contribution to the rows of e.
+    def _face(self, e, f, e2, rect, uE, uH, vE, vH, dt, t0, g):
+        """Contribution of one piece of face f of e (neighbour e2 or -1) to the rows of e.
 
         uE/uH: own coefficients [B, 3, q+1, N3]; vE/vH: the neighbour's (or None).
+        rect = (u0, u1, v0, v1): the piece in e's tangential reference coordinates.
         """
         p, q = int(self.p[e]), int(self.q[e])
         d, s = divmod(f, 2)
         X8 = self.X8(e)
-        e2, f2 = self.nbr[e, f]
         interior = e2 >= 0
         p2 = int(self.p[e2]) if interior else p
         q2 = int(self.q[e2]) if interior else q
         nq = max(p, p2) + 2
         xh, wa = _face_grid(d, s, nq)
-        pts = self._pts(e, p, xh, ("face", f, nq))
+        a1_, a2_ = [a for a in range(3) if a != d]
+        u0, u1, v0, v1 = rect
+        xh[:, a1_] = u0 + (u1 - u0) * xh[:, a1_]
+        xh[:, a2_] = v0 + (v1 - v0) * xh[:, a2_]
+        wa = wa * (u1 - u0) * (v1 - v0)
+        pts = self._pts(e, p, xh, ("face", f, nq, rect))
         # surface measure and outward normal from the two tangent vectors
         a1, a2 = [a for a in range(3) if a != d]
         t1, t2 = pts.DF[:, :, a1], pts.DF[:, :, a2]
@@ -302,7 +382,7 @@ class Oracle:
         nn = n[None, None, :, :]
         if interior:
             X8b = self.X8(e2)
-            key = ("inv", f, nq, p2, tuple(np.round(X8b - X8[0], 13).ravel()))
+            key = ("inv", f, nq, p2, rect, tuple(np.round(X8b - X8[0], 13).ravel()))
             xh2 = self._vol_cache.get(key + (tuple(np.round(X8 - X8[0], 13).ravel()),))
             if xh2 is None:
                 xh2 = geometry.inverse_map(X8b, pts.x)
@@ -343,9 +423,9 @@ class Oracle:
     def element_residual(self, e, U, t0, dt, src=None, g=None, parts="all"):
         """R for the test functions of element e, layout [B, 2, 3, q, N3].
 
-        U: [B, N_trial] or [N_trial]; ``parts`` = "all" | "own" | ("nbr", f)
+        U: [B, N_trial] or [N_trial]; ``parts`` = "all" | "own" | ("nbr", e2)
         selects the contribution of element e's own coefficients (volume and
-        own face traces, no load) or of the neighbour across face f.
+        own face traces, no load) or of neighbour element e2's coefficients.
         """
         U = np.atleast_2d(U)
         B = U.shape[0]
@@ -355,19 +435,28 @@ class Oracle:
         if parts in ("all", "own"):
             R += self._volume(e, u[:, 0], u[:, 1], dt, t0, src if parts == "all" else None)
         for f in range(6):
-            e2 = self.nbr[e, f, 0]
-            if parts == "all":
-                own, nb, gg = u, (self.trial_block(U, e2) if e2 >= 0 else None), g
-            elif parts == "own":
-                own, nb, gg = u, None, None
-            else:
-                if parts[1] != f or e2 < 0:
-                    continue
-                own, nb, gg = None, self.trial_block(U, e2), None
-            R += self._face(e, f, None if own is None else own[:, 0], None if own is None else own[:, 1],
-                            None if nb is None else nb[:, 0], None if nb is None else nb[:, 1],
-                            dt, t0, gg)
+            plist = self.pieces[e][f]
+            if not plist:  # boundary face
+                if parts in ("all", "own"):
+                    R += self._face(e, f, -1, (0.0, 1.0, 0.0, 1.0), u[:, 0], u[:, 1], None, None, dt, t0,
+                                    g if parts == "all" else None)
+                continue
+            for e2, rect in plist:
+                if parts == "all":
+                    own, nb = u, self.trial_block(U, e2)
+                elif parts == "own":
+                    own, nb = u, None
+                else:
+                    if parts[1] != e2:
+                        continue
+                    own, nb = None, self.trial_block(U, e2)
+                R += self._face(e, f, e2, rect, None if own is None else own[:, 0], None if own is None else own[:, 1],
+                                None if nb is None else nb[:, 0], None if nb is None else nb[:, 1], dt, t0, None)
         return R
+
+    def neighbours_of(self, e):
+        """Elements that share a face (or a piece of one) with e."""
+        return sorted({e2 for f in range(6) for e2, _ in self.pieces[e][f]})
 
     def residual(self, U, t0, dt, src=None, g=None, elems=None) -> np.ndarray:
         """R_h(U) = B_h(U, .) - L(.) in the test layout (concatenated over ``elems``)."""
@@ -382,7 +471,7 @@ class Oracle:
         b = -self.residual(np.zeros(ntr), t0, dt, src, g)
         for e in range(self.ne):
             r0 = self.test_off[e]
-            blocks = [("own", e)] + [(("nbr", f), self.nbr[e, f, 0]) for f in range(6) if self.nbr[e, f, 0] >= 0]
+            blocks = [("own", e)] + [(("nbr", e2), e2) for e2 in self.neighbours_of(e)]
             for part, e2 in blocks:
                 m = int(self.trial_sz[e2])
                 Ub = np.zeros((m, ntr))

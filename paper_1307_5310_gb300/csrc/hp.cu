@@ -88,6 +88,43 @@ __global__ void k_energy_hp(const double* __restrict__ u, const double* __restri
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_hang(HangArgs<T> H) {
+  for (int64_t slot = blockIdx.x; slot < H.n_slots; slot += gridDim.x) {
+    const int e = H.elem[slot], face = H.face[slot], a = face >> 1;
+    int n3, q;
+    degrees(H.pq, e, n3, q);
+    const int N = (H.pq[e] & 15) + 1, N2 = N * N;
+    const int kind = H.kind[slot];
+    for (int it = threadIdx.x; it < 4 * q * N2; it += blockDim.x) {
+      const int t = it % N2, r = it / N2, i = r % q, fb = r / q;  // fb = field * 2 + comp slot
+      const int fld = fb >> 1, bi = fb & 1;
+      const int js = t / N, jf = t - js * N;
+      T acc = T(0);
+      const int nsrc = kind == 0 ? 1 : 4;
+      for (int k = 0; k < nsrc; ++k) {
+        const int es = H.src[slot * 4 + k], sf = H.src_face[slot * 4 + k];
+        const int qs = H.pq[es] >> 4, Ns = (H.pq[es] & 15) + 1;
+        if (i >= qs) continue;
+        const int u = H.quad[slot * 4 + k] & 1, v = H.quad[slot * 4 + k] >> 1;
+        const T* ts = H.tr + H.off_tr[es] + ((((int64_t)fld * 3 + a) * 2 + (sf & 1)) * 2 + bi) * qs * Ns * Ns +
+                      (int64_t)i * Ns * Ns;
+        for (int ns = 0; ns < Ns; ++ns) {
+          T row = T(0);
+          for (int nf = 0; nf < Ns; ++nf) {
+            // fine side: source modes (ns, nf) are the coarse ones; coarse side: they are fine ones
+            const T tf = kind == 0 ? H.Tm[u][jf][nf] : H.Tm[u][nf][jf];
+            row = fma(tf, ts[ns * Ns + nf], row);
+          }
+          const T tsl = kind == 0 ? H.Tm[v][js][ns] : H.Tm[v][ns][js];
+          acc = fma(tsl, row, acc);
+        }
+      }
+      H.hbuf[H.hoff[slot] + it] = T(0.5) * acc;
+    }
+  }
+}
+
 inline int egrid(int64_t ne) { return (int)(ne < 65536 ? ne : 65536); }
 
 }  // namespace
@@ -118,6 +155,13 @@ void energy_hp(const double* u, const double* mass, const int64_t* off_state, co
                double* el, cudaStream_t s) {
   k_energy_hp<<<egrid(ne), 256, 0, s>>>(u, mass, off_state, pq, ne, el);
 }
+
+template <typename T>
+void launch_hang(const HangArgs<T>& h, cudaStream_t s) {
+  if (h.n_slots > 0) k_hang<T><<<egrid(h.n_slots), 128, 0, s>>>(h);
+}
+template void launch_hang<double>(const HangArgs<double>&, cudaStream_t);
+template void launch_hang<float>(const HangArgs<float>&, cudaStream_t);
 
 template void precond_hp<double>(double*, const double*, const double*, const int64_t*, const uint8_t*, int64_t,
                                  cudaStream_t);

@@ -33,4 +33,32 @@ void extract_end_hp(double* state, const double* x, const int64_t* off_test, con
 void energy_hp(const double* u, const double* mass, const int64_t* off_state, const uint8_t* pq, int64_t ne,
                double* el, cudaStream_t s);
 
+// 2:1 faces.  For each slot (an element face on either side of a 2:1 face)
+// k_hang writes the neighbour's tangential traces as coefficients of the
+// receiving element's own face basis: for a fine face the coarse trace
+// restricted to its quarter (u, v), for a coarse face the four fine traces
+// projected onto the coarse basis, with the transfer integrals
+// T[u][j][n] = int_0^1 L_n((eta + u) / 2) L_j(eta) d eta and the factor 1/2
+// from the covariant scaling and the quarter's area.  Temporal modes stop at
+// min(q, q') (Eq. bilinearform:S).
+template <typename T>
+struct HangArgs {
+  const T* tr;              // trace buffer of all elements
+  const int64_t* off_tr;
+  const uint8_t* pq;
+  int64_t n_slots;
+  const int32_t* elem;      // [slot] receiving element
+  const int32_t* face;      // [slot] receiving face
+  const int32_t* kind;      // [slot] 0: fine side (one coarse source), 1: coarse side (four fine sources)
+  const int32_t* src;       // [slot][4] source elements
+  const int32_t* src_face;  // [slot][4] source faces
+  const int32_t* quad;      // [slot][4] quarter u | v << 1
+  const int64_t* hoff;      // [slot] offset of the slot's output
+  T* hbuf;
+  T Tm[2][8][8];
+};
+
+template <typename T>
+void launch_hang(const HangArgs<T>& h, cudaStream_t s);
+
 }  // namespace stm

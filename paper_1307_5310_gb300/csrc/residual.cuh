@@ -73,6 +73,11 @@ struct ApplyArgs {
   const uint8_t* pq = nullptr;      // per element: p | q << 4
   int um_trial = 0;                 // 1: um is in the trial layout (modes 0..q per component)
   int u0_state = 0;                 // 1: u0 is a state vector ([f][c][s]); 0: trial layout
+  // 2:1 faces: hslot[e*6+f] >= 0 names the slot whose equivalent neighbour traces
+  // (built by k_hang in the receiving element's layout [field][comp][q][N2]) start at hoff[slot]
+  const int32_t* hslot = nullptr;
+  const int64_t* hoff = nullptr;
+  const T* hbuf = nullptr;
 };
 
 // Element-local addressing of one element of class (P, Q).
@@ -262,8 +267,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           const int ep = nb[2 * a + 1], em = nb[2 * a];
           T jp, jm;
           if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP>(A, ep, 0, fp, a, bi, i, t);
+          else if (HP && ep == -2) jp = xp - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a + 1]] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jp = (fp == 0) ? xp + xp : T(0);
           if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP>(A, em, 1, fp, a, bi, i, t);
+          else if (HP && em == -2) jm = xm - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a]] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jm = (fp == 0) ? xm + xm : T(0);
           const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
           T yv[N];

@@ -203,6 +203,14 @@ struct stm_ctx {
   };
   std::vector<Class> classes;
   int64_t n_tr = 0;
+  // 2:1 faces: slots (receiving element faces) and their sources
+  int64_t n_slots = 0, n_hbuf = 0;
+  int32_t *hslot = nullptr, *s_elem = nullptr, *s_face = nullptr, *s_kind = nullptr, *s_src = nullptr,
+          *s_srcface = nullptr, *s_quad = nullptr;
+  int64_t* hoff = nullptr;
+  double* hbuf64 = nullptr;
+  float* hbuf32 = nullptr;
+  double Tm[2][8][8] = {};
   double* X8 = nullptr;
   double *eps64 = nullptr, *mu64 = nullptr;
   float *eps32 = nullptr, *mu32 = nullptr;
@@ -292,6 +300,13 @@ const float* curved_ptr<float>(stm_ctx* c, int which) {
 }
 
 template <typename T>
+const T* hbuf_ptr(stm_ctx* c);
+template <>
+const double* hbuf_ptr<double>(stm_ctx* c) { return c->hbuf64; }
+template <>
+const float* hbuf_ptr<float>(stm_ctx* c) { return c->hbuf32; }
+
+template <typename T>
 int scratch(stm_ctx* c, T** y, T** tr);
 template <>
 int scratch<double>(stm_ctx* c, double** y, double** tr) {
@@ -357,7 +372,31 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
     LaunchEvents ev, none;
     int rc = record_events<T>(c, ev);
     if (rc) return rc;
+    a.hslot = c->hslot;
+    a.hoff = c->hoff;
+    a.hbuf = hbuf_ptr<T>(c);
     for (int phase = 1; phase <= 2; ++phase) {
+      if (phase == 2 && c->n_slots > 0) {
+        // 2:1 faces: equivalent neighbour traces from all classes' traces
+        HangArgs<T> h;
+        h.tr = tr;
+        h.off_tr = c->off_tr;
+        h.pq = c->pq;
+        h.n_slots = c->n_slots;
+        h.elem = c->s_elem;
+        h.face = c->s_face;
+        h.kind = c->s_kind;
+        h.src = c->s_src;
+        h.src_face = c->s_srcface;
+        h.quad = c->s_quad;
+        h.hoff = c->hoff;
+        h.hbuf = const_cast<T*>(hbuf_ptr<T>(c));
+        for (int u = 0; u < 2; ++u)
+          for (int j = 0; j < 8; ++j)
+            for (int nn = 0; nn < 8; ++nn) h.Tm[u][j][nn] = (T)c->Tm[u][j][nn];
+        launch_hang<T>(h, c->stream);
+        c->launches += 1;
+      }
       for (size_t k = 0; k < c->classes.size(); ++k) {
         const auto& cl = c->classes[k];
         a.elist = cl.elist;
@@ -752,8 +791,11 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     if (m->q[e] < 1 || m->q[e] > kMaxQ) return bad(STM_EINVAL, "q must be 1..6");
     if (m->p[e] != c->P || m->q[e] != c->Q) c->hp = true;
   }
+  for (int64_t k = 0; k < 6 * c->ne; ++k)
+    if (m->nbr[k] == -2) c->hp = true;  // 2:1 faces run through the per-element-offset kernels
   if (c->hp && m->geometry != STM_GEOM_BRICK)
-    return bad(STM_EUNSUPPORTED, "uneven (p, q) is handled on brick meshes only");
+    return bad(STM_EUNSUPPORTED, "uneven (p, q) and 2:1 faces are handled on brick meshes only");
+  if (m->n_hang < 0 || (m->n_hang > 0 && !m->hang)) return bad(STM_EINVAL, "bad hang list");
   if (m->geometry != STM_GEOM_BRICK && m->geometry != STM_GEOM_TRILINEAR) return bad(STM_EINVAL, "unknown geometry");
   const bool curved = m->geometry == STM_GEOM_TRILINEAR;
   c->geometry = m->geometry;
@@ -837,7 +879,8 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   for (int64_t e = 0; e < c->ne; ++e) {
     for (int f = 0; f < 6; ++f) {
       const int64_t e2 = m->nbr[6 * e + f];
-      if (e2 < -1 || e2 >= c->ne) return bad(STM_EINVAL, "neighbour id out of range");
+      if (e2 < -2 || e2 >= c->ne) return bad(STM_EINVAL, "neighbour id out of range");
+      if (e2 == -2 && curved) return bad(STM_EUNSUPPORTED, "2:1 faces are handled on brick meshes only");
       if (e2 >= 0) {
         const int d = f / 2, s = f % 2;
         if (m->nbr[6 * e2 + (2 * d + 1 - s)] != e) return bad(STM_EINVAL, "neighbour lists are not symmetric");
@@ -872,6 +915,78 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     }
   }
   c->h_nbr = nb;
+  // 2:1 faces: validate the hang rows and build one slot per receiving element face
+  std::vector<int32_t> hslot(6 * c->ne, -1), s_elem, s_face, s_kind, s_src, s_srcface, s_quad;
+  std::vector<int64_t> hoff;
+  {
+    auto slot_of = [&](int64_t e, int f, int kind) -> int {
+      int32_t& sl = hslot[6 * e + f];
+      if (sl < 0) {
+        sl = (int32_t)s_elem.size();
+        s_elem.push_back((int32_t)e);
+        s_face.push_back(f);
+        s_kind.push_back(kind);
+        for (int k = 0; k < 4; ++k) {
+          s_src.push_back(-1);
+          s_srcface.push_back(-1);
+          s_quad.push_back(-1);
+        }
+      }
+      return s_kind[sl] == kind ? sl : -1;
+    };
+    for (int64_t r = 0; r < m->n_hang; ++r) {
+      const int64_t* H = m->hang + 6 * r;
+      const int64_t eb = H[0], es = H[2];
+      const int fb = (int)H[1], fs = (int)H[3], u = (int)H[4], v = (int)H[5];
+      if (eb < 0 || eb >= c->ne || es < 0 || es >= c->ne || fb < 0 || fb > 5 || fs < 0 || fs > 5 || (u & ~1) ||
+          (v & ~1) || fb / 2 != fs / 2 || fb % 2 == fs % 2 || m->nbr[6 * eb + fb] != -2 || m->nbr[6 * es + fs] != -2)
+        return bad(STM_EINVAL, "inconsistent row in the hang list");
+      const int d = fb / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const double* xb = &c->h_x0[3 * eb];
+      const double* hb = &c->h_h[3 * eb];
+      const double* xs = &c->h_x0[3 * es];
+      const double* hs = &c->h_h[3 * es];
+      const double tol = 1e-9 * hb[t1];
+      const double pb = xb[d] + (fb % 2 ? hb[d] : 0.0), ps = xs[d] + (fs % 2 ? hs[d] : 0.0);
+      if (std::fabs(pb - ps) > tol || std::fabs(2 * hs[t1] - hb[t1]) > tol || std::fabs(2 * hs[t2] - hb[t2]) > tol ||
+          std::fabs(xs[t1] - (xb[t1] + u * hs[t1])) > tol || std::fabs(xs[t2] - (xb[t2] + v * hs[t2])) > tol)
+        return bad(STM_EINVAL, "hang row does not describe a quarter of the coarse face");
+      const int sb = slot_of(eb, fb, 1), ss = slot_of(es, fs, 0);
+      if (sb < 0 || ss < 0) return bad(STM_EINVAL, "a face is both coarse and fine side of 2:1 faces");
+      const int q4 = u | (v << 1);
+      if (s_src[4 * sb + q4] >= 0 || s_src[4 * ss] >= 0) return bad(STM_EINVAL, "duplicate row in the hang list");
+      s_src[4 * sb + q4] = (int32_t)es;
+      s_srcface[4 * sb + q4] = fs;
+      s_quad[4 * sb + q4] = q4;
+      s_src[4 * ss] = (int32_t)eb;
+      s_srcface[4 * ss] = fb;
+      s_quad[4 * ss] = q4;
+    }
+    for (int64_t k = 0; k < 6 * c->ne; ++k)
+      if (m->nbr[k] == -2 && hslot[k] < 0) return bad(STM_EINVAL, "a face marked -2 has no row in the hang list");
+    for (size_t sl = 0; sl < s_elem.size(); ++sl)
+      for (int k = 0; k < (s_kind[sl] ? 4 : 1); ++k)
+        if (s_src[4 * sl + k] < 0) return bad(STM_EINVAL, "a coarse 2:1 face lacks one of its four fine faces");
+    int64_t off = 0;
+    for (size_t sl = 0; sl < s_elem.size(); ++sl) {
+      hoff.push_back(off);
+      const int64_t n = c->h_p[s_elem[sl]] + 1;
+      off += 4LL * c->h_q[s_elem[sl]] * n * n;
+    }
+    c->n_slots = (int64_t)s_elem.size();
+    c->n_hbuf = off;
+    // transfer integrals T[u][j][n] = int_0^1 L_n((eta + u) / 2) L_j(eta) d eta (exact Gauss rule)
+    std::vector<double> xg, wg;
+    gauss01(10, xg, wg);
+    for (int u = 0; u < 2; ++u)
+      for (size_t g = 0; g < xg.size(); ++g) {
+        double Lj[8], Ln[8];
+        legendre01(8, xg[g], Lj);
+        legendre01(8, 0.5 * (xg[g] + u), Ln);
+        for (int j = 0; j < 8; ++j)
+          for (int n = 0; n < 8; ++n) c->Tm[u][j][n] += wg[g] * Ln[n] * Lj[j];
+      }
+  }
   if (cudaGetDevice(&c->device) != cudaSuccess) return bad(STM_EDEVICE, "no CUDA device");
   // 0 is the CUDA default stream, so work is ordered with a caller that uses it
   c->stream = (cudaStream_t)(intptr_t)c->opts.stream;
@@ -974,6 +1089,29 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
         if (okh) cudaMemcpy(cl.elist, L.data(), L.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
         c->classes.push_back(cl);
       }
+    if (okh && c->n_slots > 0) {
+      const size_t ns = (size_t)c->n_slots;
+      okh = cudaMalloc(&c->hslot, 6 * c->ne * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->s_elem, ns * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->s_face, ns * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->s_kind, ns * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->s_src, 4 * ns * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->s_srcface, 4 * ns * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->s_quad, 4 * ns * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c->hoff, ns * sizeof(int64_t)) == cudaSuccess &&
+            cudaMalloc(&c->hbuf64, c->n_hbuf * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->hbuf32, c->n_hbuf * sizeof(float)) == cudaSuccess;
+      if (okh) {
+        cudaMemcpy(c->hslot, hslot.data(), 6 * c->ne * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->s_elem, s_elem.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->s_face, s_face.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->s_kind, s_kind.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->s_src, s_src.data(), 4 * ns * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->s_srcface, s_srcface.data(), 4 * ns * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->s_quad, s_quad.data(), 4 * ns * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->hoff, hoff.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice);
+      }
+    }
     if (okh) {
       cudaMemcpy(c->pq, pq.data(), c->ne, cudaMemcpyHostToDevice);
       cudaMemcpy(c->off_trial, c->h_off_trial.data(), (c->ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -1008,7 +1146,9 @@ int32_t stm_destroy(stm_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
-  void* hp_ptrs[] = {c->pq, c->off_trial, c->off_test, c->off_state, c->off_tr};
+  void* hp_ptrs[] = {c->pq,     c->off_trial, c->off_test, c->off_state, c->off_tr, c->hslot,  c->s_elem,
+                     c->s_face, c->s_kind,    c->s_src,    c->s_srcface, c->s_quad, c->hoff,   c->hbuf64,
+                     c->hbuf32};
   for (void* p : hp_ptrs)
     if (p) cudaFree(p);
   for (auto& k : c->classes)

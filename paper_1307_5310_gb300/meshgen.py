@@ -164,3 +164,124 @@ def random_materials(mesh: dict, seed_eps: int, seed_mu: int, lo=1.0, hi=4.0) ->
     ne = mesh["hex"].shape[0]
     mesh["eps"] = np.random.Generator(np.random.PCG64(seed_eps)).uniform(lo, hi, size=ne)
     mesh["mu"] = np.random.Generator(np.random.PCG64(seed_mu)).uniform(lo, hi, size=ne)
+
+
+def corner_octree_mesh(n0: int, radii, p=1, q=1, order: str = "morton") -> dict:
+    """Unit cube, base grid n0^3, refined towards the corner (0,0,0), 2:1 balanced.
+
+    A cell of level L (edge 1/(n0 2^L)) is split while L < len(radii) and the
+    distance of its corner nearest the origin is below radii[L]; afterwards
+    cells are split until face neighbours differ by at most one level.
+    Conforming faces get nbr >= 0; a face shared by one coarse and four fine
+    cells gets nbr = -2 on both sides and one row per fine cell in ``hang``:
+    (coarse element, coarse face, fine element, fine face, u, v), where u and
+    v (0 or 1) locate the fine face's quarter along the lower and the higher
+    of the two tangential axes.  Elements are numbered along the Z-order curve
+    of their corners at the finest level (``order="morton"``).
+    """
+    L_max_req = len(radii)
+    leaves = {(0, i, j, k) for i in range(n0) for j in range(n0) for k in range(n0)}
+
+    def refine(cell):
+        L, i, j, k = cell
+        leaves.discard(cell)
+        for c in range(8):
+            leaves.add((L + 1, 2 * i + (c & 1), 2 * j + ((c >> 1) & 1), 2 * k + ((c >> 2) & 1)))
+
+    for L in range(L_max_req):
+        h = 1.0 / (n0 * 2 ** L)
+        for cell in [c for c in leaves if c[0] == L]:
+            _, i, j, k = cell
+            if np.sqrt((i * h) ** 2 + (j * h) ** 2 + (k * h) ** 2) < radii[L]:
+                refine(cell)
+
+    def covering(L, c):
+        """The leaf that contains level-L cell position c (at level <= L), or None."""
+        for Lp in range(L, -1, -1):
+            s = L - Lp
+            key = (Lp, c[0] >> s, c[1] >> s, c[2] >> s)
+            if key in leaves:
+                return key
+        return None
+
+    changed = True
+    while changed:
+        changed = False
+        for cell in sorted(leaves, key=lambda c: -c[0]):
+            if cell not in leaves:
+                continue
+            L, i, j, k = cell
+            nL = n0 * 2 ** L
+            for d in range(3):
+                for s in (-1, 1):
+                    c = [i, j, k]
+                    c[d] += s
+                    if c[d] < 0 or c[d] >= nL:
+                        continue
+                    cov = covering(L, c)
+                    if cov is not None and cov[0] < L - 1:
+                        refine(cov)
+                        changed = True
+
+    Lmax = max(c[0] for c in leaves)
+    scale = 2 ** Lmax
+    cells = sorted(leaves)
+    ii = np.array([c[1] << (Lmax - c[0]) for c in cells])
+    jj = np.array([c[2] << (Lmax - c[0]) for c in cells])
+    kk = np.array([c[3] << (Lmax - c[0]) for c in cells])
+    perm = morton_order(ii, jj, kk) if order == "morton" else np.arange(len(cells))
+    cells = [cells[t] for t in perm]
+    index = {c: e for e, c in enumerate(cells)}
+    ne = len(cells)
+    nfine = n0 * scale
+    vid = {}
+    vert = []
+    hexes = np.empty((ne, 8), dtype=np.int64)
+    for e, (L, i, j, k) in enumerate(cells):
+        f = 2 ** (Lmax - L)
+        for v in range(8):
+            key = ((i + (v & 1)) * f, (j + ((v >> 1) & 1)) * f, (k + ((v >> 2) & 1)) * f)
+            if key not in vid:
+                vid[key] = len(vert)
+                vert.append(key)
+            hexes[e, v] = vid[key]
+    vert = np.array(vert, dtype=np.float64) / nfine
+    nbr = np.full((ne, 6), -1, dtype=np.int64)
+    hang = []
+    for e, (L, i, j, k) in enumerate(cells):
+        nL = n0 * 2 ** L
+        for d in range(3):
+            for s in (0, 1):
+                c = [i, j, k]
+                c[d] += 1 if s else -1
+                if c[d] < 0 or c[d] >= nL:
+                    continue
+                key = (L,) + tuple(c)
+                if key in index:
+                    nbr[e, 2 * d + s] = index[key]
+                    continue
+                par = (L - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1)
+                if L > 0 and par in index:
+                    # this (fine) face is a quarter of the coarse neighbour's face
+                    nbr[e, 2 * d + s] = -2
+                    t1, t2 = [a for a in range(3) if a != d]
+                    hang.append((index[par], 2 * d + (1 - s), e, 2 * d + s, c[t1] & 1, c[t2] & 1))
+                else:
+                    nbr[e, 2 * d + s] = -2  # coarse side: four finer neighbours
+    hang = np.array(hang, dtype=np.int64).reshape(-1, 6)
+    return {
+        "vert": vert, "hex": hexes, "nbr": nbr, "hang": hang,
+        "p": np.full(ne, p, dtype=np.uint8), "q": np.full(ne, q, dtype=np.uint8),
+        "eps": np.ones(ne), "mu": np.ones(ne), "geometry": "brick",
+        "level": np.array([c[0] for c in cells], dtype=np.int64),
+    }
+
+
+def random_hp(mesh: dict, seed: int, p_range=(1, 7), q_range=(1, 4), eps_values=(1.0, 2.25, 4.0)) -> None:
+    """Per-element p ~ U{p_range}, q ~ U{q_range}, eps ~ U{eps_values}, mu = 1 (PCG64 seed)."""
+    ne = mesh["hex"].shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mesh["p"] = rng.integers(p_range[0], p_range[1] + 1, ne).astype(np.uint8)
+    mesh["q"] = rng.integers(q_range[0], q_range[1] + 1, ne).astype(np.uint8)
+    mesh["eps"] = np.asarray(eps_values, dtype=np.float64)[rng.integers(0, len(eps_values), ne)]
+    mesh["mu"] = np.ones(ne)

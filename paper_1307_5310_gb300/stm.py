@@ -49,6 +49,7 @@ class stm_mesh(C.Structure):
     _fields_ = [
         ("n_elem", C.c_int64), ("n_vert", C.c_int64),
         ("vert", C.POINTER(C.c_double)), ("hex", C.POINTER(C.c_int64)), ("nbr", C.POINTER(C.c_int64)),
+        ("n_hang", C.c_int64), ("hang", C.POINTER(C.c_int64)),
         ("p", C.POINTER(C.c_uint8)), ("q", C.POINTER(C.c_uint8)),
         ("eps", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
         ("geometry", C.c_int32),
@@ -195,12 +196,15 @@ class Slab:
             "q": np.ascontiguousarray(np.asarray(mesh["q"]).reshape(ne), dtype=np.uint8),
             "eps": np.ascontiguousarray(mesh["eps"], dtype=np.float64),
             "mu": np.ascontiguousarray(mesh["mu"], dtype=np.float64),
+            "hang": np.ascontiguousarray(np.asarray(mesh.get("hang", np.zeros((0, 6)))).reshape(-1, 6),
+                                         dtype=np.int64),
         }
         geom = {"brick": STM_GEOM_BRICK, "trilinear": STM_GEOM_TRILINEAR}[mesh.get("geometry", "brick")]
         m = stm_mesh(ne, arr["vert"].shape[0],
                      arr["vert"].ctypes.data_as(C.POINTER(C.c_double)),
                      arr["hex"].ctypes.data_as(C.POINTER(C.c_int64)),
                      arr["nbr"].ctypes.data_as(C.POINTER(C.c_int64)),
+                     arr["hang"].shape[0], arr["hang"].ctypes.data_as(C.POINTER(C.c_int64)),
                      arr["p"].ctypes.data_as(C.POINTER(C.c_uint8)),
                      arr["q"].ctypes.data_as(C.POINTER(C.c_uint8)),
                      arr["eps"].ctypes.data_as(C.POINTER(C.c_double)),

@@ -204,6 +204,42 @@ def test_energy_identity(case):
     assert abs(lhs - dE) <= 1e-12 * max(1.0, abs(dE))
 
 
+@pytest.mark.parametrize("uneven", [False, True])
+def test_energy_identity_hanging(uneven):
+    """2:1 hanging faces (corner-refined octree): the identity needs every face piece."""
+    m = meshgen.corner_octree_mesh(2, [0.8], p=2, q=2)
+    assert m["hang"].shape[0] == 12
+    if uneven:
+        meshgen.random_hp(m, 3, p_range=(1, 3), q_range=(1, 3))
+    else:
+        meshgen.random_materials(m, 5, 6)
+    o = stdg.Oracle(m)
+    # the oracle finds the hanging faces itself: 3 coarse faces in 4 pieces each, 12 fine faces
+    assert sum(len(o.pieces[e][f]) == 4 for e in range(o.ne) for f in range(6)) == 3
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) <= 1e-12 * max(1.0, abs(dE))
+
+
+def test_patch_hanging():
+    """E = (y, x, 0), H = (0, 0, 1) is reproduced exactly across 2:1 faces."""
+    m = meshgen.corner_octree_mesh(2, [0.8], p=1, q=1)
+    meshgen.random_hp(m, 9, p_range=(1, 2), q_range=(1, 3), eps_values=(1.0,))
+    o = stdg.Oracle(m)
+    Ef = lambda x: np.stack([x[:, 1], x[:, 0], 0 * x[:, 0]], 1)
+    Hf = lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], 1 + 0 * x[:, 0]], 1)
+    u0 = o.project(Ef, Hf)
+    U = o.embed_start(u0)
+    for e in range(o.ne):
+        blk = o.trial_block(U, e)
+        blk[:, :, 1, :] = blk[:, :, 0, :]
+
+    def g(x, t):
+        z = np.zeros(np.broadcast(x[..., 0], t).shape)
+        return np.stack([x[..., 1] + z, x[..., 0] + z, z], -1)
+
+    assert np.abs(o.residual(U, 0.0, 0.2, g=g)).max() < 1e-12
+
+
 # --------------------------------------------------------------------------
 # P6: polynomial patch test E = (0,0,x), H = (0,t,0), g = E
 # --------------------------------------------------------------------------
@@ -433,9 +469,9 @@ def test_planted_mistakes_fail_pins(monkeypatch):
     assert np.abs(R).max() < 1e-12
     orig_face = stdg.Oracle._face
 
-    def bad_face(self, e, f, uE, uH, vE, vH, dt, t0, g):
-        r = orig_face(self, e, f, uE, uH, vE, vH, dt, t0, g)
-        if self.nbr[e, f, 0] >= 0:
+    def bad_face(self, e, f, e2, rect, uE, uH, vE, vH, dt, t0, g):
+        r = orig_face(self, e, f, e2, rect, uE, uH, vE, vH, dt, t0, g)
+        if e2 >= 0:
             r = r.copy()
             r[:, 0] *= 2.0
         return r
