@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--q", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the hp-batch, curved and serving legs")
     ap.add_argument("--reorth", type=int, default=0, help="second Gram-Schmidt pass (DGKS test); off by default: same iteration count and accuracy on this workload")
     return ap.parse_args()
 
@@ -214,6 +215,141 @@ def measure_solve(s, u_init, dt, steps, warmup, barrier):
             "rel_residual": max(r["rel_residual"] for _, r in reps), "rc": [rc for rc, _ in reps]}
 
 
+def curved_flops_per_element(p, q):
+    """Algorithmic flops of one curved apply per element (both fields): the O(p^5)
+    sum-factorised mass replaces the affine mass term."""
+    n, nq = p + 1, p + 2
+    fl_prep, fl_apply = flops_per_element(p, q)
+    affine_mass = 2 * 2 * (3 * q * n ** 3)
+    mass = 2 * 2 * q * (6 * (n ** 3 * nq + n ** 2 * nq ** 2 + n * nq ** 3) + 9 * nq ** 3)
+    return fl_prep, fl_apply - affine_mass, mass
+
+
+def time_applies(s, m, dt, prec, reps=5, warm=2):
+    """CUDA-event time of `reps` residual applies through the C ABI on device buffers; profile dict."""
+    import torch
+
+    from paper_1307_5310_gb300 import stm
+
+    dtp = torch.float64 if prec == stm.STM_FP64 else torch.float32
+    U = torch.empty(s.n_trial, dtype=dtp, device="cuda").uniform_(-1, 1)
+    R = torch.empty(s.n_test, dtype=dtp, device="cuda")
+    for _ in range(warm):
+        s.residual_apply(U, R, 0.0, dt, prec=prec)
+    s.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        s.residual_apply(U, R, 0.0, dt, prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    del U, R
+    return e0.elapsed_time(e1) / reps, prof
+
+
+def leg_hp_batch(fp64_peak):
+    """2:1 corner-refined octree, 203,736 elements, p ~ U{1..7}, q ~ U{1..4}, eps ~ {1, 2.25, 4}."""
+    import numpy as np
+
+    from paper_1307_5310_gb300 import meshgen, stm
+
+    m = meshgen.corner_octree_mesh(50, [0.45, 0.2])
+    meshgen.random_hp(m, 1307)
+    p, q = m["p"].astype(np.int64), m["q"].astype(np.int64)
+    dof = int(np.sum(6 * (q + 1) * (p + 1) ** 3))
+    fl = sum(sum(flops_per_element(int(pp), int(qq))) for pp, qq in zip(p, q))
+    s = stm.Slab(m, tol=1e-9, max_it=400, reorth=False)
+    dt = (1.0 / 200) / 15
+    ms64, _ = time_applies(s, m, dt, stm.STM_FP64)
+    ms32, _ = time_applies(s, m, dt, stm.STM_FP32)
+    by32 = sum(bytes_per_element(int(pp), int(qq), 4) for pp, qq in zip(p, q))
+    ach = fl / (ms64 / 1e3) / 1e12
+    s.close()
+    return {"workload": "2:1 corner octree 203,736 elements, p~U{1..7}, q~U{1..4}, eps~{1,2.25,4}, all "
+                        f"{len(set(zip(p.tolist(), q.tolist())))} (p,q) classes + 2:1 transfers per apply",
+            "elements": int(m["hex"].shape[0]), "hanging_rows": int(m["hang"].shape[0]), "dof": dof,
+            "fp64": {"ms_per_apply": ms64, "gdofs": dof / (ms64 / 1e3) / 1e9,
+                     "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": ach / fp64_peak}},
+            "fp32": {"ms_per_apply": ms32, "gdofs": dof / (ms32 / 1e3) / 1e9,
+                     "roofline": {"bound": "hbm", "achieved": by32 / (ms32 / 1e3) / 1e9, "peak": 6780.0,
+                                  "unit": "GB/s", "frac": by32 / (ms32 / 1e3) / 1e9 / 6780.0}}}
+
+
+def leg_curved(fp64_peak):
+    """32^3 trilinear hexes (vertices moved by 0.1 h sin sin sin), p in {3, 5, 7}, q = p - 1."""
+    from paper_1307_5310_gb300 import meshgen, stm
+
+    out = {}
+    for p in (3, 5, 7):
+        q = p - 1
+        m = meshgen.box_mesh(32, p=p, q=q, perturb=0.1, order="morton")
+        meshgen.random_materials(m, 1307, 1308)
+        s = stm.Slab(m)
+        ne = m["hex"].shape[0]
+        dt = (1.0 / 32) / (2 * p + 1)
+        ms64, _ = time_applies(s, m, dt, stm.STM_FP64, reps=3)
+        ms32, _ = time_applies(s, m, dt, stm.STM_FP32, reps=3)
+        fp, fa, fm = curved_flops_per_element(p, q)
+        ach = (fp + fa + fm) * ne / (ms64 / 1e3) / 1e12
+        dof = ne * 6 * (q + 1) * (p + 1) ** 3
+        out[f"p{p}"] = {"ms_fp64": ms64, "ms_fp32": ms32, "gdofs_fp64": dof / (ms64 / 1e3) / 1e9,
+                        "gdofs_fp32": dof / (ms32 / 1e3) / 1e9, "flops_per_element": fp + fa + fm,
+                        "roofline_fp64": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                          "frac": ach / fp64_peak}}
+        s.close()
+    return out
+
+
+def leg_serving(n_req=48, rate=50.0, seed=1311):
+    """Poisson stream (mean `rate` req/s) of cavity/scattering requests, n^3 meshes with n
+    log-uniform in [8, 24] (multiples of 4), p ~ U{2..6}, q ~ U{1..3}, random eps/mu boxes and
+    Gaussian pulses, 10 slabs each to 1e-9, mixed precision."""
+    import numpy as np
+
+    from paper_1307_5310_gb300 import stm
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, n_req)
+    reqs = []
+    for k in range(n_req):
+        n = int(4 * round(np.exp(rng.uniform(np.log(8), np.log(24))) / 4))
+        p, q = int(rng.integers(2, 7)), int(rng.integers(1, 4))
+        boxes = []
+        for _ in range(int(rng.integers(1, 5))):
+            a = rng.uniform(0, 0.7, 3)
+            b = a + rng.uniform(0.1, 0.3, 3)
+            boxes.append(tuple(a) + tuple(np.minimum(b, 1.0)) + (rng.uniform(1, 4), rng.uniform(1, 4)))
+        srcs = []
+        for _ in range(int(rng.integers(1, 4))):
+            d = rng.normal(size=3)
+            srcs.append(dict(centre=tuple(rng.uniform(0.2, 0.8, 3)), dir=tuple(d / np.linalg.norm(d)), sigma_x=0.05,
+                             t0=0.2, sigma_t=0.05, amp=1.0))
+        kind = int(rng.integers(0, 2))
+        reqs.append(dict(n=n, p=p, q=q, n_slabs=10, dt=(1.0 / n) / (2 * p + 1), kind=kind, boxes=boxes,
+                         sources=srcs if kind == 1 else srcs[:1]))
+    srv = stm.Server(workers=8, precision=stm.STM_MIXED, tol=1e-9, max_it=2000)
+    t0 = time.perf_counter()
+    tickets = []
+    for k, r in enumerate(reqs):
+        while time.perf_counter() - t0 < float(np.sum(gaps[:k + 1])):
+            time.sleep(0.0005)
+        tickets.append(srv.submit(**r))
+    res = [srv.wait(t)[0] for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = sorted(r["latency_ms"] for r in res if r["status"] >= 0)
+    return {"requests": n_req, "offered_req_per_s": rate, "achieved_req_per_s": len(lat) / wall,
+            "completed": st["completed"], "failed": st["failed"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "slab_solves_per_s": st["solves_per_s"], "peak_admitted_gb": st["peak_admitted_bytes"] / 1e9,
+            "max_rel_residual": max(r["max_rel_residual"] for r in res), "workers": 8, "precision": "mixed",
+            "workload": "Poisson stream; n^3 unit-cube bricks, n log-uniform in [8,24] (x4), p~U{2..6}, q~U{1..3}, "
+                        "1-4 eps/mu boxes U[1,4], 1-3 Gaussian pulses, cavity or scattering, 10 slabs to 1e-9"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -334,6 +470,16 @@ def run_ours(args):
     except Exception as ex:  # reported, never replaced by another path
         mixed = {"error": repr(ex)}
 
+    extra = {}
+    if not args.no_extra:
+        for name, fn in (("hp_batch", lambda: leg_hp_batch(fp64_peak)), ("curved", lambda: leg_curved(fp64_peak)),
+                         ("serving", leg_serving)):
+            try:
+                extra[name] = fn()
+            except Exception as ex:  # reported, never replaced by another path
+                extra[name] = {"error": repr(ex)}
+            torch.cuda.empty_cache()
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -354,6 +500,7 @@ def run_ours(args):
             "roofline": roofline, "mixed": mixed, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": r64["launches"],
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

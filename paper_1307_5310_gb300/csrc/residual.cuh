@@ -208,26 +208,37 @@ __device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int ns
   return A.tr[A.off_tr[en] + so * (Nn * Nn) + slow * Nn + fast];
 }
 
+// Shared memory per k_apply pass: y of the other field and the residual rows;
+// both fields in one pass when that fits in ~110 KB, else one field per pass.
+template <typename T, int P, int Q>
+struct ApplyShape {
+  static constexpr int N3 = (P + 1) * (P + 1) * (P + 1);
+  static constexpr bool split = 12 * Q * N3 * sizeof(T) > 110 * 1024;
+  static constexpr int NF = split ? 1 : 2;  // fields per pass
+  static constexpr size_t smem = sizeof(T) * 2 * NF * 3 * Q * N3;
+};
+
 template <typename T, int P, int Q, bool HP>
 __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  constexpr int NF = ApplyShape<T, P, Q>::NF;
+  constexpr int FB = 3 * Q * N3;           // one field's block
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ys = reinterpret_cast<T*>(smem_raw);  // [3][Q][N3]: y of the other field
-  T* Rs = ys + 3 * Q * N3;                  // [3][Q][N3]: residual rows of this field
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [NF][3][Q][N3]: y of the other field
+  T* Rs = ys + NF * FB;                     // [NF][3][Q][N3]: residual rows
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
     const ElemAddr<T, P, Q, HP> ad(A, blk);
     const int64_t e = ad.e;
     const int32_t* nb = A.nbr + e * 6;
 #pragma unroll 1
-    for (int f = 0; f < 2; ++f) {
-      const int fp = 1 - f;
-      const T* yg = A.y + ad.R + fp * (int64_t)(3 * Q * N3);
-      T* Rg = A.R + ad.R + f * (int64_t)(3 * Q * N3);
-      const T* bg = A.b ? A.b + ad.R + f * (int64_t)(3 * Q * N3) : nullptr;
-      for (int it = threadIdx.x; it < 3 * Q * N3; it += blockDim.x) {
-        ys[it] = yg[it];
-        const int cc = it / (Q * N3);
-        const int r = it - cc * (Q * N3);
+    for (int f0 = 0; f0 < 2; f0 += NF) {
+      for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
+        const int fl = NF == 1 ? 0 : it / FB;
+        const int f = f0 + fl, fp = 1 - f;
+        const int w = it - fl * FB;
+        ys[it] = A.y[ad.R + fp * (int64_t)FB + w];
+        const int cc = w / (Q * N3);
+        const int r = w - cc * (Q * N3);
         const int i = r / N3, s = r - i * N3;
         const int fc = f * 3 + cc;
         T v;
@@ -236,19 +247,21 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           v = mc * A.um[ad.um + fc * ad.um_cs + i * N3 + s];
           if (i == 0 && A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
         } else {
-          v = Rg[it];
+          v = A.R[ad.R + f * (int64_t)FB + w];
         }
-        if (bg) v -= bg[it];
+        if (A.b) v -= A.b[ad.R + f * (int64_t)FB + w];
         Rs[it] = v;
       }
       __syncthreads();
 #pragma unroll 1
       for (int k = 0; k < 2; ++k) {
-        for (int it = threadIdx.x; it < 3 * Q * N2; it += blockDim.x) {
+        for (int it = threadIdx.x; it < NF * 3 * Q * N2; it += blockDim.x) {
           int r = it;
           const int t = r % N2; r /= N2;
-          const int i = r % Q;
-          const int c = r / Q;
+          const int i = r % Q; r /= Q;
+          const int c = r % 3;
+          const int fl = r / 3;
+          const int f = f0 + fl, fp = 1 - f;
           const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
           const int b = 3 - c - a;
           // eps_{c a b}: +1 for cyclic (c, a, b); the sign s_F eps_{cab} is applied by
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
           int base, stride;
           line_geom<N>(a, t, base, stride);
-          const T* yl = ys + (b * Q + i) * N3 + base;
+          const T* yl = ys + fl * FB + (b * Q + i) * N3 + base;
           // jumps of the tangential component b of field fp on the faces normal to a
           const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * Q + i;  // side-0 slot within an element
           const T* tre = A.tr + ad.tr;
@@ -276,7 +289,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           T yv[N];
 #pragma unroll
           for (int j = 0; j < N; ++j) yv[j] = flip_sign(yl[j * stride], flip);
-          T* Rl = Rs + (c * Q + i) * N3 + base;
+          T* Rl = Rs + fl * FB + (c * Q + i) * N3 + base;
 #pragma unroll
           for (int al = 0; al < N; ++al) {
             T r2 = Rl[al * stride];
@@ -289,7 +302,8 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         }
         __syncthreads();
       }
-      for (int it = threadIdx.x; it < 3 * Q * N3; it += blockDim.x) Rg[it] = Rs[it];
+      T* Rg = A.R + ad.R + f0 * (int64_t)FB;
+      for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) Rg[it] = Rs[it];
       __syncthreads();
     }
   }
@@ -446,7 +460,7 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   constexpr int N = P + 1, N3 = N * N * N;
   constexpr int N2 = N * N;
   const size_t sm_prep = sizeof(T) * 6 * Q * N3;
-  const size_t sm_apply = sm_prep;
+  const size_t sm_apply = ApplyShape<T, P, Q>::smem;
   const size_t sm_fused = 2 * sm_prep + sizeof(T) * 24 * Q * N2;
   // thread-safe one-time set-up (function-local static initialisation)
   static const bool configured = [&] {
