@@ -100,6 +100,9 @@ typedef struct {
   int64_t stream;        /* cudaStream_t as integer; 0 = the CUDA default stream  */
   int32_t reorth;        /* 1: second Gram-Schmidt pass when the norm drops below
                             1/sqrt(2) of its value (DGKS test); 0: never           */
+  int32_t graph;         /* 1: on meshes with several (p, q) classes or 2:1 faces,
+                            capture each residual apply (all launches) once in a
+                            CUDA graph per (buffers, dt) and replay it             */
 } stm_opts;
 
 typedef struct {
@@ -171,6 +174,15 @@ int32_t stm_slab_solve(stm_ctx *ctx, double dt, stm_solve_report *rep);
 
 /* Discrete energy 1/2 int eps E.E + mu H.H of the state (Eq. stability:energydef), FP64. */
 int32_t stm_energy(stm_ctx *ctx, double *energy);
+
+/* Autotuner (the paper has no counterpart): for every (p, q) class of the mesh
+ * (one class on uniform meshes) time the residual kernels with 64, 128 and
+ * 256 threads per block, reps times each, on scratch data of the mesh's own
+ * layout, and keep the fastest for later applies.  Reports per class (up to
+ * n_max) the degrees, the chosen block size and its time in ms; *n_out = the
+ * number of classes.  Allocates scratch buffers for the duration of the call. */
+int32_t stm_autotune(stm_ctx *ctx, double dt, int32_t reps, int32_t n_max, int32_t *P, int32_t *Q,
+                     int32_t *block, double *ms, int32_t *n_out);
 
 /* Number of kernels this context has launched (residual, Krylov, energy). */
 int32_t stm_launch_count(stm_ctx *ctx, int64_t *n);

@@ -227,9 +227,18 @@ class Oracle:
     def X8(self, e: int) -> np.ndarray:
         return self.vert[self.hex[e]]
 
-    def trial_block(self, U: np.ndarray, e: int) -> np.ndarray:
-        """[..., 2, 3, q+1, N3] view of element e's trial coefficients (U [..., N_trial])."""
-        p, q = self.p[e], self.q[e]
+    def trial_block(self, U, e: int) -> np.ndarray:
+        """[..., 2, 3, q+1, N3] view of element e's trial coefficients.
+
+        U is a trial vector [..., N_trial] or a dict {element: block [B, 2, 3, q+1, N3]}
+        holding only some elements' blocks (the others are zero).
+        """
+        p, q = int(self.p[e]), int(self.q[e])
+        if isinstance(U, dict):
+            if e in U:
+                return U[e]
+            B = next(iter(U.values())).shape[0]
+            return np.zeros((B, 2, 3, q + 1, (p + 1) ** 3))
         blk = U[..., self.trial_off[e]:self.trial_off[e + 1]]
         return blk.reshape(blk.shape[:-1] + (2, 3, q + 1, (p + 1) ** 3))
 
@@ -427,9 +436,10 @@ class Oracle:
         selects the contribution of element e's own coefficients (volume and
         own face traces, no load) or of neighbour element e2's coefficients.
         """
-        U = np.atleast_2d(U)
-        B = U.shape[0]
+        if not isinstance(U, dict):
+            U = np.atleast_2d(U)
         u = self.trial_block(U, e)
+        B = u.shape[0]
         p, q = int(self.p[e]), int(self.q[e])
         R = np.zeros((B, 2, 3, q, (p + 1) ** 3))
         if parts in ("all", "own"):
@@ -474,8 +484,8 @@ class Oracle:
             blocks = [("own", e)] + [(("nbr", e2), e2) for e2 in self.neighbours_of(e)]
             for part, e2 in blocks:
                 m = int(self.trial_sz[e2])
-                Ub = np.zeros((m, ntr))
-                Ub[np.arange(m), self.trial_off[e2] + np.arange(m)] = 1.0
+                # unit vectors of element e2's trial block (only that block is formed)
+                Ub = {e2: np.eye(m).reshape(m, 2, 3, int(self.q[e2]) + 1, (int(self.p[e2]) + 1) ** 3)}
                 Rb = self.element_residual(e, Ub, t0, dt, None, None, parts=part).reshape(m, -1)
                 Rb = Rb.T  # [test, m]
                 ii, jj = np.nonzero(Rb)

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -211,6 +213,19 @@ struct stm_ctx {
   double* hbuf64 = nullptr;
   float* hbuf32 = nullptr;
   double Tm[2][8][8] = {};
+  // uniform-mesh block size (autotuned), CUDA graphs of multi-class applies
+  int block = 256;
+  cudaStream_t cap_stream = nullptr;
+  struct GraphKey {
+    int prec, um_layout, u0_layout;
+    const void *um, *u0, *b, *R;
+    double dt;
+    bool operator<(const GraphKey& o) const {
+      return std::tie(prec, um_layout, u0_layout, um, u0, b, R, dt) <
+             std::tie(o.prec, o.um_layout, o.u0_layout, o.um, o.u0, o.b, o.R, o.dt);
+    }
+  };
+  std::map<GraphKey, cudaGraphExec_t> graphs;
   double* X8 = nullptr;
   double *eps64 = nullptr, *mu64 = nullptr;
   float *eps32 = nullptr, *mu32 = nullptr;
@@ -369,6 +384,19 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
     a.off_R = c->off_test;
     a.off_tr = c->off_tr;
     a.pq = c->pq;
+    const bool use_graph = c->opts.graph && !c->profiling;
+    typename stm_ctx::GraphKey key{sizeof(T) == 8 ? 0 : 1, um_layout, u0_layout, um, u0, b, R, dt};
+    if (use_graph) {
+      auto it = c->graphs.find(key);
+      if (it != c->graphs.end()) {
+        c->launches += 2 * (int64_t)c->classes.size() + (c->n_slots > 0);
+        STM_CK(cudaGraphLaunch(it->second, c->stream));
+        return STM_OK;
+      }
+      if (!c->cap_stream) STM_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      STM_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    }
+    cudaStream_t ls = use_graph ? c->cap_stream : c->stream;
     LaunchEvents ev, none;
     int rc = record_events<T>(c, ev);
     if (rc) return rc;
@@ -394,7 +422,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         for (int u = 0; u < 2; ++u)
           for (int j = 0; j < 8; ++j)
             for (int nn = 0; nn < 8; ++nn) h.Tm[u][j][nn] = (T)c->Tm[u][j][nn];
-        launch_hang<T>(h, c->stream);
+        launch_hang<T>(h, ls);
         c->launches += 1;
       }
       for (size_t k = 0; k < c->classes.size(); ++k) {
@@ -407,10 +435,31 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         if (phase == 1 && k + 1 == c->classes.size()) e2.mid = ev.mid;
         if (phase == 2 && k + 1 == c->classes.size()) e2.stop = ev.stop;
         const int grid = (int)std::min<int64_t>(cl.count, 1 << 30);
-        const int e = launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, e2, phase, cl.block);
+        const int e = launch_residual_ph<T>(cl.P, cl.Q, a, ls, grid, e2, phase, cl.block);
         c->launches += 1;
-        if (e) return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
+        if (e) {
+          if (use_graph) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(c->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+          }
+          return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
+        }
       }
+    }
+    if (use_graph) {
+      cudaGraph_t g = nullptr;
+      STM_CK(cudaStreamEndCapture(c->cap_stream, &g));
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return fail(c, STM_EDEVICE, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      if (c->graphs.size() > 64) {
+        for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+        c->graphs.clear();
+      }
+      c->graphs[key] = ex;
+      STM_CK(cudaGraphLaunch(ex, c->stream));
     }
     return STM_OK;
   }
@@ -437,7 +486,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   int rc = record_events<T>(c, ev);
   if (rc) return rc;
   c->launches += 2;
-  const int e = launch_residual<T>(c->P, c->Q, a, c->stream, grid, ev);
+  const int e = launch_residual_ph<T>(c->P, c->Q, a, c->stream, grid, ev, 0, c->block);
   if (e) return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
   return STM_OK;
 }
@@ -829,6 +878,7 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     c->opts.deterministic = 1;
     c->opts.stream = 0;
     c->opts.reorth = 1;
+    c->opts.graph = 1;
   }
   if (c->opts.restart < 1 || c->opts.restart > kMaxDots - 1)
     return bad(STM_EINVAL, "restart must be 1..15");
@@ -1154,6 +1204,8 @@ int32_t stm_destroy(stm_ctx* c) {
   for (auto& k : c->classes)
     if (k.elist) cudaFree(k.elist);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return STM_OK;
@@ -1417,6 +1469,113 @@ int32_t stm_set_boundary(stm_ctx* c, stm_st_field_fn g, void* user) {
   c->gfn = g;
   c->guser = user;
   c->load_valid = false;
+  return STM_OK;
+}
+
+}  // extern "C"
+
+// Autotuner: for every (p, q) class (or the whole uniform mesh) time the
+// residual kernels with 64, 128 and 256 threads per block on the context's
+// own data layout and keep the fastest; later applies use it.
+template <typename T>
+int autotune_prec(stm_ctx* c, double dt, int reps, std::vector<double>& best_ms) {
+  T *U = nullptr, *R = nullptr;
+  if (cudaMalloc(&U, c->n_trial * sizeof(T)) != cudaSuccess || cudaMalloc(&R, c->n_test * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    if (U) cudaFree(U);
+    return fail(c, STM_ENOMEM, "autotune buffers");
+  }
+  cudaMemsetAsync(U, 0, c->n_trial * sizeof(T), c->stream);
+  const bool saved_graph = c->opts.graph != 0;
+  c->opts.graph = 0;
+  int rc = apply<T>(c, dt, U, L_TRIAL, U, L_TRIAL, nullptr, R);  // warm up, traces for every class
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cands[3] = {64, 128, 256};
+  const size_t ncl = c->hp ? c->classes.size() : 1;
+  best_ms.assign(ncl, 0.0);
+  for (size_t k = 0; k < ncl && rc == STM_OK; ++k) {
+    double best = 1e30;
+    int bb = 256;
+    for (int cb : cands) {
+      if (c->hp) c->classes[k].block = cb;
+      else c->block = cb;
+      float ms = 0.f;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && rc == STM_OK; ++r) {
+        if (!c->hp) {
+          rc = apply<T>(c, dt, U, L_TRIAL, U, L_TRIAL, nullptr, R);
+        } else {
+          // this class alone (its trace pass, then its apply pass; other classes' traces are current)
+          const auto& cl = c->classes[k];
+          T *y = nullptr, *tr = nullptr;
+          scratch<T>(c, &y, &tr);
+          ApplyArgs<T> a;
+          a.y = y;
+          a.tr = tr;
+          a.R = R;
+          a.nbr = c->nbr;
+          a.mass = mass_ptr<T>(c);
+          a.um = U;
+          a.u0 = U;
+          a.off_um = c->off_trial;
+          a.um_trial = 1;
+          a.off_u0 = c->off_trial;
+          a.off_R = c->off_test;
+          a.off_tr = c->off_tr;
+          a.pq = c->pq;
+          a.hslot = c->hslot;
+          a.hoff = c->hoff;
+          a.hbuf = hbuf_ptr<T>(c);
+          a.elist = cl.elist;
+          a.n_elem = cl.count;
+          a.tb = make_tables<T>(cl.P, kMaxQ, dt);
+          const int grid = (int)std::min<int64_t>(cl.count, 1 << 30);
+          LaunchEvents none;
+          if (launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, none, 1, cb) ||
+              launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, none, 2, cb))
+            rc = fail(c, STM_EDEVICE, "autotune launch");
+        }
+      }
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bb = cb;
+      }
+    }
+    if (c->hp) c->classes[k].block = bb;
+    else c->block = bb;
+    best_ms[k] = best / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(U);
+  cudaFree(R);
+  c->opts.graph = saved_graph;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // launch shapes changed
+  c->graphs.clear();
+  return rc;
+}
+
+extern "C" {
+
+int32_t stm_autotune(stm_ctx* c, double dt, int32_t reps, int32_t n_max, int32_t* P, int32_t* Q, int32_t* block,
+                     double* ms, int32_t* n_out) {
+  if (!c || !(dt > 0) || reps < 1) return STM_EINVAL;
+  std::vector<double> best;
+  int rc = autotune_prec<double>(c, dt, reps, best);
+  if (rc) return rc;
+  const int ncl = c->hp ? (int)c->classes.size() : 1;
+  if (n_out) *n_out = ncl;
+  for (int k = 0; k < ncl && k < n_max; ++k) {
+    if (P) P[k] = c->hp ? c->classes[k].P : c->P;
+    if (Q) Q[k] = c->hp ? c->classes[k].Q : c->Q;
+    if (block) block[k] = c->hp ? c->classes[k].block : c->block;
+    if (ms) ms[k] = best[k];
+  }
   return STM_OK;
 }
 

@@ -41,7 +41,7 @@ EXPORTS = (
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
     "stm_set_source_gauss", "stm_set_boundary",
     "stm_server_create", "stm_server_submit", "stm_server_poll", "stm_server_wait", "stm_server_stats",
-    "stm_server_destroy",
+    "stm_server_destroy", "stm_autotune",
 )
 
 
@@ -58,7 +58,7 @@ class stm_mesh(C.Structure):
 
 class stm_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32),
-                ("deterministic", C.c_int32), ("stream", C.c_int64), ("reorth", C.c_int32)]
+                ("deterministic", C.c_int32), ("stream", C.c_int64), ("reorth", C.c_int32), ("graph", C.c_int32)]
 
 
 class stm_solve_report(C.Structure):
@@ -131,6 +131,8 @@ def lib() -> C.CDLL:
         L.stm_server_wait.argtypes = [vp, i64, C.POINTER(stm_result), vp]
         L.stm_server_stats.argtypes = [vp, C.POINTER(stm_stats)]
         L.stm_server_destroy.argtypes = [vp]
+        L.stm_autotune.argtypes = [vp, d, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(d),
+                                   C.POINTER(i32)]
         for name in EXPORTS:
             if name != "stm_last_error":
                 getattr(L, name).restype = C.c_int32
@@ -184,7 +186,7 @@ class Slab:
     """One library context for a mesh (see include/stm.h)."""
 
     def __init__(self, mesh: dict, precision=STM_FP64, tol=1e-12, restart=10, max_it=500,
-                 deterministic=True, stream=None, reorth=True):
+                 deterministic=True, stream=None, reorth=True, graph=True):
         L = lib()
         self._keep = {}
         ne = mesh["hex"].shape[0]
@@ -213,7 +215,8 @@ class Slab:
             import torch
 
             stream = torch.cuda.current_stream().cuda_stream
-        o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream), 1 if reorth else 0)
+        o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream), 1 if reorth else 0,
+                     1 if graph else 0)
         h = C.c_void_p()
         rc = L.stm_create(C.byref(h), C.byref(m), C.byref(o))
         if rc != STM_OK:
@@ -277,6 +280,14 @@ class Slab:
         e = C.c_double()
         self._check(lib().stm_energy(self.ctx, C.byref(e)))
         return e.value
+
+    def autotune(self, dt: float, reps: int = 3):
+        """Pick the block size of every (p, q) class; returns [(p, q, block, ms)]."""
+        n = 64
+        P, Q, B = (C.c_int32 * n)(), (C.c_int32 * n)(), (C.c_int32 * n)()
+        ms, cnt = (C.c_double * n)(), C.c_int32()
+        self._check(lib().stm_autotune(self.ctx, dt, reps, n, P, Q, B, ms, C.byref(cnt)))
+        return [(P[k], Q[k], B[k], ms[k]) for k in range(min(cnt.value, n))]
 
     def launch_count(self) -> int:
         n = C.c_int64()

@@ -71,7 +71,7 @@ def test_residual_hanging_fp32(stm):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_slab_solve_hanging(stm, precision):
     m = meshgen.corner_octree_mesh(2, [0.8])
-    meshgen.random_hp(m, 9, p_range=(1, 3), q_range=(1, 3))
+    meshgen.random_hp(m, 9, p_range=(1, 2), q_range=(1, 3))
     o = stdg.Oracle(m)
     n_state = int(np.sum(6 * (m["p"].astype(np.int64) + 1) ** 3))
     u0 = np.random.Generator(np.random.PCG64(10)).uniform(-1, 1, n_state)
@@ -115,3 +115,41 @@ def test_hp_batch_full_size_sampled(stm):
     for e, le in zip(sample, loc):
         Ro = o.element_residual(le, Us, 0.0, dt)[0].ravel()
         assert rel(R[off[e]:off[e + 1]], Ro) < 1e-12, e
+
+
+def test_graph_and_autotune(stm):
+    """Graph-captured multi-class applies and autotuned block sizes give the same residual,
+    and a graph-replayed slab solve matches the oracle."""
+    import torch
+
+    m = meshgen.corner_octree_mesh(2, [0.8, 0.4])
+    meshgen.random_hp(m, 12, p_range=(1, 5), q_range=(1, 4))
+    U = torch.from_numpy(meshgen.random_coeffs(m, 13)).cuda()
+    ref = stm.Slab(m, graph=False)
+    R0 = torch.empty(ref.n_test, dtype=torch.float64, device="cuda")
+    ref.residual_apply(U, R0, 0.0, 0.02)
+    s = stm.Slab(m, graph=True)
+    R1 = torch.empty_like(R0)
+    for _ in range(3):  # first call captures, the others replay
+        R1.zero_()
+        s.residual_apply(U, R1, 0.0, 0.02)
+        torch.cuda.synchronize()
+        assert torch.equal(R1, R0)
+    tuned = s.autotune(0.02, reps=2)
+    assert len(tuned) == len(set(zip(m["p"].tolist(), m["q"].tolist())))
+    assert all(b in (64, 128, 256) for _, _, b, _ in tuned)
+    s.residual_apply(U, R1, 0.0, 0.02)
+    torch.cuda.synchronize()
+    assert torch.equal(R1, R0)
+    # slab solve with replayed graphs vs the oracle (a smaller hp mesh)
+    m = meshgen.corner_octree_mesh(2, [0.8])
+    meshgen.random_hp(m, 15, p_range=(1, 2), q_range=(1, 2))
+    o = stdg.Oracle(m)
+    n_state = int(np.sum(6 * (m["p"].astype(np.int64) + 1) ** 3))
+    u0 = np.random.Generator(np.random.PCG64(14)).uniform(-1, 1, n_state)
+    uo = o.end_state(o.slab_solve(u0, 0.0, 0.02))
+    s2 = stm.Slab(m, graph=True, tol=1e-14, max_it=4000)
+    s2.set_state(u0)
+    rc, rep = s2.slab_solve(0.02)
+    assert rc == stm.STM_OK
+    assert rel(s2.get_state()[0], uo) < 1e-11
