@@ -26,7 +26,7 @@ __device__ double block_sum(double v, double* sh) {
 }
 
 // Per-thread accumulator: FP64 for double storage; for float storage, FP32
-// sums of 8 consecutive products flushed into an FP64 total.
+// sums of the 4 products of one 16-byte chunk flushed into an FP64 total.
 template <typename S>
 struct Acc;
 template <>
@@ -48,23 +48,77 @@ struct Acc<float> {
   __device__ __forceinline__ double get() const { return a + (double)f; }
 };
 
+// 16-byte vectors: float4 / double2.  Basis columns are 16-byte aligned
+// (their leading dimension is padded); a scalar loop takes the tail.
+template <typename S>
+struct Vec;
+template <>
+struct Vec<float> {
+  using T = float4;
+  static constexpr int W = 4;
+  __device__ static float get(const float4& v, int l) { return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w; }
+  __device__ static void set(float4& v, int l, float x) {
+    if (l == 0) v.x = x; else if (l == 1) v.y = x; else if (l == 2) v.z = x; else v.w = x;
+  }
+};
+template <>
+struct Vec<double> {
+  using T = double2;
+  static constexpr int W = 2;
+  __device__ static double get(const double2& v, int l) { return l == 0 ? v.x : v.y; }
+  __device__ static void set(double2& v, int l, double x) {
+    if (l == 0) v.x = x; else v.y = x;
+  }
+};
+
+// chunks per loop trip: enough independent 16-byte loads in flight per thread
+template <int K>
+struct Unroll {
+  static constexpr int U = K <= 1 ? 4 : (K <= 3 ? 2 : 1);
+};
+
 template <typename S, int K>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const S* __restrict__ w, const S* __restrict__ V,
                                                           int64_t ldv, int with_norm, int64_t n,
                                                           double* __restrict__ partial) {
+  using VT = typename Vec<S>::T;
+  constexpr int W = Vec<S>::W, U = Unroll<K>::U;
   __shared__ double sh[32];
   Acc<S> acc[K + 1];
-  int cnt = 0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    const S wj = w[j];
+  const int64_t nv = n / W;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const VT* w4 = reinterpret_cast<const VT*>(w);
+  for (int64_t c0 = tid; c0 < nv; c0 += nth * U) {
+    VT wv[U], vv[U][K > 0 ? K : 1];
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i].add(wj, V[i * ldv + j]);
-    if (with_norm) acc[K].add(wj, wj);
-    if (++cnt == 8) {
-      cnt = 0;
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * nth;
+      if (c < nv) {
+        wv[u] = w4[c];
 #pragma unroll
-      for (int i = 0; i <= K; ++i) acc[i].flush();
+        for (int i = 0; i < K; ++i) vv[u][i] = reinterpret_cast<const VT*>(V + i * ldv)[c];
+      }
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c0 + u * nth < nv) {
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+          const S x = Vec<S>::get(wv[u], l);
+#pragma unroll
+          for (int i = 0; i < K; ++i) acc[i].add(x, Vec<S>::get(vv[u][i], l));
+          if (with_norm) acc[K].add(x, x);
+        }
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc[i].flush();
+      }
+    }
+  }
+  for (int64_t j = nv * W + tid; j < n; j += nth) {  // tail
+    const S x = w[j];
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i].add(x, V[i * ldv + j]);
+    if (with_norm) acc[K].add(x, x);
   }
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -80,22 +134,50 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const S* __restrict__ 
 template <typename S, int K>
 __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(S* __restrict__ w, const S* __restrict__ V, int64_t ldv,
                                                            Coef16 c, int64_t n, double* __restrict__ partial) {
+  using VT = typename Vec<S>::T;
+  constexpr int W = Vec<S>::W, U = Unroll<K>::U;
   __shared__ double sh[32];
   S cc[K > 0 ? K : 1];
 #pragma unroll
   for (int i = 0; i < K; ++i) cc[i] = (S)c.c[i];
   Acc<S> acc;
-  int cnt = 0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    S v = w[j];
+  const int64_t nv = n / W;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  VT* w4 = reinterpret_cast<VT*>(w);
+  for (int64_t c0 = tid; c0 < nv; c0 += nth * U) {
+    VT wv[U], vv[U][K > 0 ? K : 1];
 #pragma unroll
-    for (int i = 0; i < K; ++i) v = fma(-cc[i], V[i * ldv + j], v);
-    if (K > 0) w[j] = v;
-    acc.add(v, v);
-    if (++cnt == 8) {
-      cnt = 0;
-      acc.flush();
+    for (int u = 0; u < U; ++u) {
+      const int64_t cix = c0 + u * nth;
+      if (cix < nv) {
+        wv[u] = w4[cix];
+#pragma unroll
+        for (int i = 0; i < K; ++i) vv[u][i] = reinterpret_cast<const VT*>(V + i * ldv)[cix];
+      }
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t cix = c0 + u * nth;
+      if (cix < nv) {
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+          S x = Vec<S>::get(wv[u], l);
+#pragma unroll
+          for (int i = 0; i < K; ++i) x = fma(-cc[i], Vec<S>::get(vv[u][i], l), x);
+          Vec<S>::set(wv[u], l, x);
+          acc.add(x, x);
+        }
+        acc.flush();
+        if (K > 0) w4[cix] = wv[u];
+      }
+    }
+  }
+  for (int64_t j = nv * W + tid; j < n; j += nth) {  // tail
+    S x = w[j];
+#pragma unroll
+    for (int i = 0; i < K; ++i) x = fma(-cc[i], V[i * ldv + j], x);
+    if (K > 0) w[j] = x;
+    acc.add(x, x);
   }
   const double r = block_sum(acc.get(), sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -120,8 +202,19 @@ __device__ __forceinline__ int64_t block_of(int64_t j, int64_t blk) {
 template <typename S, bool Small>
 __global__ void k_precond(S* __restrict__ z, const S* __restrict__ v, const S* __restrict__ inv, int64_t blk,
                           int64_t n) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    z[j] = v[j] * inv[block_of<Small>(j, blk)];
+  using VT = typename Vec<S>::T;
+  constexpr int W = Vec<S>::W;
+  const int64_t nv = n / W;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = tid; c < nv && blk >= W; c += nth) {  // blocks of at least W entries: <= 2 per vector
+    VT x = reinterpret_cast<const VT*>(v)[c];
+    const int64_t j0 = c * W, b0 = block_of<Small>(j0, blk), edge = (b0 + 1) * blk;
+    const S s0 = inv[b0], s1 = (j0 + W > edge) ? inv[b0 + 1] : s0;
+#pragma unroll
+    for (int l = 0; l < W; ++l) Vec<S>::set(x, l, Vec<S>::get(x, l) * (j0 + l < edge ? s0 : s1));
+    reinterpret_cast<VT*>(z)[c] = x;
+  }
+  for (int64_t j = (blk >= W ? nv * W : 0) + tid; j < n; j += nth) z[j] = v[j] * inv[block_of<Small>(j, blk)];
 }
 
 template <typename S, typename X, int K, bool Small>

@@ -716,8 +716,8 @@ int norm2(stm_ctx* c, S* v, int64_t n, double* out) {
 // of basis vectors used and the coefficients yc[i] such that the correction
 // is P^{-1} sum_{i<k} yc[i] V[i]; *res is the residual norm estimate |g_k|.
 template <typename S>
-int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double tol_abs, int max_iters, int* k_out,
-                Coef16* yc, double* res, int* iters) {
+int gmres_cycle(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n, double a0, double tol_abs, int max_iters,
+                int* k_out, Coef16* yc, double* res, int* iters) {
   const int m = c->opts.restart;
   const int64_t qn3 = (int64_t)c->Q * c->N3;
   std::vector<double> H((m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), alpha(m + 1), yv(m);
@@ -725,16 +725,16 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double 
   g[0] = std::fabs(a0);
   int k = 0, rc;
   for (int j = 0; j < m && *iters < max_iters; ++j) {
-    S* W = V + (size_t)(j + 1) * n;
+    S* W = V + (size_t)(j + 1) * ldv;
     if (c->geometry == STM_GEOM_TRILINEAR)
-      precond_curved<S, S>(z, V + (size_t)j * n, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream);
+      precond_curved<S, S>(z, V + (size_t)j * ldv, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream);
     else if (c->hp)
-      precond_hp<S>(z, V + (size_t)j * n, inv_ptr<S>(c), c->off_test, c->pq, c->ne, c->stream);
+      precond_hp<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), c->off_test, c->pq, c->ne, c->stream);
     else
-      precond_apply<S>(z, V + (size_t)j * n, inv_ptr<S>(c), qn3, n, c->stream);
+      precond_apply<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), qn3, n, c->stream);
     c->launches += 1;
     if ((rc = linop<S>(c, dt, z, W))) return rc;
-    multidot<S>(W, V, n, j + 1, true, n, c->red_partial, c->red_out, c->stream);
+    multidot<S>(W, V, ldv, j + 1, true, n, c->red_partial, c->red_out, c->stream);
     c->launches += 2;
     STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
@@ -744,13 +744,13 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double 
       cc.c[i] = c->h_pinned[i] / (alpha[i] * alpha[i]);
       H[i * m + j] = c->h_pinned[i] / (alpha[i] * alpha[j]);
     }
-    axpy_norm<S>(W, V, n, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
+    axpy_norm<S>(W, V, ldv, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
     c->launches += 2;
     STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
     double after = c->h_pinned[0];
     if (c->opts.reorth && after < 0.5 * before) {
-      multidot<S>(W, V, n, j + 1, false, n, c->red_partial, c->red_out, c->stream);
+      multidot<S>(W, V, ldv, j + 1, false, n, c->red_partial, c->red_out, c->stream);
       c->launches += 2;
       STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       STM_CK(cudaStreamSynchronize(c->stream));
@@ -758,7 +758,7 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, S* z, int64_t n, double a0, double 
         cc.c[i] = c->h_pinned[i] / (alpha[i] * alpha[i]);
         H[i * m + j] += c->h_pinned[i] / (alpha[i] * alpha[j]);
       }
-      axpy_norm<S>(W, V, n, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
+      axpy_norm<S>(W, V, ldv, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
       c->launches += 2;
       STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       STM_CK(cudaStreamSynchronize(c->stream));
@@ -1376,12 +1376,14 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   const int64_t qn3 = (int64_t)c->Q * c->N3;
   int rc;
   // FP64 buffers: x (unknowns), z (work / residual); basis in FP64 or FP32
+  // basis columns start on 16-byte (here 512-byte) boundaries for vector loads
+  const int64_t ldv = (n + 63) / 64 * 64;
   if ((rc = ensure_buf<double>(c, &c->x, &c->x_len, n)) || (rc = ensure_buf<double>(c, &c->z, &c->z_len, n))) return rc;
   if (mixed) {
-    if ((rc = ensure_buf<float>(c, &c->V32, &c->V32_len, (m + 1) * n)) ||
+    if ((rc = ensure_buf<float>(c, &c->V32, &c->V32_len, (m + 1) * ldv)) ||
         (rc = ensure_buf<float>(c, &c->z32, &c->z32_len, n)))
       return rc;
-  } else if ((rc = ensure_buf<double>(c, &c->V, &c->V_len, (m + 1) * n))) {
+  } else if ((rc = ensure_buf<double>(c, &c->V, &c->V_len, (m + 1) * ldv))) {
     return rc;
   }
   const double* b = nullptr;
@@ -1415,11 +1417,12 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
     double res = 0.0;
     if (!mixed) {
       // V[0] = R = -r, so v_0 = V[0] / (-beta)
-      if ((rc = gmres_cycle<double>(c, dt, c->V, c->z, n, -beta, tol * ref, c->opts.max_it, &k, &yc, &res, &iters)))
+      if ((rc = gmres_cycle<double>(c, dt, c->V, ldv, c->z, n, -beta, tol * ref, c->opts.max_it, &k, &yc, &res,
+                                    &iters)))
         return rc;
-      if (curved) precond_curved<double, double>(c->x, c->V, n, k, yc.c, c->Pinv64, qn3, c->ne, true, c->stream);
-      else if (c->hp) combine_hp<double, double>(c->x, c->V, n, k, yc, c->inv64, c->off_test, c->pq, c->ne, c->stream);
-      else precond_combine<double, double>(c->x, c->V, n, k, yc, c->inv64, qn3, n, c->stream);
+      if (curved) precond_curved<double, double>(c->x, c->V, ldv, k, yc.c, c->Pinv64, qn3, c->ne, true, c->stream);
+      else if (c->hp) combine_hp<double, double>(c->x, c->V, ldv, k, yc, c->inv64, c->off_test, c->pq, c->ne, c->stream);
+      else precond_combine<double, double>(c->x, c->V, ldv, k, yc, c->inv64, qn3, n, c->stream);
     } else {
       // FP32 inner GMRES(m) cycle on A d = r, started from the rounded FP64 residual;
       // the inner target is the outer one or what FP32 can resolve, whichever is larger
@@ -1429,11 +1432,11 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       if ((rc = norm2<float>(c, c->V32, n, &b32))) return rc;
       b32 = std::sqrt(b32);
       const double tin = std::max(tol * ref, 1e-6 * b32);
-      if ((rc = gmres_cycle<float>(c, dt, c->V32, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
+      if ((rc = gmres_cycle<float>(c, dt, c->V32, ldv, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
         return rc;
-      if (curved) precond_curved<float, double>(c->x, c->V32, n, k, yc.c, c->Pinv32, qn3, c->ne, true, c->stream);
-      else if (c->hp) combine_hp<float, double>(c->x, c->V32, n, k, yc, c->inv32, c->off_test, c->pq, c->ne, c->stream);
-      else precond_combine<float, double>(c->x, c->V32, n, k, yc, c->inv32, qn3, n, c->stream);
+      if (curved) precond_curved<float, double>(c->x, c->V32, ldv, k, yc.c, c->Pinv32, qn3, c->ne, true, c->stream);
+      else if (c->hp) combine_hp<float, double>(c->x, c->V32, ldv, k, yc, c->inv32, c->off_test, c->pq, c->ne, c->stream);
+      else precond_combine<float, double>(c->x, c->V32, ldv, k, yc, c->inv32, qn3, n, c->stream);
     }
     c->launches += 1;
     ++cycles;
