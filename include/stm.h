@@ -184,6 +184,12 @@ int32_t stm_energy(stm_ctx *ctx, double *energy);
 int32_t stm_autotune(stm_ctx *ctx, double dt, int32_t reps, int32_t n_max, int32_t *P, int32_t *Q,
                      int32_t *block, double *ms, int32_t *n_out);
 
+/* Page-locked host buffers for STM_MEM_HOST arguments (the paper has no
+ * counterpart): copies from and to them run at full host-device bandwidth.
+ * stm_host_free releases a buffer from stm_host_alloc. */
+int32_t stm_host_alloc(void **ptr, int64_t bytes);
+int32_t stm_host_free(void *ptr);
+
 /* Number of kernels this context has launched (residual, Krylov, energy). */
 int32_t stm_launch_count(stm_ctx *ctx, int64_t *n);
 

@@ -1582,6 +1582,24 @@ int32_t stm_autotune(stm_ctx* c, double dt, int32_t reps, int32_t n_max, int32_t
   return STM_OK;
 }
 
+int32_t stm_host_alloc(void** ptr, int64_t bytes) {
+  if (!ptr || bytes <= 0) return STM_EINVAL;
+  *ptr = nullptr;
+  if (cudaMallocHost(ptr, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return STM_ENOMEM;
+  }
+  return STM_OK;
+}
+
+int32_t stm_host_free(void* ptr) {
+  if (ptr && cudaFreeHost(ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return STM_EINVAL;
+  }
+  return STM_OK;
+}
+
 int32_t stm_launch_count(stm_ctx* c, int64_t* n) {
   if (!c || !n) return STM_EINVAL;
   *n = c->launches;

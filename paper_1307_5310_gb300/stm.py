@@ -41,7 +41,7 @@ EXPORTS = (
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
     "stm_set_source_gauss", "stm_set_boundary",
     "stm_server_create", "stm_server_submit", "stm_server_poll", "stm_server_wait", "stm_server_stats",
-    "stm_server_destroy", "stm_autotune",
+    "stm_server_destroy", "stm_autotune", "stm_host_alloc", "stm_host_free",
 )
 
 
@@ -131,6 +131,8 @@ def lib() -> C.CDLL:
         L.stm_server_wait.argtypes = [vp, i64, C.POINTER(stm_result), vp]
         L.stm_server_stats.argtypes = [vp, C.POINTER(stm_stats)]
         L.stm_server_destroy.argtypes = [vp]
+        L.stm_host_alloc.argtypes = [C.POINTER(vp), i64]
+        L.stm_host_free.argtypes = [vp]
         L.stm_autotune.argtypes = [vp, d, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(d),
                                    C.POINTER(i32)]
         for name in EXPORTS:
@@ -153,6 +155,27 @@ def residual_apply_noalloc(n_elem, p, q, dt, nbr, h, eps, mu, U, R, stream=None)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     return lib().stm_residual_apply_noalloc(n_elem, p, q, dt, *args, int(stream))
+
+
+class HostBuffer:
+    """Page-locked host array from stm_host_alloc (numpy view in .array)."""
+
+    def __init__(self, n, dtype=np.float64):
+        dtype = np.dtype(dtype)
+        p = C.c_void_p()
+        rc = lib().stm_host_alloc(C.byref(p), int(n) * dtype.itemsize)
+        if rc != STM_OK:
+            raise StmError(rc, "stm_host_alloc failed")
+        self._p = p
+        self.array = np.ctypeslib.as_array(C.cast(p, C.POINTER(np.ctypeslib.as_ctypes_type(dtype))), shape=(int(n),))
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self.array = None
+            lib().stm_host_free(self._p)
+            self._p = None
+
+    __del__ = close
 
 
 class StmError(RuntimeError):
