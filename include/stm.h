@@ -103,6 +103,11 @@ typedef struct {
   int32_t graph;         /* 1: on meshes with several (p, q) classes or 2:1 faces,
                             capture each residual apply (all launches) once in a
                             CUDA graph per (buffers, dt) and replay it             */
+  double eta_tol;        /* > 0: inexact solve (Sec. 5.3, brick meshes): a slab
+                            stops once its share of the guaranteed iteration-error
+                            bound eta_it of Eq. a_posteriori:iteration is at most
+                            eta_tol / sqrt(t_final / dt); tol is then unused       */
+  double t_final;        /* final time t_N of the bound (inexact solve)             */
 } stm_opts;
 
 typedef struct {
@@ -110,6 +115,9 @@ typedef struct {
   int32_t restarts;        /* restart cycles (outer refinements in STM_MIXED)    */
   double rel_residual;     /* final ||R(U)||_2 / ||R(U^(0))||_2, FP64            */
   double energy;           /* discrete energy at the slab end (Eq. stability:energydef) */
+  double eta2;             /* inexact solve: this slab's term of eta_it^2, i.e.
+                              4 c_E |R_E|^2_{W'} + 4 c_H |R_H|^2_{W'} at the
+                              returned iterate (sum over slabs = eta_it^2)          */
 } stm_solve_report;
 
 /* Create a context on the current CUDA device.  Validates the mesh, copies

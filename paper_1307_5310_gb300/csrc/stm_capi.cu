@@ -158,6 +158,11 @@ struct stm_ctx {
   stm_opts opts{};
   std::string err;
   std::vector<double> h_x0, h_h, h_mass;  // [ne][3], [ne][3], [ne][6]
+  std::vector<double> h_eps, h_mu;         // [ne]
+  // inexact solve (Sec. 5.3): per (element, field, component) weights sqrt(4 c_f / (dt G_c))
+  double* sw64 = nullptr;
+  float* sw32 = nullptr;
+  double sw_dt = 0.0;
   int32_t* nbr = nullptr;
   double* mass64 = nullptr;
   float* mass32 = nullptr;
@@ -715,6 +720,54 @@ int norm2(stm_ctx* c, S* v, int64_t n, double* out) {
 // drops below 1/sqrt(2) of its value before the update.  Returns the number k
 // of basis vectors used and the coefficients yc[i] such that the correction
 // is P^{-1} sum_{i<k} yc[i] V[i]; *res is the residual norm estimate |g_k|.
+// Weights of the iteration-error bound of Sec. 5.3 (Eq. a_posteriori:iteration):
+// eta_it^2 = 4 sum_n [(2 t_N/eps_min + dt^2/(2 t_N eps_min)) |R_E|^2_{W'} + (same, mu) |R_H|^2_{W'}],
+// with the dual norm on the test space |R|^2_{W'} = R^T M_W^{-1} R and, on
+// bricks, M_W = dt diag(G_c) (orthonormal test basis in time and space).  So
+// eta-contribution^2 of a slab = |S R|_2^2 with S = diag(sqrt(4 c_f / (dt G_c))).
+int build_eta_weights(stm_ctx* c, double dt) {
+  if (c->sw64 && c->sw_dt == dt) return STM_OK;
+  const double emin = *std::min_element(c->h_eps.begin(), c->h_eps.end());
+  const double mmin = *std::min_element(c->h_mu.begin(), c->h_mu.end());
+  const double tN = c->opts.t_final;
+  const double cf[2] = {2 * tN / emin + dt * dt / (2 * tN * emin), 2 * tN / mmin + dt * dt / (2 * tN * mmin)};
+  std::vector<double> w(6 * c->ne);
+  std::vector<float> w32(6 * c->ne);
+  for (int64_t e = 0; e < c->ne; ++e)
+    for (int fc = 0; fc < 6; ++fc) {
+      const double mat = fc < 3 ? c->h_eps[e] : c->h_mu[e];
+      const double G = c->h_mass[6 * e + fc] / mat;
+      w[6 * e + fc] = std::sqrt(4.0 * cf[fc / 3] / (dt * G));
+      w32[6 * e + fc] = (float)w[6 * e + fc];
+    }
+  if (!c->sw64) {
+    if (cudaMalloc(&c->sw64, w.size() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->sw32, w32.size() * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, STM_ENOMEM, "weight allocation failed");
+    }
+  }
+  STM_CK(cudaMemcpy(c->sw64, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  STM_CK(cudaMemcpy(c->sw32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  c->sw_dt = dt;
+  return STM_OK;
+}
+
+template <typename S>
+const S* sw_ptr(stm_ctx* c);
+template <>
+const double* sw_ptr<double>(stm_ctx* c) { return c->sw64; }
+template <>
+const float* sw_ptr<float>(stm_ctx* c) { return c->sw32; }
+
+// v <- S v (per-block weights), in place
+template <typename S>
+void scale_blocks(stm_ctx* c, S* v, const S* w, int64_t n) {
+  if (c->hp) precond_hp<S>(v, v, w, c->off_test, c->pq, c->ne, c->stream);
+  else precond_apply<S>(v, v, w, (int64_t)c->Q * c->N3, n, c->stream);
+  c->launches += 1;
+}
+
 template <typename S>
 int gmres_cycle(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n, double a0, double tol_abs, int max_iters,
                 int* k_out, Coef16* yc, double* res, int* iters) {
@@ -734,6 +787,7 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n, doubl
       precond_apply<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), qn3, n, c->stream);
     c->launches += 1;
     if ((rc = linop<S>(c, dt, z, W))) return rc;
+    if (c->opts.eta_tol > 0) scale_blocks<S>(c, W, sw_ptr<S>(c), n);  // residual space weighted by S
     multidot<S>(W, V, ldv, j + 1, true, n, c->red_partial, c->red_out, c->stream);
     c->launches += 2;
     STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -894,6 +948,8 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       for (int d = 0; d < 3; ++d) c->h_X8[24 * e + 3 * v + d] = m->vert[3 * hv[v] + d];
     }
     if (!(m->eps[e] > 0) || !(m->mu[e] > 0)) return bad(STM_EINVAL, "eps and mu must be positive");
+    c->h_eps.push_back(m->eps[e]);
+    c->h_mu.push_back(m->mu[e]);
     const double* v0 = m->vert + 3 * hv[0];
     const double* v7 = m->vert + 3 * hv[7];
     double h[3];
@@ -1192,7 +1248,8 @@ int32_t stm_destroy(stm_ctx* c) {
   void* ptrs[] = {c->nbr,     c->mass64,  c->mass32, c->y64,   c->tr64, c->y32, c->tr32,
                   c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
-                  c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32};
+                  c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
+                  c->sw64,    c->sw32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1400,24 +1457,48 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   else k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
   c->launches += 1;
   int iters = 0, cycles = 0;
-  double rel = 0.0;
+  double rel = 0.0, phi = 0.0;
   const double tol = c->opts.tol;
+  // inexact solve: stop when this slab's share of eta_it (Sec. 5.3) is below eta_tol / sqrt(slabs)
+  const bool inexact = c->opts.eta_tol > 0;
+  double budget = 0.0;
+  if (inexact) {
+    if (curved) return fail(c, STM_EUNSUPPORTED, "the inexact solve is built for brick meshes");
+    for (const auto& k : c->classes)  // the bound needs one temporal degree everywhere
+      if (k.Q != c->classes[0].Q) return fail(c, STM_EUNSUPPORTED, "the inexact solve needs a uniform q");
+    if (!(c->opts.t_final > 0)) return fail(c, STM_EINVAL, "opts.t_final must be positive for the inexact solve");
+    if ((rc = build_eta_weights(c, dt))) return rc;
+    const double nslab = std::max(1.0, std::round(c->opts.t_final / dt));
+    budget = c->opts.eta_tol / std::sqrt(nslab);
+  }
+  bool done = false;
   for (;;) {
     // true FP64 residual R(u0, x)
     double* R64 = mixed ? c->z : c->V;
     if ((rc = resid64(c, dt, c->x, b, R64))) return rc;
     double beta2;
     if ((rc = norm2<double>(c, R64, n, &beta2))) return rc;
-    const double beta = std::sqrt(beta2);
+    double beta = std::sqrt(beta2);
     rel = ref > 0 ? beta / ref : beta;
     if (!std::isfinite(rel)) return fail(c, STM_ENAN, "non-finite residual in slab solve");
-    if (rel <= tol || iters >= c->opts.max_it || beta == 0.0) break;
+    if (inexact) {
+      scale_blocks<double>(c, R64, c->sw64, n);
+      double p2;
+      if ((rc = norm2<double>(c, R64, n, &p2))) return rc;
+      phi = std::sqrt(p2);
+      beta = phi;  // GMRES works on the weighted residual S R
+      done = phi <= budget;
+    } else {
+      done = rel <= tol;
+    }
+    if (done || iters >= c->opts.max_it || beta == 0.0) break;
+    const double cyc_tol = inexact ? budget : tol * ref;
     int k = 0;
     Coef16 yc{};
     double res = 0.0;
     if (!mixed) {
       // V[0] = R = -r, so v_0 = V[0] / (-beta)
-      if ((rc = gmres_cycle<double>(c, dt, c->V, ldv, c->z, n, -beta, tol * ref, c->opts.max_it, &k, &yc, &res,
+      if ((rc = gmres_cycle<double>(c, dt, c->V, ldv, c->z, n, -beta, cyc_tol, c->opts.max_it, &k, &yc, &res,
                                     &iters)))
         return rc;
       if (curved) precond_curved<double, double>(c->x, c->V, ldv, k, yc.c, c->Pinv64, qn3, c->ne, true, c->stream);
@@ -1431,7 +1512,7 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       double b32;
       if ((rc = norm2<float>(c, c->V32, n, &b32))) return rc;
       b32 = std::sqrt(b32);
-      const double tin = std::max(tol * ref, 1e-6 * b32);
+      const double tin = std::max(cyc_tol, 1e-6 * b32);
       if ((rc = gmres_cycle<float>(c, dt, c->V32, ldv, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
         return rc;
       if (curved) precond_curved<float, double>(c->x, c->V32, ldv, k, yc.c, c->Pinv32, qn3, c->ne, true, c->stream);
@@ -1454,8 +1535,9 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
     rep->restarts = cycles;
     rep->rel_residual = rel;
     rep->energy = en;
+    rep->eta2 = inexact ? phi * phi : 0.0;
   }
-  return rel <= tol ? STM_OK : STM_ENOTCONV;
+  return done ? STM_OK : STM_ENOTCONV;
 }
 
 int32_t stm_set_source_gauss(stm_ctx* c, const stm_gauss_src* src, int32_t n_src) {
