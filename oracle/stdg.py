@@ -14,6 +14,11 @@ paper's definitions literally:
 * the stabilisation S_h of Eq. bilinearform:S on interior faces whose two
   elements have different temporal degrees, with the projector onto the
   common temporal test space computed as an L2 projection by quadrature;
+* optionally the dissipative (upwind-type) term of Sec. 4.2,
+      D_h(U, V) = <alpha_E [E]_T, [Pi~ v]_T>_{F0} + <alpha_E [E - g]_T, [v]_T>_{Fb}
+                  + <alpha_H [H]_T, [Pi~ w]_T>_{F0},
+  alpha_E = c / {sqrt(mu/eps)}, alpha_H = c / {sqrt(eps/mu)}, c >= 0
+  (``c_diss``; on a boundary face the average is the element's own value);
 * the load L(V) = (J, v) - <n x g, w>_{Fb} and the residual
   R_h(V) = B_h(U, V) - L(V) (Eq. residual).
 
@@ -206,7 +211,8 @@ class Oracle:
     mesh: dict with vert [nv,3], hex [ne,8], p [ne], q [ne], eps [ne], mu [ne].
     """
 
-    def __init__(self, mesh: dict):
+    def __init__(self, mesh: dict, c_diss: float = 0.0):
+        self.c_diss = float(c_diss)
         self.vert = np.asarray(mesh["vert"], dtype=np.float64)
         self.hex = np.asarray(mesh["hex"], dtype=np.int64)
         self.ne = self.hex.shape[0]
@@ -408,6 +414,17 @@ class Oracle:
             # H-eq: -<[E]_T, {w}> , {w} = w / 2
             RH = _test_project(-0.5 * jE, pts, Lt, wgt)
             qt = min(q, q2)
+            if self.c_diss > 0:
+                # D_h: <alpha [F]_T, [Pi~ v]_T>; for the rows of e, [v]_T = n x v, and
+                # a . (n x v) = v . (a x n)
+                aE = self.c_diss / (0.5 * (np.sqrt(self.mu[e] / self.eps[e]) + np.sqrt(self.mu[e2] / self.eps[e2])))
+                aH = self.c_diss / (0.5 * (np.sqrt(self.eps[e] / self.mu[e]) + np.sqrt(self.eps[e2] / self.mu[e2])))
+                Lp = Lt
+                if qt < q:
+                    Lq_ = basis.legendre(qt - 1, tau)
+                    Lp = np.einsum("ik,kt->it", np.einsum("kt,t,it->ik", Lq_, wt, Lt), Lq_)  # Pi~ L_i
+                RE = RE + aE * _test_project(_cross(jE, nn), pts, Lp, wgt)
+                RH = RH + aH * _test_project(_cross(jH, nn), pts, Lp, wgt)
             if qt < q:
                 # S_h: test factors (Pi~ L_i - L_i) with Pi~ the L2 projection onto P_{qt-1}
                 Lq = basis.legendre(qt - 1, tau)
@@ -421,11 +438,17 @@ class Oracle:
             # boundary: {H} = H, [v]_T = n x v ; [E]_T = n x E, {w} = w
             RE = _test_project(_cross(H1, nn), pts, Lt, wgt)
             RH = _test_project(-_cross(nn, E1), pts, Lt, wgt)
+            gv = None
             if g is not None:
                 # -l_H(w) = + <n x g, w>
                 t = t0 + dt * tau
                 gv = g(pts.x[None, :, :], t[:, None])  # [T, A, 3]
                 RH = RH + _test_project(_cross(nn, gv[None]), pts, Lt, wgt)
+            if self.c_diss > 0:
+                # D_h on F_b: <alpha_E n x (E - g), n x v>, alpha_E = c / sqrt(mu/eps) of e
+                aE = self.c_diss / np.sqrt(self.mu[e] / self.eps[e])
+                jb = _cross(nn, E1 if gv is None else E1 - gv[None])
+                RE = RE + aE * _test_project(_cross(jb, nn), pts, Lt, wgt)
         return np.stack([RE, RH], axis=1)
 
     # -- public API ------------------------------------------------------------

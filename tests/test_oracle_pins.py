@@ -172,6 +172,67 @@ def test_two_cube_p0_closed_form():
         assert np.abs(R[k, 1] - RH).max() < 1e-14
 
 
+def test_two_cube_p0_dissipation_closed_form():
+    """D_h (Sec. 4.2) on two unit cubes, p = 0, q = 1, by hand: the E rows of
+    component d collect alpha dt (mean E jump)_d over every face tangential to
+    d (boundary faces: alpha_E = c sqrt(eps/mu) of the element, jump = E), the
+    H rows only the interior face."""
+    m = meshgen.box_mesh(2, 1, 1, hi=(2.0, 1.0, 1.0), p=0, q=1)
+    m["eps"] = np.array([2.0, 3.0])
+    m["mu"] = np.array([1.5, 0.5])
+    c = 0.7
+    o, o0 = stdg.Oracle(m, c_diss=c), stdg.Oracle(m)
+    rng = np.random.Generator(np.random.PCG64(4))
+    U = rng.uniform(-1, 1, o.trial_off[-1])
+    dt = 0.29
+    D = (o.residual(U, 0.0, dt) - o0.residual(U, 0.0, dt)).reshape(2, 2, 3)
+    u = U.reshape(2, 2, 3, 2)
+    Ebar = 0.5 * (u[:, 0, :, 0] + u[:, 0, :, 1])
+    Hbar = 0.5 * (u[:, 1, :, 0] + u[:, 1, :, 1])
+    eps, mu = m["eps"], m["mu"]
+    aE = c / (0.5 * (np.sqrt(mu[0] / eps[0]) + np.sqrt(mu[1] / eps[1])))
+    aH = c / (0.5 * (np.sqrt(eps[0] / mu[0]) + np.sqrt(eps[1] / mu[1])))
+    quad = 0.0
+    for k in (0, 1):
+        ab = c * np.sqrt(eps[k] / mu[k])
+        nb = np.array([4, 3, 3])  # boundary faces tangential to x, y, z
+        DE = ab * dt * nb * Ebar[k]
+        DH = np.zeros(3)
+        for d in (1, 2):  # tangential to the shared x-face
+            DE[d] += aE * dt * (Ebar[k, d] - Ebar[1 - k, d])
+            DH[d] += aH * dt * (Hbar[k, d] - Hbar[1 - k, d])
+        assert np.abs(D[k, 0] - DE).max() < 1e-14
+        assert np.abs(D[k, 1] - DH).max() < 1e-14
+        quad += ab * dt * float(nb @ Ebar[k] ** 2)
+    jE, jH = Ebar[0, 1:] - Ebar[1, 1:], Hbar[0, 1:] - Hbar[1, 1:]
+    quad += aE * dt * float(jE @ jE) + aH * dt * float(jH @ jH)
+    # dissipation identity: R(U) . Pi U = E(t1) - E(t0) + D(U, Pi U), the last a sum of squares
+    lhs = o.residual(U, 0.0, dt) @ o.test_projection_in_time(U)
+    dE = o.energy(o.end_state(U)) - o.energy(o.start_state(U))
+    assert abs(lhs - dE - quad) < 1e-13
+
+
+@pytest.mark.parametrize("case", ["brick", "uneven_q", "uneven_p"])
+def test_dissipation_nonnegative(case):
+    """With c > 0 the energy identity gains -D(U, Pi U) <= 0, linear in c."""
+    m = meshgen.box_mesh(2, p=2, q=2)
+    if case == "uneven_q":
+        m["q"] = np.array([1, 2, 3, 1, 2, 3, 4, 1], dtype=np.uint8)
+    elif case == "uneven_p":
+        m["p"] = np.array([1, 2, 3, 1, 2, 3, 1, 2], dtype=np.uint8)
+    meshgen.random_materials(m, 5, 6)
+    U = meshgen.random_coeffs(m, 11)
+    dt = 0.13
+    out = []
+    for c in (0.0, 0.5, 1.0):
+        o = stdg.Oracle(m, c_diss=c)
+        piU = o.test_projection_in_time(U)
+        dE = o.energy(o.end_state(U)) - o.energy(o.start_state(U))
+        out.append(o.residual(U, 0.0, dt) @ piU - dE)
+    assert abs(out[0]) <= 1e-12 * max(1.0, abs(out[2]))
+    assert out[1] > 0 and abs(out[2] - 2 * out[1]) <= 1e-11 * out[2]
+
+
 # --------------------------------------------------------------------------
 # P4: discrete energy identity for arbitrary U (Theorems 3.1 / 4.1)
 # --------------------------------------------------------------------------
@@ -244,8 +305,8 @@ def test_patch_hanging():
 # P6: polynomial patch test E = (0,0,x), H = (0,t,0), g = E
 # --------------------------------------------------------------------------
 
-def _patch(m, t0=0.3, dt=0.2):
-    o = stdg.Oracle(m)
+def _patch(m, t0=0.3, dt=0.2, c_diss=0.0):
+    o = stdg.Oracle(m, c_diss=c_diss)
 
     def Ef(x):
         z = np.zeros(x.shape[0])
@@ -290,6 +351,19 @@ def test_patch_exact(case):
     assert np.abs(R).max() < 1e-12
     Us = o.slab_solve(u0, t0, dt, g=g)
     assert np.abs(Us - U).max() < 1e-11
+
+
+@pytest.mark.parametrize("case", ["brick", "uneven"])
+def test_patch_exact_dissipative(case):
+    """D_h vanishes on a solution with continuous tangential traces and E = g on F_b."""
+    m = meshgen.box_mesh(2, 2, 1, p=1, q=1) if case == "brick" else meshgen.box_mesh(2, p=2, q=2)
+    if case == "uneven":
+        m["p"] = np.array([1, 2, 1, 2, 2, 1, 2, 1], dtype=np.uint8)
+        m["q"] = np.array([2, 3, 4, 2, 3, 2, 2, 3], dtype=np.uint8)
+    o, U, u0, g, t0, dt = _patch(m, c_diss=0.8)
+    assert np.abs(o.residual(U, t0, dt, g=g)).max() < 1e-12
+    # without the boundary data the E - g term of D_h is what remains on F_b
+    assert np.abs(o.residual(U, t0, dt)).max() > 1e-3
 
 
 def test_patch_time_constant_uneven_q():
