@@ -108,6 +108,11 @@ typedef struct {
                             bound eta_it of Eq. a_posteriori:iteration is at most
                             eta_tol / sqrt(t_final / dt); tol is then unused       */
   double t_final;        /* final time t_N of the bound (inexact solve)             */
+  double c_diss;         /* >= 0: adds the dissipative upwind term D_h of Sec. 4.2
+                            with alpha_E = c/{sqrt(mu/eps)}, alpha_H = c/{sqrt(eps/mu)}
+                            (0: the non-dissipative method).  Brick meshes with one
+                            q and no 2:1 faces; else stm_create returns
+                            STM_EUNSUPPORTED                                        */
 } stm_opts;
 
 typedef struct {

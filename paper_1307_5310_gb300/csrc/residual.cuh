@@ -78,6 +78,11 @@ struct ApplyArgs {
   const int32_t* hslot = nullptr;
   const int64_t* hoff = nullptr;
   const T* hbuf = nullptr;
+  // dissipative term D_h (Sec. 4.2), or nullptr: kap[e][field][face][tangential comp] =
+  // alpha (c / {Z} for E, c / {Y} for H; E on PEC faces c / Z_K, H there 0) times the
+  // brick's face factor h_b / h_c; scaled by dt_k at apply time
+  const T* kap = nullptr;
+  T dt_k = T(0);
 };
 
 // Element-local addressing of one element of class (P, Q).
@@ -290,14 +295,38 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
 #pragma unroll
           for (int j = 0; j < N; ++j) yv[j] = flip_sign(yl[j * stride], flip);
           T* Rl = Rs + fl * FB + (c * Q + i) * N3 + base;
+          if (A.kap) {
+            // D_h: alpha-weighted jumps of component c of the same field f on the two
+            // faces normal to a, lifted with L_al(1) and L_al(0) = (-1)^al L_al(1);
+            // on a PEC face the E jump is the own trace (E - g, g in the load)
+            const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
+            const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * Q + i;
+            const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * Q) * N2 + t];
+            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP>(A, ep, 0, f, a, bc, i, t) : (f == 0 ? zp : T(0));
+            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP>(A, em, 1, f, a, bc, i, t) : (f == 0 ? zm : T(0));
+            const T* kp = A.kap + e * 24 + f * 12 + 4 * a + bc;
+            const T dp = A.dt_k * kp[2] * gp, dn = A.dt_k * kp[0] * gm;
+            // the central-flux lift hf[al] = (dt/2) lv[al] shares the factor lv[al]
+            const T zev = fma(-A.tb.hf[0], dm, dp + dn), zod = fma(-A.tb.hf[0], sp, dp - dn);
 #pragma unroll
-          for (int al = 0; al < N; ++al) {
-            T r2 = Rl[al * stride];
-            r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
+            for (int al = 0; al < N; ++al) {
+              T r2 = Rl[al * stride];
+              r2 = fma(A.tb.lv[al], (al & 1) ? zod : zev, r2);
 #pragma unroll
-            for (int be = 0; be < N; ++be)
-              if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
-            Rl[al * stride] = r2;
+              for (int be = 0; be < N; ++be)
+                if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
+              Rl[al * stride] = r2;
+            }
+          } else {
+#pragma unroll
+            for (int al = 0; al < N; ++al) {
+              T r2 = Rl[al * stride];
+              r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+              for (int be = 0; be < N; ++be)
+                if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
+              Rl[al * stride] = r2;
+            }
           }
         }
         __syncthreads();
@@ -481,7 +510,7 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   (void)configured;
   const bool hp = args.elist != nullptr;
   if constexpr (sizeof(T) == 4) {
-    if (!hp) {
+    if (!hp && !args.kap) {
       // single pass: ev.start/ev.stop bracket k_fused (reported in the apply slot)
       if (ev.start) cudaEventRecord(ev.start, s);
       if (ev.mid) cudaEventRecord(ev.mid, s);

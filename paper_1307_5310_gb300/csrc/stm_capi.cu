@@ -159,6 +159,10 @@ struct stm_ctx {
   std::string err;
   std::vector<double> h_x0, h_h, h_mass;  // [ne][3], [ne][3], [ne][6]
   std::vector<double> h_eps, h_mu;         // [ne]
+  // dissipative term D_h (Sec. 4.2): per element [field][face][tangential comp] coefficients
+  double* kap64 = nullptr;
+  float* kap32 = nullptr;
+  std::vector<double> h_kap;
   // inexact solve (Sec. 5.3): per (element, field, component) weights sqrt(4 c_f / (dt G_c))
   double* sw64 = nullptr;
   float* sw32 = nullptr;
@@ -365,9 +369,15 @@ int record_events(stm_ctx* c, LaunchEvents& ev) {
 // the trial layout (um_layout = L_TRIAL, mode 0 skipped) or the test layout;
 // u0 is mode 0 (trial layout or a state vector) or null; b is the load or null.
 template <typename T>
+const T* kap_ptr(stm_ctx* c) {
+  if constexpr (sizeof(T) == 8) return c->kap64;
+  else return c->kap32;
+}
+
+template <typename T>
 int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R) {
   T *y = nullptr, *tr = nullptr;
-  if (sizeof(T) == 8 || c->hp) {  // the uniform FP32 kernel is single-pass and needs no scratch
+  if (sizeof(T) == 8 || c->hp || c->kap64) {  // the uniform FP32 kernel is single-pass and needs no scratch
     int rc = scratch<T>(c, &y, &tr);
     if (rc) return rc;
   }
@@ -378,6 +388,8 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   a.R = R;
   a.nbr = c->nbr;
   a.mass = mass_ptr<T>(c);
+  a.kap = kap_ptr<T>(c);
+  a.dt_k = (T)dt;
   const int N3 = c->N3, Q = c->Q;
   if (c->hp) {
     a.um = um;
@@ -611,6 +623,26 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
               ng[1] = nv[2] * gh[0] - nv[0] * gh[2];
               ng[2] = nv[0] * gh[1] - nv[1] * gh[0];
               const double w = dt * wt[tq] * wq[u] * wq[v];
+              if (c->opts.c_diss > 0) {
+                // D_h on F_b: the g part of <alpha_E n x (E - g), n x v> moves into the load
+                for (int bc = 0; bc < 2; ++bc) {
+                  const int cc = (d == 0) ? bc + 1 : (d == 1 ? 2 * bc : bc);
+                  const double kg = c->h_kap[e * 24 + f * 2 + bc] * gh[cc];
+                  for (int i = 0; i < Q; ++i) {
+                    const double wi = w * Lt[tq * kMaxQ + i] * kg;
+                    double* row = &hb[((e * 2 + 0) * 3 + cc) * (int64_t)Q * N3 + (int64_t)i * N3];
+                    for (int al = 0; al < N; ++al)
+                      for (int j1 = 0; j1 < N; ++j1)
+                        for (int j2 = 0; j2 < N; ++j2) {
+                          int idx[3];
+                          idx[d] = al;
+                          idx[a1] = j1;
+                          idx[a2] = j2;
+                          row[(idx[2] * N + idx[1]) * N + idx[0]] += wi * Lside[al] * Lq[u * N + j1] * Lq[v * N + j2];
+                        }
+                  }
+                }
+              }
               for (int cc = 0; cc < 3; ++cc) {
                 if (ng[cc] == 0.0) continue;
                 for (int i = 0; i < Q; ++i) {
@@ -898,6 +930,14 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     if (m->nbr[k] == -2) c->hp = true;  // 2:1 faces run through the per-element-offset kernels
   if (c->hp && m->geometry != STM_GEOM_BRICK)
     return bad(STM_EUNSUPPORTED, "uneven (p, q) and 2:1 faces are handled on brick meshes only");
+  if (o && o->c_diss != 0.0) {
+    if (!(o->c_diss > 0)) return bad(STM_EINVAL, "c_diss must be >= 0");
+    if (m->geometry != STM_GEOM_BRICK) return bad(STM_EUNSUPPORTED, "the dissipative term is built for brick meshes");
+    for (int64_t e = 0; e < c->ne; ++e)
+      if (m->q[e] != c->Q) return bad(STM_EUNSUPPORTED, "the dissipative term needs a uniform q");
+    for (int64_t k = 0; k < 6 * c->ne; ++k)
+      if (m->nbr[k] == -2) return bad(STM_EUNSUPPORTED, "the dissipative term is not built for 2:1 faces");
+  }
   if (m->n_hang < 0 || (m->n_hang > 0 && !m->hang)) return bad(STM_EINVAL, "bad hang list");
   if (m->geometry != STM_GEOM_BRICK && m->geometry != STM_GEOM_TRILINEAR) return bad(STM_EINVAL, "unknown geometry");
   const bool curved = m->geometry == STM_GEOM_TRILINEAR;
@@ -1232,6 +1272,44 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       return STM_ENOMEM;
     }
   }
+  if (c->opts.c_diss > 0) {
+    // D_h coefficients: alpha_E = c / {sqrt(mu/eps)}, alpha_H = c / {sqrt(eps/mu)} on interior
+    // faces; alpha_E = c sqrt(eps/mu) of the element and no H term on PEC faces.  On a brick the
+    // tangential product <E_c, v_c> over a face normal to a is (h_b / h_c) times the reference one.
+    std::vector<double> k64(24 * c->ne);
+    for (int64_t e = 0; e < c->ne; ++e) {
+      const double Ze = std::sqrt(c->h_mu[e] / c->h_eps[e]);
+      for (int face = 0; face < 6; ++face) {
+        const int a = face / 2;
+        const int32_t e2 = c->h_nbr[6 * e + face];
+        double al[2];
+        if (e2 >= 0) {
+          const double Z2 = std::sqrt(c->h_mu[e2] / c->h_eps[e2]);
+          al[0] = c->opts.c_diss / (0.5 * (Ze + Z2));
+          al[1] = c->opts.c_diss / (0.5 * (1.0 / Ze + 1.0 / Z2));
+        } else {
+          al[0] = c->opts.c_diss / Ze;
+          al[1] = 0.0;
+        }
+        for (int bc = 0; bc < 2; ++bc) {
+          const int cc = (a == 0) ? bc + 1 : (a == 1 ? 2 * bc : bc), bb = 3 - a - cc;
+          const double geo = c->h_h[3 * e + bb] / c->h_h[3 * e + cc];
+          for (int f = 0; f < 2; ++f) k64[e * 24 + f * 12 + face * 2 + bc] = al[f] * geo;
+        }
+      }
+    }
+    std::vector<float> k32(k64.begin(), k64.end());
+    c->h_kap = k64;
+    if (cudaMalloc(&c->kap64, k64.size() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->kap32, k32.size() * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      stm_destroy(c);
+      fprintf(stderr, "stm_create: allocation of the dissipation coefficients failed\n");
+      return STM_ENOMEM;
+    }
+    cudaMemcpy(c->kap64, k64.data(), k64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->kap32, k32.data(), k32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (curved) {  // the diagonal brick factors do not apply
     cudaFree(c->mass64);
     cudaFree(c->mass32);
@@ -1249,7 +1327,7 @@ int32_t stm_destroy(stm_ctx* c) {
                   c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
                   c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
-                  c->sw64,    c->sw32};
+                  c->sw64,    c->sw32,    c->kap64,  c->kap32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);

@@ -59,7 +59,7 @@ class stm_mesh(C.Structure):
 class stm_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32),
                 ("deterministic", C.c_int32), ("stream", C.c_int64), ("reorth", C.c_int32), ("graph", C.c_int32),
-                ("eta_tol", C.c_double), ("t_final", C.c_double)]
+                ("eta_tol", C.c_double), ("t_final", C.c_double), ("c_diss", C.c_double)]
 
 
 class stm_solve_report(C.Structure):
@@ -210,7 +210,8 @@ class Slab:
     """One library context for a mesh (see include/stm.h)."""
 
     def __init__(self, mesh: dict, precision=STM_FP64, tol=1e-12, restart=10, max_it=500,
-                 deterministic=True, stream=None, reorth=True, graph=True, eta_tol=0.0, t_final=0.0):
+                 deterministic=True, stream=None, reorth=True, graph=True, eta_tol=0.0, t_final=0.0,
+                 c_diss=0.0):
         L = lib()
         self._keep = {}
         ne = mesh["hex"].shape[0]
@@ -240,7 +241,7 @@ class Slab:
 
             stream = torch.cuda.current_stream().cuda_stream
         o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream), 1 if reorth else 0,
-                     1 if graph else 0, eta_tol, t_final)
+                     1 if graph else 0, eta_tol, t_final, c_diss)
         h = C.c_void_p()
         rc = L.stm_create(C.byref(h), C.byref(m), C.byref(o))
         if rc != STM_OK:
