@@ -28,9 +28,19 @@ elements of different degree: the larger of the two).  Physical fields are
 obtained from reference fields through DF^{-T} (values) and (1/J) DF (curl,
 the Piola identity, checked against finite differences in the tests).
 
+Local refinement in time (Sec. 2.2, Sec. 4.1): element K may split the slab
+into N_K equal sub-intervals I_k^K (``mesh["nk"]``, default 1).  The trial
+space is continuous piecewise P_q in time, the test space discontinuous
+piecewise P_{q-1}; on a face whose two elements have different temporal test
+spaces, S_h projects onto their intersection (piecewise P_{min(q)-1} on the
+coarser partition), computed by quadrature on the finer partition.
+
 Coefficient layout of one element (trial): [field E,H][component x,y,z]
-[temporal mode m = 0..q][spatial index s], s = (l (p+1) + k)(p+1) + j with j
-the x^ degree.  Test/residual layout: the same with modes i = 0..q-1.
+[temporal index M][spatial index s], s = (l (p+1) + k)(p+1) + j with j the x^
+degree, M = 0 the slab-start coefficient u_0 and M = 1 + k q + (m - 1) the
+mode m >= 1 of sub-interval k (mode 0 of sub-interval k > 0 is mode 1 of
+sub-interval k - 1: continuity).  With N_K = 1 this is [mode m = 0..q].
+Test/residual layout: [field][component][k q + i][s], i = 0..q-1.
 
 Face neighbours are found from the element-to-vertex lists (shared vertex
 quadruples); the neighbour's reference coordinates of every face quadrature
@@ -150,10 +160,47 @@ def _points(X8, p, xh) -> _Pts:
     return _Pts(xh, geometry.map_points(X8, xh), DF, np.linalg.inv(DF), J, phi, gphi)
 
 
-def _fields(u, pts: _Pts, q: int, tau: np.ndarray, dt: float, derivs: bool = True):
+def _sub_of(nk: int, tau: np.ndarray):
+    """Sub-interval index and local coordinate of slab times tau in [0, 1]."""
+    k = np.minimum(np.floor(tau * nk).astype(np.int64), nk - 1)
+    return k, tau * nk - k
+
+
+def trial_time_nk(q: int, nk: int, tau: np.ndarray, deriv: bool = False) -> np.ndarray:
+    """[N_K q + 1, T] factors of the trial coefficients (layout above) at slab times tau;
+    with ``deriv`` the derivative d/dxi, xi = (t - t0)/dt the slab coordinate."""
+    k, s = _sub_of(nk, tau)
+    lt = basis.trial_time_deriv(q, s) * nk if deriv else basis.trial_time(q, s)  # [q+1, T]
+    out = np.zeros((nk * q + 1, tau.size))
+    cols = np.arange(tau.size)
+    out[np.where(k == 0, 0, 1 + (k - 1) * q), cols] += lt[0]
+    for m in range(1, q + 1):
+        out[1 + k * q + m - 1, cols] += lt[m]
+    return out
+
+
+def test_time_nk(q: int, nk: int, tau: np.ndarray) -> np.ndarray:
+    """[N_K q, T]: L_i on sub-interval k (row k q + i), zero outside it."""
+    k, s = _sub_of(nk, tau)
+    L = basis.legendre(q - 1, s)
+    out = np.zeros((nk * q, tau.size))
+    cols = np.arange(tau.size)
+    for i in range(q):
+        out[k * q + i, cols] = L[i]
+    return out
+
+
+def time_rule(q: int, nk: int):
+    """Gauss rule with q+2 points on each of nk equal sub-intervals of [0, 1]."""
+    x, w = basis.gauss01(q + 2)
+    tau = ((np.arange(nk)[:, None] + x[None, :]) / nk).ravel()
+    return tau, np.tile(w / nk, nk)
+
+
+def _fields(u, pts: _Pts, q: int, tau: np.ndarray, dt: float, derivs: bool = True, nk: int = 1):
     """Physical E (or H) values, time derivative and curl at (tau x points).
 
-    u: [B, 3, q+1, N3] trial coefficients of one field (None means zero).
+    u: [B, 3, N_K q + 1, N3] trial coefficients of one field (None means zero).
     Returns val, dtval, curl, each [B, T, P, 3] (dtval, curl are None unless
     ``derivs``).
     """
@@ -161,16 +208,17 @@ def _fields(u, pts: _Pts, q: int, tau: np.ndarray, dt: float, derivs: bool = Tru
         return 0.0, 0.0, 0.0
     B = u.shape[0]
     P = pts.phi.shape[0]
-    lt = basis.trial_time(q, tau)        # [q+1, T]
-    S = (u.reshape(-1, u.shape[-1]) @ pts.phi.T).reshape(B, 3, q + 1, P)
+    M = u.shape[2]
+    lt = trial_time_nk(q, nk, tau)        # [M, T]
+    S = (u.reshape(-1, u.shape[-1]) @ pts.phi.T).reshape(B, 3, M, P)
     ref = np.einsum("mt,bcmp->btpc", lt, S, optimize=True)      # reference field
     val = np.einsum("pci,btpc->btpi", pts.DFinv, ref, optimize=True)  # DF^{-T} ref
     if not derivs:
         return val, None, None
-    dlt = basis.trial_time_deriv(q, tau)  # [q+1, T]
+    dlt = trial_time_nk(q, nk, tau, deriv=True)  # [M, T]
     dref = np.einsum("mt,bcmp->btpc", dlt, S, optimize=True)
     gp = pts.gphi.transpose(1, 0, 2).reshape(pts.gphi.shape[1], -1)   # [N3, P*3]
-    G = (u.reshape(-1, u.shape[-1]) @ gp).reshape(B, 3, q + 1, P, 3)
+    G = (u.reshape(-1, u.shape[-1]) @ gp).reshape(B, 3, M, P, 3)
     gref = np.einsum("mt,bcmpa->btpca", lt, G, optimize=True)   # d ref_c / d x^_a
     # reference curl: (curl)_i = eps_{i a c} d_a ref_c
     cref = np.einsum("iac,btpca->btpi", _LEVI, gref, optimize=True)
@@ -220,11 +268,14 @@ class Oracle:
         self.q = np.asarray(mesh["q"], dtype=np.int64).reshape(self.ne)
         self.eps = np.asarray(mesh["eps"], dtype=np.float64).reshape(self.ne)
         self.mu = np.asarray(mesh["mu"], dtype=np.float64).reshape(self.ne)
+        self.nk = np.asarray(mesh.get("nk", np.ones(self.ne)), dtype=np.int64).reshape(self.ne)
+        if np.any(self.nk < 1):
+            raise ValueError("N_K must be >= 1")
         self.nbr = face_neighbours(self.hex)
         self.pieces = self._face_pieces()
         n3 = (self.p + 1) ** 3
-        self.trial_sz = 6 * (self.q + 1) * n3
-        self.test_sz = 6 * self.q * n3
+        self.trial_sz = 6 * (self.nk * self.q + 1) * n3
+        self.test_sz = 6 * self.nk * self.q * n3
         self.trial_off = np.concatenate([[0], np.cumsum(self.trial_sz)])
         self.test_off = np.concatenate([[0], np.cumsum(self.test_sz)])
         self._vol_cache = {}
@@ -239,14 +290,14 @@ class Oracle:
         U is a trial vector [..., N_trial] or a dict {element: block [B, 2, 3, q+1, N3]}
         holding only some elements' blocks (the others are zero).
         """
-        p, q = int(self.p[e]), int(self.q[e])
+        p, M = int(self.p[e]), int(self.nk[e] * self.q[e]) + 1
         if isinstance(U, dict):
             if e in U:
                 return U[e]
             B = next(iter(U.values())).shape[0]
-            return np.zeros((B, 2, 3, q + 1, (p + 1) ** 3))
+            return np.zeros((B, 2, 3, M, (p + 1) ** 3))
         blk = U[..., self.trial_off[e]:self.trial_off[e + 1]]
-        return blk.reshape(blk.shape[:-1] + (2, 3, q + 1, (p + 1) ** 3))
+        return blk.reshape(blk.shape[:-1] + (2, 3, M, (p + 1) ** 3))
 
     def _pts(self, e: int, p: int, xh: np.ndarray, tag) -> _Pts:
         """Geometry/basis tables at reference points xh of element e.
@@ -341,15 +392,15 @@ class Oracle:
     # -- volume terms ----------------------------------------------------------
     def _volume(self, e, uE, uH, dt, t0, src):
         """Volume part of R for element e: [B, 2, 3, q, N3]."""
-        p, q = int(self.p[e]), int(self.q[e])
+        p, q, nk = int(self.p[e]), int(self.q[e]), int(self.nk[e])
         X8 = self.X8(e)
         xh, wx = _grid3(p + 2)
         pts = self._pts(e, p, xh, ("vol", p + 2))
-        tau, wt = basis.gauss01(q + 2)
-        Lt = basis.legendre(q - 1, tau)  # [q, T]
+        tau, wt = time_rule(q, nk)
+        Lt = test_time_nk(q, nk, tau)  # [N_K q, T]
         wgt = dt * np.outer(wt, wx * pts.J)  # [T, P] : dt dxi * J dx^
-        E, dE, cE = _fields(uE, pts, q, tau, dt)
-        H, dH, cH = _fields(uH, pts, q, tau, dt)
+        E, dE, cE = _fields(uE, pts, q, tau, dt, nk=nk)
+        H, dH, cH = _fields(uH, pts, q, tau, dt, nk=nk)
         RE = _test_project(self.eps[e] * dE, pts, Lt, wgt) - _test_project_curl(H, pts, Lt, wgt)
         RH = _test_project(self.mu[e] * dH + cE, pts, Lt, wgt)
         if src is not None:
@@ -366,12 +417,13 @@ class Oracle:
         uE/uH: own coefficients [B, 3, q+1, N3]; vE/vH: the neighbour's (or None).
         rect = (u0, u1, v0, v1): the piece in e's tangential reference coordinates.
         """
-        p, q = int(self.p[e]), int(self.q[e])
+        p, q, nk = int(self.p[e]), int(self.q[e]), int(self.nk[e])
         d, s = divmod(f, 2)
         X8 = self.X8(e)
         interior = e2 >= 0
         p2 = int(self.p[e2]) if interior else p
         q2 = int(self.q[e2]) if interior else q
+        nk2 = int(self.nk[e2]) if interior else nk
         nq = max(p, p2) + 2
         xh, wa = _face_grid(d, s, nq)
         a1_, a2_ = [a for a in range(3) if a != d]
@@ -388,12 +440,12 @@ class Oracle:
         n = c / dS[:, None]
         outward = pts.DF[:, :, d] * (1.0 if s == 1 else -1.0)
         n = n * np.sign(np.sum(n * outward, axis=1))[:, None]
-        T = max(q, q2) + 2
-        tau, wt = basis.gauss01(T)
-        Lt = basis.legendre(q - 1, tau)  # [q, T]
+        # time rule on the finer of the two partitions (they are nested or equal)
+        tau, wt = time_rule(max(q, q2), max(nk, nk2))
+        Lt = test_time_nk(q, nk, tau)  # [N_K q, T]
         wgt = dt * np.outer(wt, wa * dS)  # [T, A]
-        E1, _, _ = _fields(uE, pts, q, tau, dt, derivs=False)
-        H1, _, _ = _fields(uH, pts, q, tau, dt, derivs=False)
+        E1, _, _ = _fields(uE, pts, q, tau, dt, derivs=False, nk=nk)
+        H1, _, _ = _fields(uH, pts, q, tau, dt, derivs=False, nk=nk)
         nn = n[None, None, :, :]
         if interior:
             X8b = self.X8(e2)
@@ -403,8 +455,8 @@ class Oracle:
                 xh2 = geometry.inverse_map(X8b, pts.x)
                 self._vol_cache[key + (tuple(np.round(X8 - X8[0], 13).ravel()),)] = xh2
             pts2 = self._pts(e2, p2, xh2, ("nbrface", tuple(np.round(xh2, 12).ravel())))
-            E2, _, _ = _fields(vE, pts2, q2, tau, dt, derivs=False)
-            H2, _, _ = _fields(vH, pts2, q2, tau, dt, derivs=False)
+            E2, _, _ = _fields(vE, pts2, q2, tau, dt, derivs=False, nk=nk2)
+            H2, _, _ = _fields(vH, pts2, q2, tau, dt, derivs=False, nk=nk2)
             Havg = 0.5 * (H1 + H2)
             Eavg = 0.5 * (E1 + E2)
             jE = _cross(nn, E1) - _cross(nn, E2)  # [E]_T = n1 x E1 + n2 x E2, n2 = -n1
@@ -414,22 +466,24 @@ class Oracle:
             # H-eq: -<[E]_T, {w}> , {w} = w / 2
             RH = _test_project(-0.5 * jE, pts, Lt, wgt)
             qt = min(q, q2)
+            # Pi~ L: L2 projection of the own temporal test factors onto the largest common
+            # test space, piecewise P_{qt-1} on the coarser partition (None: own space itself)
+            PL = None
+            if qt < q or nk2 < nk:
+                Lc = test_time_nk(qt, min(nk, nk2), tau)
+                gram = np.einsum("kt,t,lt->kl", Lc, wt, Lc)
+                PL = np.linalg.solve(gram, np.einsum("kt,t,it->ki", Lc, wt, Lt)).T @ Lc
             if self.c_diss > 0:
                 # D_h: <alpha [F]_T, [Pi~ v]_T>; for the rows of e, [v]_T = n x v, and
                 # a . (n x v) = v . (a x n)
                 aE = self.c_diss / (0.5 * (np.sqrt(self.mu[e] / self.eps[e]) + np.sqrt(self.mu[e2] / self.eps[e2])))
                 aH = self.c_diss / (0.5 * (np.sqrt(self.eps[e] / self.mu[e]) + np.sqrt(self.eps[e2] / self.mu[e2])))
-                Lp = Lt
-                if qt < q:
-                    Lq_ = basis.legendre(qt - 1, tau)
-                    Lp = np.einsum("ik,kt->it", np.einsum("kt,t,it->ik", Lq_, wt, Lt), Lq_)  # Pi~ L_i
+                Lp = Lt if PL is None else PL
                 RE = RE + aE * _test_project(_cross(jE, nn), pts, Lp, wgt)
                 RH = RH + aH * _test_project(_cross(jH, nn), pts, Lp, wgt)
-            if qt < q:
-                # S_h: test factors (Pi~ L_i - L_i) with Pi~ the L2 projection onto P_{qt-1}
-                Lq = basis.legendre(qt - 1, tau)
-                proj = np.einsum("kt,t,it->ik", Lq, wt, Lt)       # <L_i, L_k>, k < qt
-                Ld = np.einsum("ik,kt->it", proj, Lq) - Lt          # (Pi~ - I) L_i at tau
+            if PL is not None:
+                # S_h: test factors (Pi~ L_i - L_i)
+                Ld = PL - Lt
                 # E rows: 1/2 ( <{H}, n x (Pi~v - v)> + <[H]_T, (Pi~v - v)/2> )
                 RE = RE + 0.5 * _test_project(_cross(Havg, nn) + 0.5 * jH, pts, Ld, wgt)
                 # H rows: -1/2 ( <{E}, n x (Pi~w - w)> + <[E]_T, (Pi~w - w)/2> )
@@ -464,7 +518,7 @@ class Oracle:
         u = self.trial_block(U, e)
         B = u.shape[0]
         p, q = int(self.p[e]), int(self.q[e])
-        R = np.zeros((B, 2, 3, q, (p + 1) ** 3))
+        R = np.zeros((B, 2, 3, int(self.nk[e]) * q, (p + 1) ** 3))
         if parts in ("all", "own"):
             R += self._volume(e, u[:, 0], u[:, 1], dt, t0, src if parts == "all" else None)
         for f in range(6):
@@ -508,7 +562,7 @@ class Oracle:
             for part, e2 in blocks:
                 m = int(self.trial_sz[e2])
                 # unit vectors of element e2's trial block (only that block is formed)
-                Ub = {e2: np.eye(m).reshape(m, 2, 3, int(self.q[e2]) + 1, (int(self.p[e2]) + 1) ** 3)}
+                Ub = {e2: np.eye(m).reshape(m, 2, 3, int(self.nk[e2] * self.q[e2]) + 1, (int(self.p[e2]) + 1) ** 3)}
                 Rb = self.element_residual(e, Ub, t0, dt, None, None, parts=part).reshape(m, -1)
                 Rb = Rb.T  # [test, m]
                 ii, jj = np.nonzero(Rb)
@@ -525,8 +579,7 @@ class Oracle:
         mask = np.zeros(int(self.trial_off[-1]), dtype=bool)
         for e in range(self.ne):
             n3 = (self.p[e] + 1) ** 3
-            q = self.q[e]
-            blk = np.zeros((2, 3, q + 1, n3), dtype=bool)
+            blk = np.zeros((2, 3, self.nk[e] * self.q[e] + 1, n3), dtype=bool)
             blk[:, :, 1:, :] = True
             mask[self.trial_off[e]:self.trial_off[e + 1]] = blk.ravel()
         return mask
@@ -549,35 +602,30 @@ class Oracle:
         return U
 
     def embed_start(self, u0) -> np.ndarray:
-        """Trial vector with mode 0 = u0 and all other modes 0."""
+        """Trial vector with the slab-start coefficient u0 and all other modes 0."""
         U = np.zeros(int(self.trial_off[-1]))
         o0 = 0
         for e in range(self.ne):
             n3 = int((self.p[e] + 1) ** 3)
-            q = int(self.q[e])
-            blk = np.zeros((2, 3, q + 1, n3))
+            blk = np.zeros((2, 3, int(self.nk[e] * self.q[e]) + 1, n3))
             blk[:, :, 0, :] = u0[o0:o0 + 6 * n3].reshape(2, 3, n3)
             o0 += 6 * n3
             U[self.trial_off[e]:self.trial_off[e + 1]] = blk.ravel()
         return U
 
     def end_state(self, U) -> np.ndarray:
-        """Spatial coefficients of the trial function at xi = 1 (sum_m l_m(1) u_m)."""
-        out = []
-        for e in range(self.ne):
-            q = int(self.q[e])
-            u = self.trial_block(U, e)
-            l1 = basis.trial_time(q, np.array([1.0]))[:, 0]
-            out.append(np.einsum("m,fcms->fcs", l1, u).ravel())
-        return np.concatenate(out)
+        """Spatial coefficients of the trial function at xi = 1."""
+        return self._state_at(U, 1.0)
 
     def start_state(self, U) -> np.ndarray:
+        return self._state_at(U, 0.0)
+
+    def _state_at(self, U, xi) -> np.ndarray:
         out = []
         for e in range(self.ne):
-            q = int(self.q[e])
             u = self.trial_block(U, e)
-            l0 = basis.trial_time(q, np.array([0.0]))[:, 0]
-            out.append(np.einsum("m,fcms->fcs", l0, u).ravel())
+            lt = trial_time_nk(int(self.q[e]), int(self.nk[e]), np.array([xi]))[:, 0]
+            out.append(np.einsum("m,fcms->fcs", lt, u).ravel())
         return np.concatenate(out)
 
     def energy(self, u) -> float:
@@ -627,14 +675,16 @@ class Oracle:
         return np.einsum("pci,fpc->fpi", pts.DFinv, ref)
 
     def test_projection_in_time(self, U) -> np.ndarray:
-        """pi U: Legendre-in-time coefficients (modes 0..q-1) of U, in the test layout."""
+        """pi U: the L2 projection of U onto the element's temporal test space, as
+        coefficients of the test functions L_i on each sub-interval (test layout)."""
         out = []
         for e in range(self.ne):
-            q = int(self.q[e])
+            q, nk = int(self.q[e]), int(self.nk[e])
             u = self.trial_block(U, e)
-            tau, wt = basis.gauss01(q + 2)
-            lt = basis.trial_time(q, tau)
-            Lt = basis.legendre(q - 1, tau)
-            B = np.einsum("it,t,mt->im", Lt, wt, lt)
+            tau, wt = time_rule(q, nk)
+            lt = trial_time_nk(q, nk, tau)
+            Lt = test_time_nk(q, nk, tau)
+            # int_{I_k} L_i^k L_i^k dxi = 1/N_K
+            B = nk * np.einsum("it,t,mt->im", Lt, wt, lt)
             out.append(np.einsum("im,fcms->fcis", B, u).ravel())
         return np.concatenate(out)

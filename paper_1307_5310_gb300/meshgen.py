@@ -131,23 +131,25 @@ def box_mesh(
     return mesh
 
 
-def trial_size(p, q) -> np.ndarray:
-    """Trial coefficients per element: 2 fields x 3 components x (q+1) modes x (p+1)^3."""
+def trial_size(p, q, nk=1) -> np.ndarray:
+    """Trial coefficients per element: 2 fields x 3 components x (N_K q + 1) temporal
+    coefficients (the slab start and q modes per sub-interval) x (p+1)^3."""
     p = np.asarray(p, dtype=np.int64)
     q = np.asarray(q, dtype=np.int64)
-    return 6 * (q + 1) * (p + 1) ** 3
+    return 6 * (np.asarray(nk, dtype=np.int64) * q + 1) * (p + 1) ** 3
 
 
-def test_size(p, q) -> np.ndarray:
-    """Test coefficients (= residual entries = unknowns) per element: 6 q (p+1)^3."""
+def test_size(p, q, nk=1) -> np.ndarray:
+    """Test coefficients (= residual entries = unknowns) per element: 6 N_K q (p+1)^3."""
     p = np.asarray(p, dtype=np.int64)
     q = np.asarray(q, dtype=np.int64)
-    return 6 * q * (p + 1) ** 3
+    return 6 * np.asarray(nk, dtype=np.int64) * q * (p + 1) ** 3
 
 
 def dof_offsets(mesh: dict, kind: str = "trial") -> np.ndarray:
     """Prefix offsets [n_elem + 1] of the per-element coefficient blocks."""
-    sz = trial_size(mesh["p"], mesh["q"]) if kind == "trial" else test_size(mesh["p"], mesh["q"])
+    nk = mesh.get("nk", 1)
+    sz = trial_size(mesh["p"], mesh["q"], nk) if kind == "trial" else test_size(mesh["p"], mesh["q"], nk)
     off = np.zeros(sz.size + 1, dtype=np.int64)
     np.cumsum(sz, out=off[1:])
     return off
@@ -157,6 +159,13 @@ def random_coeffs(mesh: dict, seed: int, kind: str = "trial", lo=-1.0, hi=1.0) -
     """Coefficient vector with entries iid U[lo, hi) from PCG64(seed)."""
     n = int(dof_offsets(mesh, kind)[-1])
     return np.random.Generator(np.random.PCG64(seed)).uniform(lo, hi, size=n)
+
+
+def random_nk(mesh: dict, seed: int, choices=(1, 2, 4)) -> None:
+    """Per-element number of temporal sub-intervals N_K, uniform over ``choices`` (PCG64)."""
+    ne = mesh["hex"].shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mesh["nk"] = np.asarray(choices, dtype=np.uint8)[rng.integers(0, len(choices), size=ne)]
 
 
 def random_materials(mesh: dict, seed_eps: int, seed_mu: int, lo=1.0, hi=4.0) -> None:

@@ -552,3 +552,70 @@ def test_planted_mistakes_fail_pins(monkeypatch):
     monkeypatch.setattr(stdg.Oracle, "_face", bad_face)
     R = o.residual(U, t0, dt, g=g)
     assert np.abs(R).max() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Local refinement in time (N_K sub-intervals per element, Sec. 2.2 / 4.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nk,q", [(2, 1), (2, 2), (4, 2), (3, 3)])
+def test_uniform_time_refinement_is_substepping(nk, q):
+    """Every element with N_K equal sub-intervals: the common test space is the own one
+    (S_h = 0) and the sub-interval equations decouple in time order, so one slab equals
+    N_K slabs of dt / N_K."""
+    m = meshgen.box_mesh(2, 2, 1, hi=(1.0, 0.6, 0.5), p=1, q=q)
+    meshgen.random_materials(m, 3, 4)
+    o1 = stdg.Oracle(m)
+    mk = dict(m)
+    mk["nk"] = np.full(m["hex"].shape[0], nk)
+    ok = stdg.Oracle(mk)
+    u0 = np.random.Generator(np.random.PCG64(5)).uniform(-1, 1, o1.ne * 6 * 8)
+    dt, t0 = 0.3, 0.1
+    u = u0
+    for k in range(nk):
+        u = o1.end_state(o1.slab_solve(u, t0 + k * dt / nk, dt / nk))
+    uk = ok.end_state(ok.slab_solve(u0, t0, dt))
+    assert np.abs(uk - u).max() <= 1e-12 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("uneven_q", [False, True])
+def test_energy_identity_time_refinement(uneven_q):
+    """Theorem 4.1 with local refinement in time: R(U) . pi U = E(t_n+1) - E(t_n) for any U."""
+    m = meshgen.box_mesh(2, p=2, q=2)
+    meshgen.random_nk(m, 7)
+    if uneven_q:
+        m["q"] = np.array([1, 2, 3, 1, 2, 3, 2, 1], dtype=np.uint8)
+    assert len(set(m["nk"].tolist())) > 1
+    meshgen.random_materials(m, 5, 6)
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) <= 1e-12 * max(1.0, abs(dE))
+
+
+def test_patch_time_refinement():
+    """E = (0,0,x), H = (0,t,0), g = E with N_K in {1, 2, 4} and q >= 2: exact
+    (the linear-in-t H lies in every common test space)."""
+    m = meshgen.box_mesh(2, p=1, q=2)
+    m["nk"] = np.array([1, 2, 4, 2, 1, 4, 2, 1], dtype=np.uint8)
+    m["q"] = np.array([2, 2, 3, 2, 3, 2, 2, 3], dtype=np.uint8)
+    o = stdg.Oracle(m)
+    t0, dt = 0.3, 0.2
+    Ef = lambda x: np.stack([0 * x[:, 0], 0 * x[:, 0], x[:, 0]], 1)
+    Hf = lambda t: (lambda x: np.stack([0 * x[:, 0], t + 0 * x[:, 0], 0 * x[:, 0]], 1))
+    u0 = o.project(Ef, Hf(t0))
+    U = o.embed_start(u0)
+    for e in range(o.ne):
+        nk, q = int(o.nk[e]), int(o.q[e])
+        blk = o.trial_block(U, e)
+        for k in range(nk):
+            uk = o.project(Ef, Hf(t0 + (k + 1) * dt / nk))
+            n3 = 8
+            off = int(sum(6 * n3 for _ in range(e)))
+            blk[:, :, 1 + k * q, :] = uk[off:off + 6 * n3].reshape(2, 3, n3)
+
+    def g(x, t):
+        z = np.zeros(np.broadcast(x[..., 0], t).shape)
+        return np.stack([z, z, x[..., 0] + z], -1)
+
+    assert np.abs(o.residual(U, t0, dt, g=g)).max() < 1e-12
+    Us = o.slab_solve(u0, t0, dt, g=g)
+    assert np.abs(Us - U).max() < 1e-11
