@@ -89,6 +89,13 @@ typedef struct {
   const double *eps;   /* [n_elem] permittivity, > 0                             */
   const double *mu;    /* [n_elem] permeability, > 0                             */
   int32_t geometry;    /* STM_GEOM_*                                              */
+  const uint8_t *nk;   /* [n_elem] temporal sub-intervals N_K of the slab (local
+                          refinement in time, Sec. 2.2): 1, 2, 4 or 8; NULL = all
+                          1.  Element K then carries N_K q unknown temporal modes
+                          per (field, component, spatial index): trial layout
+                          [f][c][1 + N_K q][s] (index 0 the slab start, 1 + k q
+                          + m - 1 mode m of sub-interval k), test layout
+                          [f][c][N_K q][s].  Brick meshes without 2:1 faces   */
 } stm_mesh;
 
 typedef struct {

@@ -15,10 +15,9 @@ template <typename S>
 __global__ void k_precond_hp(S* __restrict__ z, const S* __restrict__ v, const S* __restrict__ inv,
                              const int64_t* __restrict__ off, const uint8_t* __restrict__ pq, int64_t ne) {
   for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
-    int n3, q;
-    degrees(pq, e, n3, q);
-    const int blk = q * n3;
+    // one (field, component) block per inverse mass entry: all temporal test functions
     const int64_t o = off[e];
+    const int blk = (int)((off[e + 1] - o) / 6);
     for (int it = threadIdx.x; it < 6 * blk; it += blockDim.x) z[o + it] = v[o + it] * inv[e * 6 + it / blk];
   }
 }
@@ -28,10 +27,8 @@ __global__ void k_combine_hp(X* __restrict__ x, const S* __restrict__ V, int64_t
                              const S* __restrict__ inv, const int64_t* __restrict__ off,
                              const uint8_t* __restrict__ pq, int64_t ne) {
   for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
-    int n3, q;
-    degrees(pq, e, n3, q);
-    const int blk = q * n3;
     const int64_t o = off[e];
+    const int blk = (int)((off[e + 1] - o) / 6);
     for (int it = threadIdx.x; it < 6 * blk; it += blockDim.x) {
       S acc = S(0);
       for (int j = 0; j < k; ++j) acc = fma((S)y.c[j], V[j * ldv + o + it], acc);
@@ -45,9 +42,11 @@ __global__ void k_init_hp(double* __restrict__ x, const double* __restrict__ st,
   for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
     int n3, q;
     degrees(pq, e, n3, q);
-    for (int it = threadIdx.x; it < 6 * q * n3; it += blockDim.x) {
-      const int fc = it / (q * n3), r = it - fc * q * n3, i = r / n3, s = r - i * n3;
-      x[ot[e] + it] = (i == 0) ? st[os[e] + fc * n3 + s] : 0.0;
+    // qe = N_K q temporal unknowns; mode 1 of every sub-interval = state: constant in time
+    const int qe = (int)((ot[e + 1] - ot[e]) / (6 * n3));
+    for (int it = threadIdx.x; it < 6 * qe * n3; it += blockDim.x) {
+      const int fc = it / (qe * n3), r = it - fc * qe * n3, i = r / n3, s = r - i * n3;
+      x[ot[e] + it] = (i % q == 0) ? st[os[e] + fc * n3 + s] : 0.0;
     }
   }
 }
@@ -57,9 +56,11 @@ __global__ void k_extract_hp(double* __restrict__ st, const double* __restrict__
   for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
     int n3, q;
     degrees(pq, e, n3, q);
+    // the slab end is mode 1 of the last sub-interval
+    const int qe = (int)((ot[e + 1] - ot[e]) / (6 * n3));
     for (int it = threadIdx.x; it < 6 * n3; it += blockDim.x) {
       const int fc = it / n3, s = it - fc * n3;
-      st[os[e] + it] = x[ot[e] + fc * q * n3 + s];
+      st[os[e] + it] = x[ot[e] + (fc * qe + qe - q) * n3 + s];
     }
   }
 }

@@ -1,7 +1,8 @@
 // Vector kernels for meshes whose elements have different (p, q): every
 // per-element block is located through offset arrays (test layout off_test,
-// state layout off_state) and the degrees pq[e] = p | q << 4.  One CTA walks
-// one element's block at a time.
+// state layout off_state, ne + 1 entries: block sizes are offset differences,
+// which covers N_K temporal sub-intervals) and the degrees pq[e] = p | q << 4.
+// One CTA walks one element's block at a time.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,11 +22,11 @@ template <typename S, typename X>
 void combine_hp(X* x, const S* V, int64_t ldv, int k, const Coef16& y, const S* inv, const int64_t* off_test,
                 const uint8_t* pq, int64_t ne, cudaStream_t s);
 
-// x: mode 1 (first unknown) = state, higher modes 0.
+// x: mode 1 (first unknown) of every temporal sub-interval = state, higher modes 0.
 void init_guess_hp(double* x, const double* state, const int64_t* off_test, const int64_t* off_state,
                    const uint8_t* pq, int64_t ne, cudaStream_t s);
 
-// state = mode 1 of x (the field at the slab end).
+// state = mode 1 of the last sub-interval of x (the field at the slab end).
 void extract_end_hp(double* state, const double* x, const int64_t* off_test, const int64_t* off_state,
                     const uint8_t* pq, int64_t ne, cudaStream_t s);
 

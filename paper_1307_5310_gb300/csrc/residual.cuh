@@ -50,19 +50,20 @@ struct Tables {
 
 template <typename T>
 struct ApplyArgs {
-  const T* um;            // trial modes 1..q
-  int64_t um_es, um_cs;   //   element stride, (field,component) stride; mode stride = N3
-  const T* u0;            // trial mode 0 (slab start) or nullptr (= 0)
-  int64_t u0_es, u0_cs;
-  const T* b;             // load vector in the test layout, or nullptr
-  T* y;                   // [ne][2][3][q][N3] scratch: temporal contraction
-  T* tr;                  // [ne][2][3 axes][2 sides][2 comps][q][N2] scratch: face traces
-  T* R;                   // [ne][2][3][q][N3] residual (test layout)
-  const int32_t* nbr;     // [ne][6]
-  const T* mass;          // [ne][2][3]: eps G_c (E rows), mu G_c (H rows); nullptr: R already
-                          //   holds the mass term (curved elements, written by k_mass_curved)
-  int64_t n_elem;
-  Tables<T> tb;
+  // every member has a default: a launch reads only what its caller set, the rest is null
+  const T* um = nullptr;            // trial modes 1..q
+  int64_t um_es = 0, um_cs = 0;     //   element stride, (field,component) stride; mode stride = N3
+  const T* u0 = nullptr;            // trial mode 0 (slab start) or nullptr (= 0)
+  int64_t u0_es = 0, u0_cs = 0;
+  const T* b = nullptr;             // load vector in the test layout, or nullptr
+  T* y = nullptr;                   // [ne][2][3][q][N3] scratch: temporal contraction
+  T* tr = nullptr;                  // [ne][2][3 axes][2 sides][2 comps][q][N2] scratch: face traces
+  T* R = nullptr;                   // [ne][2][3][q][N3] residual (test layout)
+  const int32_t* nbr = nullptr;     // [ne][6]
+  const T* mass = nullptr;          // [ne][2][3]: eps G_c (E rows), mu G_c (H rows); nullptr: R already
+                                    //   holds the mass term (curved elements, written by k_mass_curved)
+  int64_t n_elem = 0;
+  Tables<T> tb{};
   // uneven (p, q): elements of one class are listed in elist; every per-element
   // block is found through offset arrays, and neighbours may belong to other classes
   const int32_t* elist = nullptr;   // [n_elem] element ids of this class (null: uniform mesh)
@@ -83,7 +84,16 @@ struct ApplyArgs {
   // brick's face factor h_b / h_c; scaled by dt_k at apply time
   const T* kap = nullptr;
   T dt_k = T(0);
+  // local refinement in time (Sec. 2.2): this class's elements split the slab into nk equal
+  // sub-intervals (the tables then hold dt / nk); nkl[e] = log2 N_K of every element (null: all 1);
+  // tmat: temporal transfer matrices M^{r,o}[a][b] = int_0^1 L_a(s) L_b((o + s) / r) ds for
+  // r = 2, 4, 8 (matrices 0-1, 2-5, 6-13), kMaxQ x kMaxQ each
+  int nk = 1;
+  const uint8_t* nkl = nullptr;
+  const T* tmat = nullptr;
 };
+
+__host__ __device__ constexpr int tmat_index(int r, int o) { return (r == 2 ? 0 : (r == 4 ? 2 : 6)) + o; }
 
 // Element-local addressing of one element of class (P, Q).
 template <typename T, int P, int Q, bool HP>
@@ -92,11 +102,12 @@ struct ElemAddr {
   int64_t e, um, um_cs, u0, u0_cs, R, tr;
   __device__ __forceinline__ ElemAddr(const ApplyArgs<T>& A, int64_t blk) {
     if (HP) {
+      const int QE = A.nk * Q;  // temporal test functions of the element (all sub-intervals)
       e = A.elist[blk];
       um = A.off_um[e] + (A.um_trial ? N3 : 0);
-      um_cs = A.um_trial ? (Q + 1) * N3 : Q * N3;
+      um_cs = A.um_trial ? (QE + 1) * N3 : QE * N3;
       u0 = A.u0 ? A.off_u0[e] : 0;
-      u0_cs = A.u0_state ? N3 : (Q + 1) * N3;
+      u0_cs = A.u0_state ? N3 : (QE + 1) * N3;
       R = A.off_R[e];
       tr = A.off_tr[e];
     } else {
@@ -139,15 +150,20 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
+  const int nk = HP ? A.nk : 1, QE = HP ? nk * Q : Q;
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
     const ElemAddr<T, P, Q, HP> ad(A, blk);
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {  // temporal sub-intervals (Sec. 2.2)
     for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
       const int fc = it / N3, s = it - fc * N3;
       T u[Q + 1];
-      u[0] = A.u0 ? A.u0[ad.u0 + fc * ad.u0_cs + s] : T(0);
+      // mode 0 of sub-interval k: the slab start, else mode 1 (end value) of sub-interval k - 1
+      if (k == 0) u[0] = A.u0 ? A.u0[ad.u0 + fc * ad.u0_cs + s] : T(0);
+      else u[0] = A.um[ad.um + fc * ad.um_cs + (k - 1) * Q * N3 + s];
 #pragma unroll
-      for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (m - 1) * N3 + s];
-      T* yg = A.y + ad.R + fc * (int64_t)(Q * N3) + s;
+      for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (k * Q + m - 1) * N3 + s];
+      T* yg = A.y + ad.R + fc * (int64_t)(QE * N3) + k * Q * N3 + s;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         T acc = T(0);
@@ -183,11 +199,12 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
         if (j & 1) od = fma(A.tb.lv[j], v, od);
         else ev = fma(A.tb.lv[j], v, ev);
       }
-      const int64_t o = ((((int64_t)f * 3 + a) * 2 + 0) * 2 + bi) * Q + i;
+      const int64_t o = ((((int64_t)f * 3 + a) * 2 + 0) * 2 + bi) * QE + k * Q + i;
       A.tr[ad.tr + o * N2 + t] = ev - od;                 // face x^_a = 0
-      A.tr[ad.tr + (o + 2 * Q) * N2 + t] = ev + od;       // face x^_a = 1
+      A.tr[ad.tr + (o + 2 * QE) * N2 + t] = ev + od;      // face x^_a = 1
     }
     __syncthreads();
+    }
   }
 }
 
@@ -197,9 +214,19 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
 // modes are truncated or zero-padded and its temporal modes cut at
 // min(q, q') (the projection onto the common temporal test space of
 // Eq. bilinearform:S).
+//
+// Local refinement in time: the own test function L_i on sub-interval k and
+// the neighbour's partition (N_K' sub-intervals) are nested.  The neighbour
+// term <H', Pi~ L_i^k> (Pi~ onto the common test space: piecewise
+// P_{min(q,q')-1} on the coarser partition) is a combination of the
+// neighbour's own temporal moments y', in units of the own dt / N_K:
+//   N_K' = N_K: y'_{k,i} (i < q');
+//   N_K' < N_K (own finer, r = N_K/N_K', k = r k' + o): sum_{l<q~} M^{r,o}[i][l] y'_{k',l};
+//   N_K' > N_K (own coarser, r = N_K'/N_K): for i < q~,
+//     sum_{o<r} (1/r) sum_{j<=i} M^{r,o}[j][i] y'_{r k + o, j}.
 template <typename T, int N, int Q, bool HP>
 __device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int nside, int fp, int a, int bi, int i,
-                                       int t) {
+                                       int t, int k = 0) {
   if (!HP) {
     constexpr int N2 = N * N;
     const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * Q + i;
@@ -208,9 +235,26 @@ __device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int ns
   const int pq = A.pq[en];
   const int Nn = (pq & 15) + 1, qn = pq >> 4;
   const int slow = t / N, fast = t - slow * N;
-  if (i >= qn || slow >= Nn || fast >= Nn) return T(0);
-  const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qn + i;
-  return A.tr[A.off_tr[en] + so * (Nn * Nn) + slow * Nn + fast];
+  const int qt = qn < Q ? qn : Q;
+  // rows i >= qt vanish in every case (M^{r,o}[i][l] = 0 for l < i: L_i is orthogonal to P_l)
+  if (i >= qt || slow >= Nn || fast >= Nn) return T(0);
+  const int nkn = A.nkl ? 1 << A.nkl[en] : 1, qen = nkn * qn, nn2 = Nn * Nn;
+  const T* src = A.tr + A.off_tr[en] + ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qen * nn2 + slow * Nn + fast;
+  if (nkn == A.nk) return src[(int64_t)(k * qn + i) * nn2];
+  if (nkn < A.nk) {
+    const int r = A.nk / nkn, kk = k / r, o = k - kk * r;
+    const T* M = A.tmat + tmat_index(r, o) * (kMaxQ * kMaxQ) + i * kMaxQ;
+    T acc = T(0);
+    for (int l = i; l < qt; ++l) acc = fma(M[l], src[(int64_t)(kk * qn + l) * nn2], acc);
+    return acc;
+  }
+  const int r = nkn / A.nk;
+  T acc = T(0);
+  for (int o = 0; o < r; ++o) {
+    const T* M = A.tmat + tmat_index(r, o) * (kMaxQ * kMaxQ);
+    for (int j = 0; j <= i; ++j) acc = fma(M[j * kMaxQ + i], src[(int64_t)((k * r + o) * qn + j) * nn2], acc);
+  }
+  return acc / T(r);
 }
 
 // Shared memory per k_apply pass: y of the other field and the residual rows;
@@ -231,17 +275,25 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [NF][3][Q][N3]: y of the other field
   T* Rs = ys + NF * FB;                     // [NF][3][Q][N3]: residual rows
+  const int nk = HP ? A.nk : 1, QE = HP ? nk * Q : Q;
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
     const ElemAddr<T, P, Q, HP> ad(A, blk);
     const int64_t e = ad.e;
     const int32_t* nb = A.nbr + e * 6;
+#pragma unroll 1
+    for (int sk = 0; sk < nk; ++sk) {  // temporal sub-intervals (Sec. 2.2)
+    // offset of (field f, component/mode/spatial index w of one sub-interval block) in the test layout
+    auto gofs = [&](int f, int w) -> int64_t {
+      const int cc = w / (Q * N3);
+      return ad.R + (int64_t)(f * 3 + cc) * QE * N3 + sk * Q * N3 + (w - cc * Q * N3);
+    };
 #pragma unroll 1
     for (int f0 = 0; f0 < 2; f0 += NF) {
       for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
         const int fl = NF == 1 ? 0 : it / FB;
         const int f = f0 + fl, fp = 1 - f;
         const int w = it - fl * FB;
-        ys[it] = A.y[ad.R + fp * (int64_t)FB + w];
+        ys[it] = A.y[gofs(fp, w)];
         const int cc = w / (Q * N3);
         const int r = w - cc * (Q * N3);
         const int i = r / N3, s = r - i * N3;
@@ -249,12 +301,16 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         T v;
         if (A.mass) {
           const T mc = A.mass[e * 6 + fc];
-          v = mc * A.um[ad.um + fc * ad.um_cs + i * N3 + s];
-          if (i == 0 && A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
+          v = mc * A.um[ad.um + fc * ad.um_cs + (sk * Q + i) * N3 + s];
+          if (i == 0) {
+            // minus mode 0 of the sub-interval: the slab start or the previous sub-interval's end
+            if (sk > 0) v = fma(-mc, A.um[ad.um + fc * ad.um_cs + (sk - 1) * Q * N3 + s], v);
+            else if (A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
+          }
         } else {
-          v = A.R[ad.R + f * (int64_t)FB + w];
+          v = A.R[gofs(f, w)];
         }
-        if (A.b) v -= A.b[ad.R + f * (int64_t)FB + w];
+        if (A.b) v -= A.b[gofs(f, w)];
         Rs[it] = v;
       }
       __syncthreads();
@@ -278,16 +334,16 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           line_geom<N>(a, t, base, stride);
           const T* yl = ys + fl * FB + (b * Q + i) * N3 + base;
           // jumps of the tangential component b of field fp on the faces normal to a
-          const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * Q + i;  // side-0 slot within an element
+          const int64_t so = ((((int64_t)fp * 3 + a) * 2) * 2 + bi) * QE + sk * Q + i;  // side-0 slot
           const T* tre = A.tr + ad.tr;
           const T xm = tre[so * N2 + t];
-          const T xp = tre[(so + 2 * Q) * N2 + t];
+          const T xp = tre[(so + 2 * QE) * N2 + t];
           const int ep = nb[2 * a + 1], em = nb[2 * a];
           T jp, jm;
-          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP>(A, ep, 0, fp, a, bi, i, t);
+          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP>(A, ep, 0, fp, a, bi, i, t, sk);
           else if (HP && ep == -2) jp = xp - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a + 1]] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jp = (fp == 0) ? xp + xp : T(0);
-          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP>(A, em, 1, fp, a, bi, i, t);
+          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP>(A, em, 1, fp, a, bi, i, t, sk);
           else if (HP && em == -2) jm = xm - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a]] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jm = (fp == 0) ? xm + xm : T(0);
           const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
@@ -300,10 +356,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
             // faces normal to a, lifted with L_al(1) and L_al(0) = (-1)^al L_al(1);
             // on a PEC face the E jump is the own trace (E - g, g in the load)
             const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
-            const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * Q + i;
-            const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * Q) * N2 + t];
-            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP>(A, ep, 0, f, a, bc, i, t) : (f == 0 ? zp : T(0));
-            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP>(A, em, 1, f, a, bc, i, t) : (f == 0 ? zm : T(0));
+            const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * QE + sk * Q + i;
+            const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * QE) * N2 + t];
+            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP>(A, ep, 0, f, a, bc, i, t, sk) : (f == 0 ? zp : T(0));
+            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP>(A, em, 1, f, a, bc, i, t, sk) : (f == 0 ? zm : T(0));
             const T* kp = A.kap + e * 24 + f * 12 + 4 * a + bc;
             const T dp = A.dt_k * kp[2] * gp, dn = A.dt_k * kp[0] * gm;
             // the central-flux lift hf[al] = (dt/2) lv[al] shares the factor lv[al]
@@ -331,9 +387,12 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         }
         __syncthreads();
       }
-      T* Rg = A.R + ad.R + f0 * (int64_t)FB;
-      for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) Rg[it] = Rs[it];
+      for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
+        const int fl = NF == 1 ? 0 : it / FB;
+        A.R[gofs(f0 + fl, it - fl * FB)] = Rs[it];
+      }
       __syncthreads();
+    }
     }
   }
 }

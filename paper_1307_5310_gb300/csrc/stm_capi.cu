@@ -211,7 +211,14 @@ struct stm_ctx {
     int64_t count;
     int32_t* elist;
     int block;
+    int NK = 1;  // temporal sub-intervals of the class's elements
   };
+  // local refinement in time: N_K per element (log2 on the device) and the temporal transfer tables
+  std::vector<int> h_nk;
+  bool ltr = false;
+  uint8_t* nkl = nullptr;
+  double* tmat64 = nullptr;
+  float* tmat32 = nullptr;
   std::vector<Class> classes;
   int64_t n_tr = 0;
   // 2:1 faces: slots (receiving element faces) and their sources
@@ -369,6 +376,12 @@ int record_events(stm_ctx* c, LaunchEvents& ev) {
 // the trial layout (um_layout = L_TRIAL, mode 0 skipped) or the test layout;
 // u0 is mode 0 (trial layout or a state vector) or null; b is the load or null.
 template <typename T>
+const T* tmat_ptr(stm_ctx* c) {
+  if constexpr (sizeof(T) == 8) return c->tmat64;
+  else return c->tmat32;
+}
+
+template <typename T>
 const T* kap_ptr(stm_ctx* c) {
   if constexpr (sizeof(T) == 8) return c->kap64;
   else return c->kap32;
@@ -381,7 +394,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
     int rc = scratch<T>(c, &y, &tr);
     if (rc) return rc;
   }
-  ApplyArgs<T> a;
+  ApplyArgs<T> a{};
   a.b = b;
   a.y = y;
   a.tr = tr;
@@ -401,6 +414,8 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
     a.off_R = c->off_test;
     a.off_tr = c->off_tr;
     a.pq = c->pq;
+    a.nkl = c->nkl;
+    a.tmat = tmat_ptr<T>(c);
     const bool use_graph = c->opts.graph && !c->profiling;
     typename stm_ctx::GraphKey key{sizeof(T) == 8 ? 0 : 1, um_layout, u0_layout, um, u0, b, R, dt};
     if (use_graph) {
@@ -446,7 +461,8 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         const auto& cl = c->classes[k];
         a.elist = cl.elist;
         a.n_elem = cl.count;
-        a.tb = make_tables<T>(cl.P, kMaxQ, dt);
+        a.nk = cl.NK;
+        a.tb = make_tables<T>(cl.P, kMaxQ, dt / cl.NK);  // sub-interval length dt / N_K
         LaunchEvents e2 = none;
         if (phase == 1 && k == 0) e2.start = ev.start;
         if (phase == 1 && k + 1 == c->classes.size()) e2.mid = ev.mid;
@@ -926,8 +942,20 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     if (m->q[e] < 1 || m->q[e] > kMaxQ) return bad(STM_EINVAL, "q must be 1..6");
     if (m->p[e] != c->P || m->q[e] != c->Q) c->hp = true;
   }
+  c->h_nk.assign(c->ne, 1);
+  for (int64_t e = 0; m->nk && e < c->ne; ++e) {
+    const int v = m->nk[e];
+    if (v != 1 && v != 2 && v != 4 && v != 8) return bad(STM_EINVAL, "N_K must be 1, 2, 4 or 8");
+    c->h_nk[e] = v;
+    if (v > 1) c->ltr = c->hp = true;  // local refinement in time runs through the per-element kernels
+  }
   for (int64_t k = 0; k < 6 * c->ne; ++k)
     if (m->nbr[k] == -2) c->hp = true;  // 2:1 faces run through the per-element-offset kernels
+  if (c->ltr) {
+    for (int64_t k = 0; k < 6 * c->ne; ++k)
+      if (m->nbr[k] == -2) return bad(STM_EUNSUPPORTED, "local refinement in time is not built for 2:1 faces");
+    if (o && o->c_diss != 0.0) return bad(STM_EUNSUPPORTED, "the dissipative term needs N_K = 1");
+  }
   if (c->hp && m->geometry != STM_GEOM_BRICK)
     return bad(STM_EUNSUPPORTED, "uneven (p, q) and 2:1 faces are handled on brick meshes only");
   if (o && o->c_diss != 0.0) {
@@ -952,7 +980,7 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
     c->h_off_state.assign(c->ne + 1, 0);
     c->h_off_tr.assign(c->ne + 1, 0);
     for (int64_t e = 0; e < c->ne; ++e) {
-      const int64_t n = c->h_p[e] + 1, n2 = n * n, n3 = n2 * n, q = c->h_q[e];
+      const int64_t n = c->h_p[e] + 1, n2 = n * n, n3 = n2 * n, q = (int64_t)c->h_nk[e] * c->h_q[e];
       c->h_off_trial[e + 1] = c->h_off_trial[e] + 6 * (q + 1) * n3;
       c->h_off_test[e + 1] = c->h_off_test[e] + 6 * q * n3;
       c->h_off_state[e + 1] = c->h_off_state[e] + 6 * n3;
@@ -1224,17 +1252,47 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
                cudaMalloc(&c->off_tr, (c->ne + 1) * sizeof(int64_t)) == cudaSuccess &&
                cudaMalloc(&c->el, c->ne * sizeof(double)) == cudaSuccess;
     // (p, q) classes, element lists in mesh order
-    std::vector<std::vector<int32_t>> lists(8 * (kMaxQ + 1));
-    for (int64_t e = 0; e < c->ne; ++e) lists[c->h_p[e] * (kMaxQ + 1) + c->h_q[e]].push_back((int32_t)e);
+    auto lg2 = [](int v) { return v == 1 ? 0 : (v == 2 ? 1 : (v == 4 ? 2 : 3)); };
+    std::vector<std::vector<int32_t>> lists(8 * (kMaxQ + 1) * 4);
+    for (int64_t e = 0; e < c->ne; ++e)
+      lists[(c->h_p[e] * (kMaxQ + 1) + c->h_q[e]) * 4 + lg2(c->h_nk[e])].push_back((int32_t)e);
     for (int pp = 0; pp < 8 && okh; ++pp)
-      for (int qq = 1; qq <= kMaxQ && okh; ++qq) {
-        const auto& L = lists[pp * (kMaxQ + 1) + qq];
-        if (L.empty()) continue;
-        stm_ctx::Class cl{pp, qq, (int64_t)L.size(), nullptr, 256};
-        okh = cudaMalloc(&cl.elist, L.size() * sizeof(int32_t)) == cudaSuccess;
-        if (okh) cudaMemcpy(cl.elist, L.data(), L.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-        c->classes.push_back(cl);
+      for (int qq = 1; qq <= kMaxQ && okh; ++qq)
+        for (int lk = 0; lk < 4 && okh; ++lk) {
+          const auto& L = lists[(pp * (kMaxQ + 1) + qq) * 4 + lk];
+          if (L.empty()) continue;
+          stm_ctx::Class cl{pp, qq, (int64_t)L.size(), nullptr, 256};
+          cl.NK = 1 << lk;
+          okh = cudaMalloc(&cl.elist, L.size() * sizeof(int32_t)) == cudaSuccess;
+          if (okh) cudaMemcpy(cl.elist, L.data(), L.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+          c->classes.push_back(cl);
+        }
+    if (okh && c->ltr) {
+      // per-element log2 N_K and the temporal transfer matrices M^{r,o}[a][b] =
+      // int_0^1 L_a(s) L_b((o + s) / r) ds by Gauss quadrature (exact: degree <= 2 kMaxQ)
+      std::vector<uint8_t> nkl(c->ne);
+      for (int64_t e = 0; e < c->ne; ++e) nkl[e] = (uint8_t)lg2(c->h_nk[e]);
+      std::vector<double> tm(14 * kMaxQ * kMaxQ, 0.0), xg, wg;
+      gauss01(kMaxQ + 1, xg, wg);
+      for (int r = 2; r <= 8; r *= 2)
+        for (int oo = 0; oo < r; ++oo)
+          for (size_t g = 0; g < xg.size(); ++g) {
+            double La[kMaxN], Lb[kMaxN];
+            legendre01(kMaxQ, xg[g], La);
+            legendre01(kMaxQ, (oo + xg[g]) / r, Lb);
+            for (int aa = 0; aa < kMaxQ; ++aa)
+              for (int bb = 0; bb < kMaxQ; ++bb) tm[(tmat_index(r, oo) * kMaxQ + aa) * kMaxQ + bb] += wg[g] * La[aa] * Lb[bb];
+          }
+      std::vector<float> tm32(tm.begin(), tm.end());
+      okh = cudaMalloc(&c->nkl, c->ne) == cudaSuccess &&
+            cudaMalloc(&c->tmat64, tm.size() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->tmat32, tm.size() * sizeof(float)) == cudaSuccess;
+      if (okh) {
+        cudaMemcpy(c->nkl, nkl.data(), c->ne, cudaMemcpyHostToDevice);
+        cudaMemcpy(c->tmat64, tm.data(), tm.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->tmat32, tm32.data(), tm32.size() * sizeof(float), cudaMemcpyHostToDevice);
       }
+    }
     if (okh && c->n_slots > 0) {
       const size_t ns = (size_t)c->n_slots;
       okh = cudaMalloc(&c->hslot, 6 * c->ne * sizeof(int32_t)) == cudaSuccess &&
@@ -1327,7 +1385,7 @@ int32_t stm_destroy(stm_ctx* c) {
                   c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
                   c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
-                  c->sw64,    c->sw32,    c->kap64,  c->kap32};
+                  c->sw64,    c->sw32,    c->kap64,  c->kap32, c->nkl,    c->tmat64, c->tmat32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1544,6 +1602,7 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
     if (curved) return fail(c, STM_EUNSUPPORTED, "the inexact solve is built for brick meshes");
     for (const auto& k : c->classes)  // the bound needs one temporal degree everywhere
       if (k.Q != c->classes[0].Q) return fail(c, STM_EUNSUPPORTED, "the inexact solve needs a uniform q");
+    if (c->ltr) return fail(c, STM_EUNSUPPORTED, "the inexact solve needs N_K = 1 (no local refinement in time)");
     if (!(c->opts.t_final > 0)) return fail(c, STM_EINVAL, "opts.t_final must be positive for the inexact solve");
     if ((rc = build_eta_weights(c, dt))) return rc;
     const double nslab = std::max(1.0, std::round(c->opts.t_final / dt));
@@ -1674,7 +1733,7 @@ int autotune_prec(stm_ctx* c, double dt, int reps, std::vector<double>& best_ms)
           const auto& cl = c->classes[k];
           T *y = nullptr, *tr = nullptr;
           scratch<T>(c, &y, &tr);
-          ApplyArgs<T> a;
+          ApplyArgs<T> a{};
           a.y = y;
           a.tr = tr;
           a.R = R;
@@ -1693,7 +1752,12 @@ int autotune_prec(stm_ctx* c, double dt, int reps, std::vector<double>& best_ms)
           a.hbuf = hbuf_ptr<T>(c);
           a.elist = cl.elist;
           a.n_elem = cl.count;
-          a.tb = make_tables<T>(cl.P, kMaxQ, dt);
+          a.nk = cl.NK;
+          a.nkl = c->nkl;
+          a.tmat = tmat_ptr<T>(c);
+          a.kap = kap_ptr<T>(c);
+          a.dt_k = (T)dt;
+          a.tb = make_tables<T>(cl.P, kMaxQ, dt / cl.NK);
           const int grid = (int)std::min<int64_t>(cl.count, 1 << 30);
           LaunchEvents none;
           if (launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, none, 1, cb) ||

@@ -101,7 +101,7 @@ extern "C" int32_t stm_residual_apply_noalloc(int64_t n_elem, int32_t p, int32_t
   const int grid_m = (int)((n_elem + 255) / 256 < 4096 ? (n_elem + 255) / 256 : 4096);
   k_noalloc_mass<<<grid_m, 256, 0, s>>>(h, eps, mu, mass, n_elem);
 
-  stm::ApplyArgs<double> a;
+  stm::ApplyArgs<double> a{};
   const int64_t tes = 6 * (q + 1) * n3, tcs = (q + 1) * n3;
   a.um = U + n3;
   a.um_es = tes;

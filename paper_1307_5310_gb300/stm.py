@@ -52,7 +52,7 @@ class stm_mesh(C.Structure):
         ("n_hang", C.c_int64), ("hang", C.POINTER(C.c_int64)),
         ("p", C.POINTER(C.c_uint8)), ("q", C.POINTER(C.c_uint8)),
         ("eps", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
-        ("geometry", C.c_int32),
+        ("geometry", C.c_int32), ("nk", C.POINTER(C.c_uint8)),
     ]
 
 
@@ -225,6 +225,7 @@ class Slab:
             "mu": np.ascontiguousarray(mesh["mu"], dtype=np.float64),
             "hang": np.ascontiguousarray(np.asarray(mesh.get("hang", np.zeros((0, 6)))).reshape(-1, 6),
                                          dtype=np.int64),
+            "nk": np.ascontiguousarray(np.asarray(mesh.get("nk", np.ones(ne))).reshape(ne), dtype=np.uint8),
         }
         geom = {"brick": STM_GEOM_BRICK, "trilinear": STM_GEOM_TRILINEAR}[mesh.get("geometry", "brick")]
         m = stm_mesh(ne, arr["vert"].shape[0],
@@ -235,7 +236,8 @@ class Slab:
                      arr["p"].ctypes.data_as(C.POINTER(C.c_uint8)),
                      arr["q"].ctypes.data_as(C.POINTER(C.c_uint8)),
                      arr["eps"].ctypes.data_as(C.POINTER(C.c_double)),
-                     arr["mu"].ctypes.data_as(C.POINTER(C.c_double)), geom)
+                     arr["mu"].ctypes.data_as(C.POINTER(C.c_double)), geom,
+                     arr["nk"].ctypes.data_as(C.POINTER(C.c_uint8)))
         if stream is None:
             import torch
 
