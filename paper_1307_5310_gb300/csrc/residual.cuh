@@ -46,6 +46,7 @@ struct Tables {
   T Dt[kMaxN][kMaxN];     // dt * D[a][b]
   T hf[kMaxN];            // dt/2 * sqrt(2a+1)
   T lv[kMaxN];            // sqrt(2a+1)
+  T kq[kMaxN];            // -1 / (4 sqrt(2a+1)): folds the flux lift into the curl (k_apply)
 };
 
 template <typename T>
@@ -257,6 +258,15 @@ __device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int ns
   return acc / T(r);
 }
 
+// Offset in the test layout [f][c][QE][N3] of entry w = (c, i, s) of one sub-interval's
+// [3][Q][N3] block of field f, the sub-interval's rows starting at rk (per component).
+template <int Q, int N3, bool HP = true>
+__device__ __forceinline__ int64_t test_ofs(int64_t rk, int f, int w, int QE) {
+  if constexpr (!HP) return rk + (int64_t)f * (3 * Q * N3) + w;  // one sub-interval: contiguous
+  const int cc = w / (Q * N3);
+  return rk + (int64_t)(f * 3 + cc) * QE * N3 + (w - cc * Q * N3);
+}
+
 // Shared memory per k_apply pass: y of the other field and the residual rows;
 // both fields in one pass when that fits in ~110 KB, else one field per pass.
 template <typename T, int P, int Q>
@@ -282,18 +292,14 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
     const int32_t* nb = A.nbr + e * 6;
 #pragma unroll 1
     for (int sk = 0; sk < nk; ++sk) {  // temporal sub-intervals (Sec. 2.2)
-    // offset of (field f, component/mode/spatial index w of one sub-interval block) in the test layout
-    auto gofs = [&](int f, int w) -> int64_t {
-      const int cc = w / (Q * N3);
-      return ad.R + (int64_t)(f * 3 + cc) * QE * N3 + sk * Q * N3 + (w - cc * Q * N3);
-    };
+    const int64_t rk = ad.R + (int64_t)sk * Q * N3;  // sub-interval sk's rows start here (per component)
 #pragma unroll 1
     for (int f0 = 0; f0 < 2; f0 += NF) {
       for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
         const int fl = NF == 1 ? 0 : it / FB;
         const int f = f0 + fl, fp = 1 - f;
         const int w = it - fl * FB;
-        ys[it] = A.y[gofs(fp, w)];
+        ys[it] = A.y[test_ofs<Q, N3, HP>(rk, fp, w, QE)];
         const int cc = w / (Q * N3);
         const int r = w - cc * (Q * N3);
         const int i = r / N3, s = r - i * N3;
@@ -308,9 +314,9 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
             else if (A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
           }
         } else {
-          v = A.R[gofs(f, w)];
+          v = A.R[test_ofs<Q, N3, HP>(rk, f, w, QE)];
         }
-        if (A.b) v -= A.b[gofs(f, w)];
+        if (A.b) v -= A.b[test_ofs<Q, N3, HP>(rk, f, w, QE)];
         Rs[it] = v;
       }
       __syncthreads();
@@ -374,10 +380,18 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
               Rl[al * stride] = r2;
             }
           } else {
+            // Dt[a][b] = 2 dt L_a(1) L_b(1) and hf[a] = dt/2 L_a(1) share the factor L_a(1), so
+            // the lift -hf[a] X of every row a but the last equals Dt[a][B] X kq[B] with B the
+            // largest index of the other parity (which every such row's curl sum reaches):
+            // folded into y[B] once per line instead of one FMA per row
+            constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2;  // largest odd index: even rows, X = dm
+            constexpr int B1 = ((N - 1) & 1) ? N - 2 : N - 1;  // largest even index: odd rows, X = sp
+            if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+            if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
 #pragma unroll
             for (int al = 0; al < N; ++al) {
               T r2 = Rl[al * stride];
-              r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
+              if (al == N - 1) r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
 #pragma unroll
               for (int be = 0; be < N; ++be)
                 if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
@@ -389,7 +403,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
       }
       for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
         const int fl = NF == 1 ? 0 : it / FB;
-        A.R[gofs(f0 + fl, it - fl * FB)] = Rs[it];
+        A.R[test_ofs<Q, N3, HP>(rk, f0 + fl, it - fl * FB, QE)] = Rs[it];
       }
       __syncthreads();
     }
@@ -518,10 +532,14 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
 #pragma unroll
         for (int j = 0; j < N; ++j) yv[j] = flip_sign(yv[j], flip);
         T* Rl = Rs + ((f * 3 + c) * Q + i) * N3 + base;
+        // flux lift folded into the curl operand as in k_apply
+        constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
+        if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+        if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
 #pragma unroll
         for (int al = 0; al < N; ++al) {
           T r2 = Rl[al * stride];
-          r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
+          if (al == N - 1) r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
 #pragma unroll
           for (int be = 0; be < N; ++be)
             if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);

@@ -84,6 +84,7 @@ Tables<T> make_tables(int P, int Q, double dt) {
     for (int m = 0; m <= kMaxQ; ++m) t.B[i][m] = (T)B[i][m];
   for (int a = 0; a < N; ++a) {
     t.lv[a] = (T)std::sqrt(2.0 * a + 1);
+    t.kq[a] = (T)(-0.25 / std::sqrt(2.0 * a + 1));
     t.hf[a] = (T)(0.5 * dt * std::sqrt(2.0 * a + 1));
     for (int b = 0; b < N; ++b)
       if (d_nz(a, b)) t.Dt[a][b] = (T)(dt * 2.0 * std::sqrt(2.0 * a + 1) * std::sqrt(2.0 * b + 1));
