@@ -377,6 +377,12 @@ int record_events(stm_ctx* c, LaunchEvents& ev) {
 // the trial layout (um_layout = L_TRIAL, mode 0 skipped) or the test layout;
 // u0 is mode 0 (trial layout or a state vector) or null; b is the load or null.
 template <typename T>
+const T* pinv_ptr(stm_ctx* c) {
+  if constexpr (sizeof(T) == 8) return c->inv64;
+  else return c->inv32;
+}
+
+template <typename T>
 const T* tmat_ptr(stm_ctx* c) {
   if constexpr (sizeof(T) == 8) return c->tmat64;
   else return c->tmat32;
@@ -389,7 +395,8 @@ const T* kap_ptr(stm_ctx* c) {
 }
 
 template <typename T>
-int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R) {
+int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R,
+          bool pre = false) {
   T *y = nullptr, *tr = nullptr;
   if (sizeof(T) == 8 || c->hp || c->kap64) {  // the uniform FP32 kernel is single-pass and needs no scratch
     int rc = scratch<T>(c, &y, &tr);
@@ -404,6 +411,8 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   a.mass = mass_ptr<T>(c);
   a.kap = kap_ptr<T>(c);
   a.dt_k = (T)dt;
+  // the fused preconditioner exists on the uniform brick path only (callers check)
+  a.pinv = pre ? pinv_ptr<T>(c) : nullptr;
   const int N3 = c->N3, Q = c->Q;
   if (c->hp) {
     a.um = um;
@@ -529,6 +538,13 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
 template <typename T>
 int linop(stm_ctx* c, double dt, const T* xin, T* out) {
   return apply<T>(c, dt, xin, L_TEST, nullptr, L_STATE, nullptr, out);
+}
+
+// A P^{-1} v in one residual launch (uniform brick meshes): the kernels scale v by the
+// inverse block-diagonal mass on load instead of a separate preconditioner pass
+template <typename T>
+int linop_pre(stm_ctx* c, double dt, const T* v, T* out) {
+  return apply<T>(c, dt, v, L_TEST, nullptr, L_STATE, nullptr, out, true);
 }
 
 // R(U) = A U - b with mode 0 = state (FP64), modes 1..q = xin and the load b (or none).
@@ -828,14 +844,24 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n, doubl
   int k = 0, rc;
   for (int j = 0; j < m && *iters < max_iters; ++j) {
     S* W = V + (size_t)(j + 1) * ldv;
-    if (c->geometry == STM_GEOM_TRILINEAR)
+    if (c->geometry == STM_GEOM_TRILINEAR) {
       precond_curved<S, S>(z, V + (size_t)j * ldv, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream);
-    else if (c->hp)
+      c->launches += 1;
+      if ((rc = linop<S>(c, dt, z, W))) return rc;
+    } else if (c->hp) {
       precond_hp<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), c->off_test, c->pq, c->ne, c->stream);
-    else
+      c->launches += 1;
+      if ((rc = linop<S>(c, dt, z, W))) return rc;
+    } else if (sizeof(S) == 4) {
+      // FP32 (memory-bound kernel): P^{-1} on load saves a pass over the basis vector
+      if ((rc = linop_pre<S>(c, dt, V + (size_t)j * ldv, W))) return rc;
+    } else {
+      // FP64: the residual kernels are bound by the FP64 pipe, where the scaling costs more
+      // than the separate (memory-bound) preconditioner pass
       precond_apply<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), qn3, n, c->stream);
-    c->launches += 1;
-    if ((rc = linop<S>(c, dt, z, W))) return rc;
+      c->launches += 1;
+      if ((rc = linop<S>(c, dt, z, W))) return rc;
+    }
     if (c->opts.eta_tol > 0) scale_blocks<S>(c, W, sw_ptr<S>(c), n);  // residual space weighted by S
     multidot<S>(W, V, ldv, j + 1, true, n, c->red_partial, c->red_out, c->stream);
     c->launches += 2;
