@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--q", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the hp-batch, curved and serving legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra legs")
+    ap.add_argument("--legs", default="hp_batch,curved,serving,inexact,dissipative,time_refinement",
+                    help="comma-separated extra legs to run")
     ap.add_argument("--reorth", type=int, default=0, help="second Gram-Schmidt pass (DGKS test); off by default: same iteration count and accuracy on this workload")
     return ap.parse_args()
 
@@ -381,6 +383,90 @@ def torch_sync():
     torch.cuda.synchronize()
 
 
+def _solve_ms(s, u0, dt, reps=2):
+    """Mean wall time of `reps` slab solves from the same state (synchronous C-ABI calls)."""
+    out = []
+    for k in range(reps + 1):
+        s.set_state(u0)
+        torch_sync()
+        a = time.perf_counter()
+        rc, rep = s.slab_solve(dt)
+        torch_sync()
+        if k > 0:
+            out.append(((time.perf_counter() - a) * 1e3, rep["iterations"], rc))
+    return statistics.mean(o[0] for o in out), out[-1][1], out[-1][2]
+
+
+def leg_dissipative(fp64_peak):
+    """The bench workload (64^3 bricks, p=4, q=3) with the dissipative term D_h of Sec. 4.2, c = 1."""
+    import numpy as np
+
+    from paper_1307_5310_gb300 import stm
+
+    n, p, q = 64, 4, 3
+    m = workload(n, p, q)
+    ne = m["hex"].shape[0]
+    dt = (1.0 / n) / (2 * p + 1)
+    dof = ne * 6 * (q + 1) * (p + 1) ** 3
+    s = stm.Slab(m, c_diss=1.0, tol=1e-9, max_it=400, reorth=False)
+    ms64, _ = time_applies(s, m, dt, stm.STM_FP64, reps=3)
+    ms32, _ = time_applies(s, m, dt, stm.STM_FP32, reps=3)
+    u0 = np.random.Generator(np.random.PCG64(1310)).uniform(-1, 1, s.n_state)
+    sol64, it64, rc64 = _solve_ms(s, u0, dt, reps=1)
+    s.close()
+    smx = stm.Slab(m, c_diss=1.0, precision=stm.STM_MIXED, tol=1e-9, max_it=400, reorth=False)
+    solmx, itmx, rcmx = _solve_ms(smx, u0, dt, reps=1)
+    smx.close()
+    fp, fa = flops_per_element(p, q)
+    fd = 2 * 3 * 2 * q * (p + 1) ** 2 * 6  # per line: two jumps, two alpha scalings, two combinations
+    ach = (fp + fa + fd) * ne / (ms64 / 1e3) / 1e12
+    return {"workload": "64^3 bricks, p=4, q=3, eps/mu U[1,4], PEC, dt=h/9, c_diss=1",
+            "fp64": {"ms_per_apply": ms64, "gdofs": dof / (ms64 / 1e3) / 1e9,
+                     "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": ach / fp64_peak, "flops_per_element": fp + fa + fd}},
+            "fp32": {"ms_per_apply": ms32, "gdofs": dof / (ms32 / 1e3) / 1e9},
+            "slab_solve_fp64": {"ms": sol64, "iterations": it64, "rc": rc64},
+            "slab_solve_mixed": {"ms": solmx, "iterations": itmx, "rc": rcmx}}
+
+
+def leg_time_refinement(fp64_peak):
+    """48^3 bricks, p=3, q=2, N_K ~ U{1,2,4} per element (local refinement in time, Sec. 2.2)."""
+    import numpy as np
+
+    from paper_1307_5310_gb300 import meshgen, stm
+
+    n, p, q = 48, 3, 2
+    m = meshgen.box_mesh(n, p=p, q=q, order="morton")
+    meshgen.random_materials(m, 1307, 1308)
+    meshgen.random_nk(m, 1309, (1, 2, 4))
+    nk = m["nk"].astype(np.int64)
+    ne = m["hex"].shape[0]
+    dt = (1.0 / n) / (2 * p + 1)
+    dof = int(np.sum(6 * (nk * q + 1) * (p + 1) ** 3))
+    s = stm.Slab(m, tol=1e-9, max_it=400, reorth=False)
+    ms64, _ = time_applies(s, m, dt, stm.STM_FP64, reps=3)
+    ms32, _ = time_applies(s, m, dt, stm.STM_FP32, reps=3)
+    u0 = np.random.Generator(np.random.PCG64(1310)).uniform(-1, 1, s.n_state)
+    sol64, it64, rc64 = _solve_ms(s, u0, dt, reps=1)
+    s.close()
+    smx = stm.Slab(m, precision=stm.STM_MIXED, tol=1e-9, max_it=400, reorth=False)
+    solmx, itmx, rcmx = _solve_ms(smx, u0, dt, reps=1)
+    smx.close()
+    fl = int(np.sum(nk)) * sum(flops_per_element(p, q))  # per sub-interval the work of a q-mode element
+    ach = fl / (ms64 / 1e3) / 1e12
+    by32 = int(np.sum(nk)) * bytes_per_element(p, q, 4)
+    return {"workload": "48^3 bricks, p=3, q=2, N_K~U{1,2,4} (PCG64 1309), eps/mu U[1,4], PEC, dt=h/7",
+            "elements": ne, "dof": dof, "classes": "(p,q,N_K) = (3,2,1|2|4)",
+            "fp64": {"ms_per_apply": ms64, "gdofs": dof / (ms64 / 1e3) / 1e9,
+                     "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": ach / fp64_peak}},
+            "fp32": {"ms_per_apply": ms32, "gdofs": dof / (ms32 / 1e3) / 1e9,
+                     "roofline": {"bound": "hbm", "achieved": by32 / (ms32 / 1e3) / 1e9, "peak": 6780.0,
+                                  "unit": "GB/s", "frac": by32 / (ms32 / 1e3) / 1e9 / 6780.0}},
+            "slab_solve_fp64": {"ms": sol64, "iterations": it64, "rc": rc64},
+            "slab_solve_mixed": {"ms": solmx, "iterations": itmx, "rc": rcmx}}
+
+
 def leg_serving(n_req=48, rate=50.0, seed=1311):
     """Poisson stream (mean `rate` req/s) of cavity/scattering requests, n^3 meshes with n
     log-uniform in [8, 24] (multiples of 4), p ~ U{2..6}, q ~ U{1..3}, random eps/mu boxes and
@@ -563,7 +649,11 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         for name, fn in (("hp_batch", lambda: leg_hp_batch(fp64_peak)), ("curved", lambda: leg_curved(fp64_peak)),
-                         ("serving", leg_serving), ("inexact", leg_inexact)):
+                         ("serving", leg_serving), ("inexact", leg_inexact),
+                         ("dissipative", lambda: leg_dissipative(fp64_peak)),
+                         ("time_refinement", lambda: leg_time_refinement(fp64_peak))):
+            if name not in args.legs.split(","):
+                continue
             try:
                 extra[name] = fn()
             except Exception as ex:  # reported, never replaced by another path

@@ -92,9 +92,9 @@ struct ApplyArgs {
   int nk = 1;
   const uint8_t* nkl = nullptr;
   const T* tmat = nullptr;
-  // uniform brick meshes: non-null means um holds a Krylov vector v and the launch applies
-  // A P^{-1} v, with pinv[e][f][c] = 1 / (mat G_c) the inverse of the block-diagonal
-  // preconditioner P = I (x) mass (Eq. preconditioner) scaling modes >= 1 on load
+  // uniform brick meshes, single-pass FP32 kernel: non-null means um holds a Krylov vector v
+  // and the launch applies A P^{-1} v, with pinv[e][f][c] = 1 / (mat G_c) the inverse of the
+  // block-diagonal preconditioner P = I (x) mass (Eq. preconditioner) scaling modes >= 1 on load
   const T* pinv = nullptr;
 };
 
@@ -168,11 +168,6 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
       else u[0] = A.um[ad.um + fc * ad.um_cs + (k - 1) * Q * N3 + s];
 #pragma unroll
       for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (k * Q + m - 1) * N3 + s];
-      if (!HP && A.pinv) {
-        const T sc = A.pinv[ad.e * 6 + fc];
-#pragma unroll
-        for (int m = 1; m <= Q; ++m) u[m] *= sc;
-      }
       T* yg = A.y + ad.R + fc * (int64_t)(QE * N3) + k * Q * N3 + s;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -316,8 +311,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         T v;
         if (A.mass) {
           const T mc = A.mass[e * 6 + fc];
-          const T um = A.um[ad.um + fc * ad.um_cs + (sk * Q + i) * N3 + s];
-          v = (!HP && A.pinv) ? um : mc * um;  // mass P^{-1} = identity
+          v = mc * A.um[ad.um + fc * ad.um_cs + (sk * Q + i) * N3 + s];
           if (i == 0) {
             // minus mode 0 of the sub-interval: the slab start or the previous sub-interval's end
             if (sk > 0) v = fma(-mc, A.um[ad.um + fc * ad.um_cs + (sk - 1) * Q * N3 + s], v);

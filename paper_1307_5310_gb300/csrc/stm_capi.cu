@@ -411,7 +411,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   a.mass = mass_ptr<T>(c);
   a.kap = kap_ptr<T>(c);
   a.dt_k = (T)dt;
-  // the fused preconditioner exists on the uniform brick path only (callers check)
+  // the fused preconditioner exists in the single-pass FP32 kernel only (callers check)
   a.pinv = pre ? pinv_ptr<T>(c) : nullptr;
   const int N3 = c->N3, Q = c->Q;
   if (c->hp) {
@@ -852,8 +852,8 @@ int gmres_cycle(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n, doubl
       precond_hp<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), c->off_test, c->pq, c->ne, c->stream);
       c->launches += 1;
       if ((rc = linop<S>(c, dt, z, W))) return rc;
-    } else if (sizeof(S) == 4) {
-      // FP32 (memory-bound kernel): P^{-1} on load saves a pass over the basis vector
+    } else if (sizeof(S) == 4 && !c->kap64) {
+      // FP32 single-pass kernel (memory-bound): P^{-1} on load saves a pass over the basis vector
       if ((rc = linop_pre<S>(c, dt, V + (size_t)j * ldv, W))) return rc;
     } else {
       // FP64: the residual kernels are bound by the FP64 pipe, where the scaling costs more
