@@ -101,13 +101,13 @@ struct ApplyArgs {
 __host__ __device__ constexpr int tmat_index(int r, int o) { return (r == 2 ? 0 : (r == 4 ? 2 : 6)) + o; }
 
 // Element-local addressing of one element of class (P, Q).
-template <typename T, int P, int Q, bool HP>
+template <typename T, int P, int Q, bool HP, bool TR = false>
 struct ElemAddr {
   static constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   int64_t e, um, um_cs, u0, u0_cs, R, tr;
   __device__ __forceinline__ ElemAddr(const ApplyArgs<T>& A, int64_t blk) {
     if (HP) {
-      const int QE = A.nk * Q;  // temporal test functions of the element (all sub-intervals)
+      const int QE = TR ? A.nk * Q : Q;  // temporal test functions of the element (all sub-intervals)
       e = A.elist[blk];
       um = A.off_um[e] + (A.um_trial ? N3 : 0);
       um_cs = A.um_trial ? (QE + 1) * N3 : QE * N3;
@@ -150,14 +150,15 @@ __device__ __forceinline__ void line_geom(int a, int t, int& base, int& stride) 
   else { base = t; stride = N * N; }
 }
 
-template <typename T, int P, int Q, bool HP>
+// TR: the mesh has elements with N_K > 1 (HP only); false compiles the one-sub-interval code
+template <typename T, int P, int Q, bool HP, bool TR = false>
 __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
-  const int nk = HP ? A.nk : 1, QE = HP ? nk * Q : Q;
+  const int nk = TR ? A.nk : 1, QE = TR ? nk * Q : Q;
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
-    const ElemAddr<T, P, Q, HP> ad(A, blk);
+    const ElemAddr<T, P, Q, HP, TR> ad(A, blk);
 #pragma unroll 1
     for (int k = 0; k < nk; ++k) {  // temporal sub-intervals (Sec. 2.2)
     for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
@@ -229,13 +230,21 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
 //   N_K' < N_K (own finer, r = N_K/N_K', k = r k' + o): sum_{l<q~} M^{r,o}[i][l] y'_{k',l};
 //   N_K' > N_K (own coarser, r = N_K'/N_K): for i < q~,
 //     sum_{o<r} (1/r) sum_{j<=i} M^{r,o}[j][i] y'_{r k + o, j}.
-template <typename T, int N, int Q, bool HP>
+template <typename T, int N, int Q, bool HP, bool TR = false>
 __device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int nside, int fp, int a, int bi, int i,
                                        int t, int k = 0) {
   if (!HP) {
     constexpr int N2 = N * N;
     const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * Q + i;
     return A.tr[en * (int64_t)(24 * Q * N2) + so * N2 + t];
+  }
+  if (!TR) {  // one sub-interval everywhere
+    const int pq = A.pq[en];
+    const int Nn = (pq & 15) + 1, qn = pq >> 4;
+    const int slow = t / N, fast = t - slow * N;
+    if (i >= qn || slow >= Nn || fast >= Nn) return T(0);
+    const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qn + i;
+    return A.tr[A.off_tr[en] + so * (Nn * Nn) + slow * Nn + fast];
   }
   const int pq = A.pq[en];
   const int Nn = (pq & 15) + 1, qn = pq >> 4;
@@ -281,7 +290,7 @@ struct ApplyShape {
   static constexpr size_t smem = sizeof(T) * 2 * NF * 3 * Q * N3;
 };
 
-template <typename T, int P, int Q, bool HP>
+template <typename T, int P, int Q, bool HP, bool TR = false>
 __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   constexpr int NF = ApplyShape<T, P, Q>::NF;
@@ -289,9 +298,9 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [NF][3][Q][N3]: y of the other field
   T* Rs = ys + NF * FB;                     // [NF][3][Q][N3]: residual rows
-  const int nk = HP ? A.nk : 1, QE = HP ? nk * Q : Q;
+  const int nk = TR ? A.nk : 1, QE = TR ? nk * Q : Q;
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
-    const ElemAddr<T, P, Q, HP> ad(A, blk);
+    const ElemAddr<T, P, Q, HP, TR> ad(A, blk);
     const int64_t e = ad.e;
     const int32_t* nb = A.nbr + e * 6;
 #pragma unroll 1
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
         const int fl = NF == 1 ? 0 : it / FB;
         const int f = f0 + fl, fp = 1 - f;
         const int w = it - fl * FB;
-        ys[it] = A.y[test_ofs<Q, N3, HP>(rk, fp, w, QE)];
+        ys[it] = A.y[test_ofs<Q, N3, TR>(rk, fp, w, QE)];
         const int cc = w / (Q * N3);
         const int r = w - cc * (Q * N3);
         const int i = r / N3, s = r - i * N3;
@@ -318,9 +327,9 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
             else if (A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
           }
         } else {
-          v = A.R[test_ofs<Q, N3, HP>(rk, f, w, QE)];
+          v = A.R[test_ofs<Q, N3, TR>(rk, f, w, QE)];
         }
-        if (A.b) v -= A.b[test_ofs<Q, N3, HP>(rk, f, w, QE)];
+        if (A.b) v -= A.b[test_ofs<Q, N3, TR>(rk, f, w, QE)];
         Rs[it] = v;
       }
       __syncthreads();
@@ -350,10 +359,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           const T xp = tre[(so + 2 * QE) * N2 + t];
           const int ep = nb[2 * a + 1], em = nb[2 * a];
           T jp, jm;
-          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP>(A, ep, 0, fp, a, bi, i, t, sk);
+          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, fp, a, bi, i, t, sk);
           else if (HP && ep == -2) jp = xp - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a + 1]] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jp = (fp == 0) ? xp + xp : T(0);
-          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP>(A, em, 1, fp, a, bi, i, t, sk);
+          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, fp, a, bi, i, t, sk);
           else if (HP && em == -2) jm = xm - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a]] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jm = (fp == 0) ? xm + xm : T(0);
           const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
@@ -368,8 +377,8 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
             const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
             const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * QE + sk * Q + i;
             const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * QE) * N2 + t];
-            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP>(A, ep, 0, f, a, bc, i, t, sk) : (f == 0 ? zp : T(0));
-            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP>(A, em, 1, f, a, bc, i, t, sk) : (f == 0 ? zm : T(0));
+            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, f, a, bc, i, t, sk) : (f == 0 ? zp : T(0));
+            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, f, a, bc, i, t, sk) : (f == 0 ? zm : T(0));
             const T* kp = A.kap + e * 24 + f * 12 + 4 * a + bc;
             const T dp = A.dt_k * kp[2] * gp, dn = A.dt_k * kp[0] * gm;
             // the central-flux lift hf[al] = (dt/2) lv[al] shares the factor lv[al]
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
       }
       for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
         const int fl = NF == 1 ? 0 : it / FB;
-        A.R[test_ofs<Q, N3, HP>(rk, f0 + fl, it - fl * FB, QE)] = Rs[it];
+        A.R[test_ofs<Q, N3, TR>(rk, f0 + fl, it - fl * FB, QE)] = Rs[it];
       }
       __syncthreads();
     }
@@ -583,10 +592,12 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
     if (sm_prep > 48 * 1024) {
       cudaFuncSetAttribute(k_prep<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
       cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+      cudaFuncSetAttribute(k_prep<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
     }
     if (sm_apply > 48 * 1024) {
       cudaFuncSetAttribute(k_apply<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
       cudaFuncSetAttribute(k_apply<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+      cudaFuncSetAttribute(k_apply<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
     }
     if constexpr (sizeof(T) == 4) {
       if (sm_fused > 48 * 1024) {
@@ -611,12 +622,14 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   }
   if (phase != 2) {
     if (ev.start) cudaEventRecord(ev.start, s);
-    if (hp) k_prep<T, P, Q, true><<<grid, block, sm_prep, s>>>(args);
+    if (hp && args.nkl) k_prep<T, P, Q, true, true><<<grid, block, sm_prep, s>>>(args);
+    else if (hp) k_prep<T, P, Q, true><<<grid, block, sm_prep, s>>>(args);
     else k_prep<T, P, Q, false><<<grid, block, sm_prep, s>>>(args);
     if (ev.mid) cudaEventRecord(ev.mid, s);
   }
   if (phase != 1) {
-    if (hp) k_apply<T, P, Q, true><<<grid, block, sm_apply, s>>>(args);
+    if (hp && args.nkl) k_apply<T, P, Q, true, true><<<grid, block, sm_apply, s>>>(args);
+    else if (hp) k_apply<T, P, Q, true><<<grid, block, sm_apply, s>>>(args);
     else k_apply<T, P, Q, false><<<grid, block, sm_apply, s>>>(args);
     if (ev.stop) cudaEventRecord(ev.stop, s);
   }
