@@ -570,8 +570,12 @@ def run_ours(args):
     sm_mhz = clocks["sm_mhz"] or 2070.0
     fp64_peak = 4.0 * SMS * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA / clock / SM
     ach = fl_apply * ne / (apply_ms / 1e3) / 1e12
+    # DRAM bytes per k_apply launch from one ncu capture of the 32^3 case (2.444 GB), scaled by the
+    # element count to this workload; valid for p=4, q=3 on 64^3 only
+    traffic = 2.444e9 * ne / 32 ** 3 if (args.n, args.p, args.q) == (64, 4, 3) else None
     roofline = {"kernel": f"k_apply<double,{args.p},{args.q}>", "bound": "alu", "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 32^3 capture x 8 (bytes)",
                 "peak_source": "FP64 pipe: 2 FMA/clock/SM x 152 SMs x median SM clock under load (of derived)",
                 "launch_ms": apply_ms,
                 "prep": {"kernel": f"k_prep<double,{args.p},{args.q}>", "launch_ms": prep_ms,
