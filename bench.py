@@ -54,6 +54,12 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the extra legs")
     ap.add_argument("--legs", default="hp_batch,curved,serving,inexact,dissipative,time_refinement",
                     help="comma-separated extra legs to run")
+    ap.add_argument("--profile-case", default=None, choices=["apply", "curved", "solve"],
+                    help="run a small fixed case for a profiler and exit (no JSON line): 'apply' = --steps "
+                         "residual applies on --n^3 bricks (p, q), 'curved' = the same on trilinear hexes "
+                         "(q = p - 1), 'solve' = --steps slab solves of the bench workload")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"],
+                    help="precision of --profile-case")
     ap.add_argument("--reorth", type=int, default=0, help="second Gram-Schmidt pass (DGKS test); off by default: same iteration count and accuracy on this workload")
     return ap.parse_args()
 
@@ -690,9 +696,47 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small fixed workloads for profiler captures (the same seeds as the bench legs)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1307_5310_gb300 import meshgen, stm
+
+    n, p = args.n, args.p
+    if args.profile_case == "solve":
+        m = workload(n, p, args.q)
+        prec = {"fp64": stm.STM_FP64, "mixed": stm.STM_MIXED}[args.precision]
+        s = stm.Slab(m, precision=prec, tol=args.tol, max_it=400, reorth=bool(args.reorth))
+        u = torch.from_numpy(np.random.Generator(np.random.PCG64(1310)).uniform(-1, 1, s.n_state)).cuda()
+        for _ in range(args.steps):
+            s.set_state(u)
+            rc, rep = s.slab_solve(1.0 / n / (2 * p + 1))
+        torch.cuda.synchronize()
+        print("ok", rc, rep)
+        return
+    q = p - 1 if args.profile_case == "curved" else args.q
+    m = meshgen.box_mesh(n, p=p, q=q, order="morton", perturb=0.1 if args.profile_case == "curved" else 0.0)
+    meshgen.random_materials(m, 1307, 1308)
+    s = stm.Slab(m)
+    dtp = torch.float64 if args.precision == "fp64" else torch.float32
+    U = torch.empty(s.n_trial, dtype=dtp, device="cuda").uniform_(-1, 1)
+    R = torch.empty(s.n_test, dtype=dtp, device="cuda")
+    prec = stm.STM_FP64 if args.precision == "fp64" else stm.STM_FP32
+    for _ in range(args.steps):
+        s.residual_apply(U, R, 0.0, 1.0 / n / (2 * p + 1), prec=prec)
+    torch.cuda.synchronize()
+    print("ok", float(R.abs().sum()))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
