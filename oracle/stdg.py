@@ -411,6 +411,19 @@ class Oracle:
         return np.stack([RE, RH], axis=1)
 
     # -- face terms ------------------------------------------------------------
+    @staticmethod
+    def _common_test_factors(q, nk, q2, nk2, tau, wt, Lt):
+        """Pi~ L at the time points tau: the L2 projection (Eq. bilinearform:S) of the own
+        temporal test factors Lt [N_K q, T] onto the largest common test space of the two
+        elements, piecewise P_{min(q,q2)-1} on the coarser of the two (nested) partitions.
+        None when that space is the own test space (Pi~ = identity on it)."""
+        qt = min(q, q2)
+        if qt == q and nk2 >= nk:
+            return None
+        Lc = test_time_nk(qt, min(nk, nk2), tau)
+        gram = np.einsum("kt,t,lt->kl", Lc, wt, Lc)
+        return np.linalg.solve(gram, np.einsum("kt,t,it->ki", Lc, wt, Lt)).T @ Lc
+
     def _face(self, e, f, e2, rect, uE, uH, vE, vH, dt, t0, g):
         """Contribution of one piece of face f of e (neighbour e2 or -1) to the rows of e.
 
@@ -465,14 +478,7 @@ class Oracle:
             RE = _test_project(_cross(Havg, nn), pts, Lt, wgt)
             # H-eq: -<[E]_T, {w}> , {w} = w / 2
             RH = _test_project(-0.5 * jE, pts, Lt, wgt)
-            qt = min(q, q2)
-            # Pi~ L: L2 projection of the own temporal test factors onto the largest common
-            # test space, piecewise P_{qt-1} on the coarser partition (None: own space itself)
-            PL = None
-            if qt < q or nk2 < nk:
-                Lc = test_time_nk(qt, min(nk, nk2), tau)
-                gram = np.einsum("kt,t,lt->kl", Lc, wt, Lc)
-                PL = np.linalg.solve(gram, np.einsum("kt,t,it->ki", Lc, wt, Lt)).T @ Lc
+            PL = self._common_test_factors(q, nk, q2, nk2, tau, wt, Lt)
             if self.c_diss > 0:
                 # D_h: <alpha [F]_T, [Pi~ v]_T>; for the rows of e, [v]_T = n x v, and
                 # a . (n x v) = v . (a x n)

@@ -591,6 +591,26 @@ def test_energy_identity_time_refinement(uneven_q):
     assert abs(lhs - dE) <= 1e-12 * max(1.0, abs(dE))
 
 
+def test_planted_time_refinement_mistakes_fail_pins(monkeypatch):
+    """With mixed N_K, dropping S_h or projecting onto the finer partition breaks the
+    energy identity (Theorem 4.1)."""
+    m = meshgen.box_mesh(2, p=1, q=2)
+    m["nk"] = np.array([1, 2, 4, 2, 1, 4, 2, 1], dtype=np.uint8)
+    meshgen.random_materials(m, 5, 6)
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) <= 1e-12 * max(1.0, abs(dE))
+    orig = stdg.Oracle._common_test_factors
+    monkeypatch.setattr(stdg.Oracle, "_common_test_factors", staticmethod(lambda *a: None))
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) > 1e-6
+
+    def finer(q, nk, q2, nk2, tau, wt, Lt):
+        return orig(q, nk, q2, nk2, tau, wt, Lt) if nk2 == nk else orig(q, nk, q2, max(nk, nk2), tau, wt, Lt)
+    monkeypatch.setattr(stdg.Oracle, "_common_test_factors", staticmethod(finer))
+    lhs, dE = _energy_identity(m)
+    assert abs(lhs - dE) > 1e-6
+
+
 def test_patch_time_refinement():
     """E = (0,0,x), H = (0,t,0), g = E with N_K in {1, 2, 4} and q >= 2: exact
     (the linear-in-t H lies in every common test space)."""
