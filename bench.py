@@ -520,6 +520,25 @@ def leg_serving(n_req=48, rate=50.0, seed=1311):
                         "1-4 eps/mu boxes U[1,4], 1-3 Gaussian pulses, cavity or scattering, 10 slabs to 1e-9"}
 
 
+def dist_max(v, device="cuda"):
+    """Maximum of v over all ranks of the default process group (v itself without one):
+    the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms_max):
+    """Units per second of the whole job: every replica processes units_per_rank, the job
+    ends with the slowest replica (weak scaling, no data-path collective)."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -541,11 +560,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return dist_max(v, "cuda")
 
     m = workload(args.n, args.p, args.q)
     ne = m["hex"].shape[0]
@@ -566,7 +581,7 @@ def run_ours(args):
     ms = max_over_ranks(r64["ms"])
     prof = r64["prof"]
     applies = prof["k_apply_fp64"][1] / args.steps
-    value = world * dof_slab * applies / (ms / 1e3) / 1e9
+    value = whole_job_rate(world, dof_slab * applies, ms) / 1e9
     u64 = torch.empty_like(u_init)
     s.get_state(u64)
 
@@ -612,7 +627,7 @@ def run_ours(args):
         parts[2] += d - c_
         per_step.append([round((b - a) * 1e3, 2), round((c_ - b) * 1e3, 2), round((d - c_) * 1e3, 2)])
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
-    e2e = {"value": world * dof_slab * applies / (e2e_ms / 1e3) / 1e9, "unit": "GDoF/s",
+    e2e = {"value": whole_job_rate(world, dof_slab * applies, e2e_ms) / 1e9, "unit": "GDoF/s",
            "h2d_bytes_per_step": int(uh.nbytes), "d2h_bytes_per_step": int(oh.nbytes), "ms_per_step": e2e_ms,
            "path": "stm_set_state (host) + stm_slab_solve + stm_get_state (host), buffers from stm_host_alloc",
            "ms_set_solve_get": [x * 1e3 / args.steps for x in parts], "ms_set_solve_get_per_step": per_step}
@@ -638,7 +653,7 @@ def run_ours(args):
         pm = rmx["prof"]
         ap64, ap32 = pm["k_apply_fp64"][1] / args.steps, pm["k_apply_fp32"][1] / args.steps
         mixed = {"ms_per_solve": msx, "slab_solves_per_s": world / (msx / 1e3),
-                 "gdofs": world * dof_slab * (ap64 + ap32) / (msx / 1e3) / 1e9,
+                 "gdofs": whole_job_rate(world, dof_slab * (ap64 + ap32), msx) / 1e9,
                  "fp64_applies": ap64, "fp32_applies": ap32, "inner_iterations": rmx["iterations"],
                  "outer_refinements": rmx["restarts"], "rel_residual": rmx["rel_residual"],
                  "rel_err_vs_fp64_ref": float(torch.linalg.norm(umx - uref) / torch.linalg.norm(uref)),
