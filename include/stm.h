@@ -186,6 +186,19 @@ typedef void (*stm_st_field_fn)(void *user, int64_t npts, const double *xt /*[np
                                 double *out /*[npts][3]*/);
 int32_t stm_set_boundary(stm_ctx *ctx, stm_st_field_fn g, void *user);
 
+/* Current density J of Eq. maxwell sampled on the host: l_E(v) = (J, v) over
+ * I_n x K (Eq. bilinearform:C), by (p+2)^3 Gauss points per element and q+2 in
+ * time; the callback gets npts space-time points (x, y, z, t) and writes J.
+ * Added to the Gaussian sources of stm_set_source_gauss.  Meshes with one
+ * (p, q) (bricks or trilinear); NULL removes it.  The library keeps the
+ * pointer; the caller keeps the callback alive while the context uses it. */
+int32_t stm_set_source(stm_ctx *ctx, stm_st_field_fn J, void *user);
+
+/* Per-element block offsets ([n_elem + 1] each, filled when non-NULL) of the
+ * trial layout (stm_residual_apply's U), the test layout (R, unknowns) and the
+ * state layout (stm_set_state / stm_get_state). */
+int32_t stm_dof_layout(stm_ctx *ctx, int64_t *off_trial, int64_t *off_test, int64_t *off_state);
+
 /* Solve one slab (Sec. 5.4): find modes 1..q of U with R_h(U) = 0 by GMRES
  * (restart opts.restart, right preconditioned by the time-derivative terms of
  * Eq. preconditioner), starting from the state; on return the state is the

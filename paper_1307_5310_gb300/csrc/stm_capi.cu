@@ -256,6 +256,8 @@ struct stm_ctx {
   std::vector<stm_gauss_src> srcs;
   stm_st_field_fn gfn = nullptr;
   void* guser = nullptr;
+  stm_st_field_fn jfn = nullptr;  // current density J(x, t) sampled on the host
+  void* juser = nullptr;
   double* load64 = nullptr;
   float* load32 = nullptr;
   bool load_valid = false;
@@ -552,12 +554,116 @@ int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* o
   return apply<double>(c, dt, xin, L_TEST, c->state, L_STATE, b, out);
 }
 
+// l_E(v) = (J, v) over I_n x K for a current density sampled on the host (Eq.
+// bilinearform:C), added into the E rows of hb.  With the covariant test
+// functions v = DF^{-T} phi_s e_c, J . v |J| = (adj(DF) J)_c phi_s, so per
+// element: values a = adj(DF) J at the (p+2)^3 x (q+2) Gauss points, weighted
+// and contracted with L_i in time, then projected on phi_s by three 1-D
+// contractions.  The trilinear map of the 8 vertices covers bricks and curved
+// elements alike.
+void add_host_current(stm_ctx* c, double t0, double dt, const std::vector<double>& xq,
+                      const std::vector<double>& wq, const std::vector<double>& xt, const std::vector<double>& wt,
+                      const std::vector<double>& Lq, const std::vector<double>& Lt, std::vector<double>& hb) {
+  const int Q = c->Q, N = c->N, N3 = c->N3, nq = (int)xq.size(), nt = (int)xt.size(), nq3 = nq * nq * nq;
+  const int64_t per_el = (int64_t)nt * nq3;
+  const int64_t chunk = std::max<int64_t>(1, (1 << 20) / per_el);
+  std::vector<double> xtp, jv, adj;
+  std::vector<double> F(3 * (size_t)Q * nq3), G1, G2;
+  for (int64_t e0 = 0; e0 < c->ne; e0 += chunk) {
+    const int64_t e1 = std::min<int64_t>(c->ne, e0 + chunk), ncnt = e1 - e0;
+    xtp.resize(4 * ncnt * per_el);
+    jv.resize(3 * ncnt * per_el);
+    adj.resize(9 * ncnt * nq3);
+    for (int64_t e = e0; e < e1; ++e) {
+      const double* X = &c->h_X8[24 * e];
+      for (int g = 0; g < nq3; ++g) {
+        const double xh[3] = {xq[g % nq], xq[(g / nq) % nq], xq[g / (nq * nq)]};
+        double x[3] = {0, 0, 0}, DF[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int v = 0; v < 8; ++v) {
+          const int bit[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+          double fa[3], dfa[3];
+          for (int a = 0; a < 3; ++a) {
+            fa[a] = bit[a] ? xh[a] : 1.0 - xh[a];
+            dfa[a] = bit[a] ? 1.0 : -1.0;
+          }
+          const double Nv = fa[0] * fa[1] * fa[2];
+          const double dN[3] = {dfa[0] * fa[1] * fa[2], fa[0] * dfa[1] * fa[2], fa[0] * fa[1] * dfa[2]};
+          for (int i = 0; i < 3; ++i) {
+            x[i] += Nv * X[3 * v + i];
+            for (int j = 0; j < 3; ++j) DF[i][j] += X[3 * v + i] * dN[j];
+          }
+        }
+        // adj(DF) = |J| DF^{-1} (cofactor transpose)
+        double* A = &adj[9 * ((e - e0) * nq3 + g)];
+        A[0] = DF[1][1] * DF[2][2] - DF[1][2] * DF[2][1];
+        A[1] = DF[0][2] * DF[2][1] - DF[0][1] * DF[2][2];
+        A[2] = DF[0][1] * DF[1][2] - DF[0][2] * DF[1][1];
+        A[3] = DF[1][2] * DF[2][0] - DF[1][0] * DF[2][2];
+        A[4] = DF[0][0] * DF[2][2] - DF[0][2] * DF[2][0];
+        A[5] = DF[0][2] * DF[1][0] - DF[0][0] * DF[1][2];
+        A[6] = DF[1][0] * DF[2][1] - DF[1][1] * DF[2][0];
+        A[7] = DF[0][1] * DF[2][0] - DF[0][0] * DF[2][1];
+        A[8] = DF[0][0] * DF[1][1] - DF[0][1] * DF[1][0];
+        for (int tq = 0; tq < nt; ++tq) {
+          double* p = &xtp[4 * ((e - e0) * per_el + (int64_t)tq * nq3 + g)];
+          p[0] = x[0];
+          p[1] = x[1];
+          p[2] = x[2];
+          p[3] = t0 + dt * xt[tq];
+        }
+      }
+    }
+    c->jfn(c->juser, ncnt * per_el, xtp.data(), jv.data());
+    for (int64_t e = e0; e < e1; ++e) {
+      std::fill(F.begin(), F.end(), 0.0);
+      for (int tq = 0; tq < nt; ++tq)
+        for (int g = 0; g < nq3; ++g) {
+          const double* J = &jv[3 * ((e - e0) * per_el + (int64_t)tq * nq3 + g)];
+          const double* A = &adj[9 * ((e - e0) * nq3 + g)];
+          const double w = dt * wt[tq] * wq[g % nq] * wq[(g / nq) % nq] * wq[g / (nq * nq)];
+          for (int cc = 0; cc < 3; ++cc) {
+            const double a = w * (A[3 * cc] * J[0] + A[3 * cc + 1] * J[1] + A[3 * cc + 2] * J[2]);
+            for (int i = 0; i < Q; ++i) F[((size_t)cc * Q + i) * nq3 + g] += Lt[tq * kMaxQ + i] * a;
+          }
+        }
+      // project on phi_s = L_j(x^) L_k(y^) L_l(z^): contract x, then y, then z
+      for (int ci = 0; ci < 3 * Q; ++ci) {
+        const double* f0 = &F[(size_t)ci * nq3];
+        G1.assign((size_t)nq * nq * N, 0.0);
+        for (int gz = 0; gz < nq; ++gz)
+          for (int gy = 0; gy < nq; ++gy)
+            for (int j = 0; j < N; ++j) {
+              double acc = 0.0;
+              for (int gx = 0; gx < nq; ++gx) acc += f0[(gz * nq + gy) * nq + gx] * Lq[gx * N + j];
+              G1[(gz * nq + gy) * N + j] = acc;
+            }
+        G2.assign((size_t)nq * N * N, 0.0);
+        for (int gz = 0; gz < nq; ++gz)
+          for (int k = 0; k < N; ++k)
+            for (int j = 0; j < N; ++j) {
+              double acc = 0.0;
+              for (int gy = 0; gy < nq; ++gy) acc += G1[(gz * nq + gy) * N + j] * Lq[gy * N + k];
+              G2[(gz * N + k) * N + j] = acc;
+            }
+        double* row = &hb[(size_t)e * 6 * Q * N3 + (size_t)ci * N3];  // E rows: field 0, (comp, mode) = ci
+        for (int l = 0; l < N; ++l)
+          for (int k = 0; k < N; ++k)
+            for (int j = 0; j < N; ++j) {
+              double acc = 0.0;
+              for (int gz = 0; gz < nq; ++gz) acc += G2[(gz * N + k) * N + j] * Lq[gz * N + l];
+              row[(l * N + k) * N + j] += acc;
+            }
+      }
+    }
+  }
+}
+
 // Load vector b = L on the slab (t0, t0 + dt] (Eq. bilinearform:C): Gaussian
 // currents on the device, boundary data g on the host.  Returns null when no
 // source and no boundary data are set (L = 0).  Cached per (t0, dt).
 int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   *out = nullptr;
-  if (c->srcs.empty() && !c->gfn) return STM_OK;
+  if (c->srcs.empty() && !c->gfn && !c->jfn) return STM_OK;
   if (c->hp) return fail(c, STM_EUNSUPPORTED, "sources and boundary data are handled on uniform (p, q) meshes only");
   if (c->load_valid && c->load_t0 == t0 && c->load_dt == dt) {
     *out = c->load64;
@@ -578,10 +684,12 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   std::vector<double> Lq(nq * N), Lt(nt * Q > 0 ? nt * kMaxQ : 1);
   for (int g = 0; g < nq; ++g) legendre01(N, xq[g], &Lq[g * N]);
   for (int g = 0; g < nt; ++g) legendre01(Q, xt[g], &Lt[g * kMaxQ]);
-  if (c->gfn) {
+  if (c->gfn || c->jfn) {
+    std::vector<double> hb(n, 0.0);
+    if (c->jfn) add_host_current(c, t0, dt, xq, wq, xt, wt, Lq, Lt, hb);
+    if (c->gfn) {
     // l_H(w) = -<n x g, w> on boundary faces; in the reference face (Nanson, covariant
     // transform) <n x g, w> = dt int int (n^ x g^) . w^ with g^ = DF^T g.
-    std::vector<double> hb(n, 0.0);
     std::vector<int64_t> faces;
     for (int64_t e = 0; e < c->ne; ++e)
       for (int f = 0; f < 6; ++f)
@@ -695,6 +803,7 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
               }
             }
       }
+    }
     }
     STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
@@ -1718,6 +1827,23 @@ int32_t stm_set_boundary(stm_ctx* c, stm_st_field_fn g, void* user) {
   c->gfn = g;
   c->guser = user;
   c->load_valid = false;
+  return STM_OK;
+}
+
+int32_t stm_set_source(stm_ctx* c, stm_st_field_fn J, void* user) {
+  if (!c) return STM_EINVAL;
+  c->jfn = J;
+  c->juser = user;
+  c->load_valid = false;
+  return STM_OK;
+}
+
+int32_t stm_dof_layout(stm_ctx* c, int64_t* off_trial, int64_t* off_test, int64_t* off_state) {
+  if (!c) return STM_EINVAL;
+  const size_t n = (size_t)c->ne + 1;
+  if (off_trial) std::copy(c->h_off_trial.begin(), c->h_off_trial.begin() + n, off_trial);
+  if (off_test) std::copy(c->h_off_test.begin(), c->h_off_test.begin() + n, off_test);
+  if (off_state) std::copy(c->h_off_state.begin(), c->h_off_state.begin() + n, off_state);
   return STM_OK;
 }
 

@@ -39,7 +39,7 @@ EXPORTS = (
     "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply",
     "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
-    "stm_set_source_gauss", "stm_set_boundary",
+    "stm_set_source_gauss", "stm_set_boundary", "stm_set_source", "stm_dof_layout",
     "stm_server_create", "stm_server_submit", "stm_server_poll", "stm_server_wait", "stm_server_stats",
     "stm_server_destroy", "stm_autotune", "stm_host_alloc", "stm_host_free",
 )
@@ -126,6 +126,8 @@ def lib() -> C.CDLL:
         L.stm_residual_apply_noalloc.argtypes = [i64, i32, i32, d, vp, vp, vp, vp, vp, vp, i64]
         L.stm_set_source_gauss.argtypes = [vp, C.POINTER(stm_gauss_src), i32]
         L.stm_set_boundary.argtypes = [vp, ST_FIELD_FN, vp]
+        L.stm_set_source.argtypes = [vp, ST_FIELD_FN, vp]
+        L.stm_dof_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         L.stm_server_create.argtypes = [C.POINTER(vp), C.POINTER(stm_server_opts)]
         L.stm_server_submit.argtypes = [vp, C.POINTER(stm_request), C.POINTER(i64)]
         L.stm_server_poll.argtypes = [vp, i64, C.POINTER(stm_result), vp]
@@ -252,6 +254,7 @@ class Slab:
         nt, ns, nst = C.c_int64(), C.c_int64(), C.c_int64()
         L.stm_sizes(h, C.byref(nt), C.byref(ns), C.byref(nst))
         self.n_trial, self.n_test, self.n_state = nt.value, ns.value, nst.value
+        self.n_elem = ne
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -341,6 +344,26 @@ class Slab:
             arr[k].sigma_x, arr[k].t0 = sd["sigma_x"], sd["t0"]
             arr[k].sigma_t, arr[k].amp = sd["sigma_t"], sd["amp"]
         return self._check(lib().stm_set_source_gauss(self.ctx, arr, len(sources)))
+
+    def set_source(self, J=None):
+        """J(x [n,3], t [n]) -> [n,3] current density, sampled on the host; None removes it."""
+        if J is None:
+            self._keep.pop("J", None)
+            return self._check(lib().stm_set_source(self.ctx, C.cast(None, ST_FIELD_FN), None))
+
+        def cb(_user, n, xt, out):
+            a = np.ctypeslib.as_array(xt, shape=(n, 4))
+            np.ctypeslib.as_array(out, shape=(n, 3))[:] = J(a[:, :3], a[:, 3])
+        f = ST_FIELD_FN(cb)
+        self._keep["J"] = f
+        return self._check(lib().stm_set_source(self.ctx, f, None))
+
+    def dof_layout(self):
+        """(trial, test, state) per-element block offsets, each [n_elem + 1]."""
+        n = self.n_elem + 1
+        out = [np.empty(n, np.int64) for _ in range(3)]
+        self._check(lib().stm_dof_layout(self.ctx, *[a.ctypes.data_as(C.POINTER(C.c_int64)) for a in out]))
+        return tuple(out)
 
     def set_boundary(self, g=None):
         """g(x [n,3], t [n]) -> [n,3] boundary data of n x E = n x g; None = PEC."""

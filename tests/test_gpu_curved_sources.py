@@ -188,3 +188,39 @@ def test_curved_full_size_sampled(stm):
     for e in sample:
         Ro = o.element_residual(loc[e], Us, 0.18, dt, src=oracle_J(src))[0].ravel()
         assert rel(R[e * per:(e + 1) * per], Ro) < 1e-12, e
+
+
+@pytest.mark.parametrize("curved", [False, True])
+def test_host_current_source(stm, curved):
+    """J(x, t) sampled on the host (stm_set_source): residual vs the oracle's load (J, v),
+    on bricks and trilinear hexes; removing it restores the source-free residual."""
+    m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.7, 0.9), p=3, q=2, perturb=0.2 if curved else 0.0)
+    meshgen.random_materials(m, 31, 32)
+    o = stdg.Oracle(m)
+
+    def J(x, t):
+        x0, x1, x2 = x[..., 0], x[..., 1], x[..., 2]
+        return np.stack(np.broadcast_arrays(np.sin(2 * x0 + t) * x1, np.cos(x2 - t) + 0 * x0, x0 * x1 * x2 * (1 + t)), -1)
+
+    U = meshgen.random_coeffs(m, 33)
+    t0, dt = 0.1, 0.07
+    s = stm.Slab(m)
+    s.set_source(J)
+    R = np.empty(s.n_test)
+    s.residual_apply(U, R, t0, dt)
+    Ro = o.residual(U, t0, dt, src=J)
+    assert rel(R, Ro) < 1e-12
+    s.set_source(None)
+    s.residual_apply(U, R, t0, dt)
+    assert rel(R, o.residual(U, t0, dt)) < 1e-12
+
+
+def test_dof_layout(stm):
+    m = meshgen.box_mesh(2, p=2, q=2)
+    m["p"] = np.array([1, 2, 3, 1, 2, 3, 1, 2], dtype=np.uint8)
+    m["q"] = np.array([1, 2, 3, 1, 2, 3, 1, 2], dtype=np.uint8)
+    s = stm.Slab(m)
+    tr, te, st = s.dof_layout()
+    assert np.array_equal(tr, meshgen.dof_offsets(m, "trial"))
+    assert np.array_equal(te, meshgen.dof_offsets(m, "test"))
+    assert st[-1] == s.n_state and tr[-1] == s.n_trial and te[-1] == s.n_test
