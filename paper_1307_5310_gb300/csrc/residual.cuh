@@ -230,30 +230,36 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
 //   N_K' < N_K (own finer, r = N_K/N_K', k = r k' + o): sum_{l<q~} M^{r,o}[i][l] y'_{k',l};
 //   N_K' > N_K (own coarser, r = N_K'/N_K): for i < q~,
 //     sum_{o<r} (1/r) sum_{j<=i} M^{r,o}[j][i] y'_{r k + o, j}.
+//
+// Uneven degrees: fc holds, per face of the element, the neighbour's trace
+// offset, degrees p | q << 4 and N_K (k_apply keeps them in shared memory, so
+// a line needs one dependent load, not three).
+struct FaceCache {
+  int64_t off[6];
+  int pq[6], nk[6];
+};
+
 template <typename T, int N, int Q, bool HP, bool TR = false>
 __device__ __forceinline__ T nbr_trace(const ApplyArgs<T>& A, int64_t en, int nside, int fp, int a, int bi, int i,
-                                       int t, int k = 0) {
+                                       int t, int k, const FaceCache& fc, int face) {
   if (!HP) {
     constexpr int N2 = N * N;
     const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * Q + i;
     return A.tr[en * (int64_t)(24 * Q * N2) + so * N2 + t];
   }
-  if (!TR) {  // one sub-interval everywhere
-    const int pq = A.pq[en];
-    const int Nn = (pq & 15) + 1, qn = pq >> 4;
-    const int slow = t / N, fast = t - slow * N;
-    if (i >= qn || slow >= Nn || fast >= Nn) return T(0);
-    const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qn + i;
-    return A.tr[A.off_tr[en] + so * (Nn * Nn) + slow * Nn + fast];
-  }
-  const int pq = A.pq[en];
+  const int pq = fc.pq[face];
   const int Nn = (pq & 15) + 1, qn = pq >> 4;
   const int slow = t / N, fast = t - slow * N;
+  if (!TR) {  // one sub-interval everywhere
+    if (i >= qn || slow >= Nn || fast >= Nn) return T(0);
+    const int64_t so = ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qn + i;
+    return A.tr[fc.off[face] + so * (Nn * Nn) + slow * Nn + fast];
+  }
   const int qt = qn < Q ? qn : Q;
   // rows i >= qt vanish in every case (M^{r,o}[i][l] = 0 for l < i: L_i is orthogonal to P_l)
   if (i >= qt || slow >= Nn || fast >= Nn) return T(0);
-  const int nkn = A.nkl ? 1 << A.nkl[en] : 1, qen = nkn * qn, nn2 = Nn * Nn;
-  const T* src = A.tr + A.off_tr[en] + ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qen * nn2 + slow * Nn + fast;
+  const int nkn = fc.nk[face], qen = nkn * qn, nn2 = Nn * Nn;
+  const T* src = A.tr + fc.off[face] + ((((int64_t)fp * 3 + a) * 2 + nside) * 2 + bi) * qen * nn2 + slow * Nn + fast;
   if (nkn == A.nk) return src[(int64_t)(k * qn + i) * nn2];
   if (nkn < A.nk) {
     const int r = A.nk / nkn, kk = k / r, o = k - kk * r;
@@ -298,11 +304,18 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [NF][3][Q][N3]: y of the other field
   T* Rs = ys + NF * FB;                     // [NF][3][Q][N3]: residual rows
+  __shared__ FaceCache fcs;                 // uneven degrees only
   const int nk = TR ? A.nk : 1, QE = TR ? nk * Q : Q;
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
     const ElemAddr<T, P, Q, HP, TR> ad(A, blk);
     const int64_t e = ad.e;
     const int32_t* nb = A.nbr + e * 6;
+    if (HP && threadIdx.x < 6) {  // read after the first barrier below
+      const int f = threadIdx.x, en = nb[f];
+      fcs.off[f] = en >= 0 ? A.off_tr[en] : (en == -2 ? A.hoff[A.hslot[e * 6 + f]] : 0);
+      fcs.pq[f] = en >= 0 ? A.pq[en] : 0;
+      fcs.nk[f] = (en >= 0 && A.nkl) ? 1 << A.nkl[en] : 1;
+    }
 #pragma unroll 1
     for (int sk = 0; sk < nk; ++sk) {  // temporal sub-intervals (Sec. 2.2)
     const int64_t rk = ad.R + (int64_t)sk * Q * N3;  // sub-interval sk's rows start here (per component)
@@ -359,11 +372,11 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           const T xp = tre[(so + 2 * QE) * N2 + t];
           const int ep = nb[2 * a + 1], em = nb[2 * a];
           T jp, jm;
-          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, fp, a, bi, i, t, sk);
-          else if (HP && ep == -2) jp = xp - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a + 1]] + ((fp * 2 + bi) * Q + i) * N2 + t];
+          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, fp, a, bi, i, t, sk, fcs, 2 * a + 1);
+          else if (HP && ep == -2) jp = xp - A.hbuf[fcs.off[2 * a + 1] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jp = (fp == 0) ? xp + xp : T(0);
-          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, fp, a, bi, i, t, sk);
-          else if (HP && em == -2) jm = xm - A.hbuf[A.hoff[A.hslot[e * 6 + 2 * a]] + ((fp * 2 + bi) * Q + i) * N2 + t];
+          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, fp, a, bi, i, t, sk, fcs, 2 * a);
+          else if (HP && em == -2) jm = xm - A.hbuf[fcs.off[2 * a] + ((fp * 2 + bi) * Q + i) * N2 + t];
           else jm = (fp == 0) ? xm + xm : T(0);
           const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
           T yv[N];
@@ -377,8 +390,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
             const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
             const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * QE + sk * Q + i;
             const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * QE) * N2 + t];
-            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, f, a, bc, i, t, sk) : (f == 0 ? zp : T(0));
-            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, f, a, bc, i, t, sk) : (f == 0 ? zm : T(0));
+            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, f, a, bc, i, t, sk, fcs, 2 * a + 1)
+                                   : (f == 0 ? zp : T(0));
+            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, f, a, bc, i, t, sk, fcs, 2 * a)
+                                   : (f == 0 ? zm : T(0));
             const T* kp = A.kap + e * 24 + f * 12 + 4 * a + bc;
             const T dp = A.dt_k * kp[2] * gp, dn = A.dt_k * kp[0] * gm;
             // the central-flux lift hf[al] = (dt/2) lv[al] shares the factor lv[al]
@@ -594,7 +609,7 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
       cudaFuncSetAttribute(k_prep<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
     }
-    if (sm_apply > 48 * 1024) {
+    if (sm_apply > 47 * 1024) {  // k_apply also has a little static shared memory
       cudaFuncSetAttribute(k_apply<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
       cudaFuncSetAttribute(k_apply<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
       cudaFuncSetAttribute(k_apply<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
