@@ -29,7 +29,17 @@
 //             gives both opposite faces (X+ = e + o at x^_a = 1, X- = e - o).
 //   k_apply : R = mass + per output component two line passes (one per axis
 //             a != c) each doing the 1-D derivative D along a and the lift of
-//             the jumps on the two faces normal to a.
+//             the jumps on the two faces normal to a (folded into the curl
+//             operand: D_ab and the lift share the factor L_a(1)).
+// and a single-pass FP32 variant (k_fused) for uniform brick meshes.
+//
+// Extensions carried by the same kernels: per-element degrees (HP: element
+// lists per (p, q, N_K) class, offset arrays, truncated or padded neighbour
+// face modes, temporal modes cut at min(q, q') for S_h of Eq.
+// bilinearform:S), 2:1 faces (equivalent traces from k_hang), local
+// refinement in time (TR: N_K sub-intervals per element, temporal transfer to
+// neighbours with another partition), the dissipative term D_h of Sec. 4.2
+// (kap), and the preconditioner on load in k_fused (pinv).
 #pragma once
 
 #include <cuda_runtime.h>
