@@ -26,7 +26,9 @@ __device__ double block_sum(double v, double* sh) {
 }
 
 // Per-thread accumulator: FP64 for double storage; for float storage, FP32
-// sums of the 4 products of one 16-byte chunk flushed into an FP64 total.
+// sums of the 16 products of four 16-byte chunks flushed into an FP64 total
+// (the kernels call flush() after every fourth chunk: one conversion and one
+// FP64 add per 16 products keeps the FP64 pipe off the critical path).
 template <typename S>
 struct Acc;
 template <>
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const S* __restrict__ 
   const int64_t nv = n / W;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   const VT* w4 = reinterpret_cast<const VT*>(w);
+  int chunks = 0;
   for (int64_t c0 = tid; c0 < nv; c0 += nth * U) {
     VT wv[U], vv[U][K > 0 ? K : 1];
 #pragma unroll
@@ -109,8 +112,10 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const S* __restrict__ 
           for (int i = 0; i < K; ++i) acc[i].add(x, Vec<S>::get(vv[u][i], l));
           if (with_norm) acc[K].add(x, x);
         }
+        if ((++chunks & 3) == 0) {
 #pragma unroll
-        for (int i = 0; i <= K; ++i) acc[i].flush();
+          for (int i = 0; i <= K; ++i) acc[i].flush();
+        }
       }
     }
   }
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(S* __restrict__ w, co
   const int64_t nv = n / W;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   VT* w4 = reinterpret_cast<VT*>(w);
+  int chunks = 0;
   for (int64_t c0 = tid; c0 < nv; c0 += nth * U) {
     VT wv[U], vv[U][K > 0 ? K : 1];
 #pragma unroll
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(S* __restrict__ w, co
           Vec<S>::set(wv[u], l, x);
           acc.add(x, x);
         }
-        acc.flush();
+        if ((++chunks & 3) == 0) acc.flush();
         if (K > 0) w4[cix] = wv[u];
       }
     }
