@@ -639,3 +639,47 @@ def test_patch_time_refinement():
     assert np.abs(o.residual(U, t0, dt, g=g)).max() < 1e-12
     Us = o.slab_solve(u0, t0, dt, g=g)
     assert np.abs(Us - U).max() < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Sec. 6.1.2: manufactured solution with a current, local refinement in time
+# --------------------------------------------------------------------------
+
+def _mms_fields(x, t):
+    """E = e^t x(x-1)z(1-z) e_y, H = e^t x(x-1)(1-2z) e_x - e^t (2x-1)z(1-z) e_z on the unit
+    cube (eps = mu = 1): H solves mu dH/dt + curl E = 0, the current is J = dE/dt - curl H,
+    and n x E = 0 on the whole boundary (PEC)."""
+    X, Z = x[..., 0], x[..., 2]
+    zero = np.zeros(np.broadcast(X, t).shape)
+    et = np.exp(t)
+    E = np.stack([zero, et * X * (X - 1) * Z * (1 - Z) + zero, zero], -1)
+    H = np.stack([et * X * (X - 1) * (1 - 2 * Z) + zero, zero, -et * (2 * X - 1) * Z * (1 - Z) + zero], -1)
+    J = np.stack([zero, et * (X * (X - 1) * Z * (1 - Z) + 2 * X * (X - 1) - 2 * Z * (1 - Z)) + zero, zero], -1)
+    return E, H, J
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_mms_nodal_superconvergence_time_refinement(q):
+    """The fields are quadratic in x and z, so Q_2 in space represents them exactly and only
+    the time discretisation errs: at the slab ends cG(q) converges with order 2q (the nodal
+    superconvergence the paper reports in Sec. 6.1.2), here with N_K in {1, 2} mixed."""
+    m = meshgen.box_mesh(2, p=2, q=q)
+    m["nk"] = np.array([1, 2, 1, 2, 2, 1, 2, 1], dtype=np.uint8)
+    o = stdg.Oracle(m)
+    E0 = lambda x: _mms_fields(x, 0.0)[0]
+    H0 = lambda x: _mms_fields(x, 0.0)[1]
+    J = lambda x, t: _mms_fields(x, t)[2]
+    T = 0.4
+    ue = o.project(lambda x: _mms_fields(x, T)[0], lambda x: _mms_fields(x, T)[1])
+    errs = []
+    for ns in (2, 4):
+        dt = T / ns
+        A, _ = o.assemble(0.0, dt)
+        zero = np.zeros(int(o.trial_off[-1]))
+        u = o.project(E0, H0)
+        for n in range(ns):
+            b = -o.residual(zero, n * dt, dt, src=J)
+            u = o.end_state(o.slab_solve(u, n * dt, dt, A_b=(A, b)))
+        errs.append(np.sqrt(2 * o.energy(u - ue)))
+    order = np.log2(errs[0] / errs[1])
+    assert abs(order - 2 * q) < 0.3, (errs, order)
