@@ -189,8 +189,10 @@ int32_t stm_set_boundary(stm_ctx *ctx, stm_st_field_fn g, void *user);
 /* Current density J of Eq. maxwell sampled on the host: l_E(v) = (J, v) over
  * I_n x K (Eq. bilinearform:C), by (p+2)^3 Gauss points per element and q+2 in
  * time; the callback gets npts space-time points (x, y, z, t) and writes J.
- * Added to the Gaussian sources of stm_set_source_gauss.  Meshes with one
- * (p, q) (bricks or trilinear); NULL removes it.  The library keeps the
+ * Added to the Gaussian sources of stm_set_source_gauss.  Any mesh: on uneven
+ * (p, q) or time-refined meshes each element uses its own degrees and N_K
+ * sub-intervals (Gaussian sources and boundary data are uniform-mesh only
+ * there); NULL removes it.  The library keeps the
  * pointer; the caller keeps the callback alive while the context uses it. */
 int32_t stm_set_source(stm_ctx *ctx, stm_st_field_fn J, void *user);
 

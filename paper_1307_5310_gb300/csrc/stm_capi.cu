@@ -555,30 +555,79 @@ int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* o
 }
 
 // l_E(v) = (J, v) over I_n x K for a current density sampled on the host (Eq.
-// bilinearform:C), added into the E rows of hb.  With the covariant test
-// functions v = DF^{-T} phi_s e_c, J . v |J| = (adj(DF) J)_c phi_s, so per
-// element: values a = adj(DF) J at the (p+2)^3 x (q+2) Gauss points, weighted
-// and contracted with L_i in time, then projected on phi_s by three 1-D
-// contractions.  The trilinear map of the 8 vertices covers bricks and curved
-// elements alike.
-void add_host_current(stm_ctx* c, double t0, double dt, const std::vector<double>& xq,
-                      const std::vector<double>& wq, const std::vector<double>& xt, const std::vector<double>& wt,
-                      const std::vector<double>& Lq, const std::vector<double>& Lt, std::vector<double>& hb) {
-  const int Q = c->Q, N = c->N, N3 = c->N3, nq = (int)xq.size(), nt = (int)xt.size(), nq3 = nq * nq * nq;
-  const int64_t per_el = (int64_t)nt * nq3;
-  const int64_t chunk = std::max<int64_t>(1, (1 << 20) / per_el);
-  std::vector<double> xtp, jv, adj;
-  std::vector<double> F(3 * (size_t)Q * nq3), G1, G2;
-  for (int64_t e0 = 0; e0 < c->ne; e0 += chunk) {
-    const int64_t e1 = std::min<int64_t>(c->ne, e0 + chunk), ncnt = e1 - e0;
-    xtp.resize(4 * ncnt * per_el);
-    jv.resize(3 * ncnt * per_el);
-    adj.resize(9 * ncnt * nq3);
+// bilinearform:C), added into the E rows of hb (test layout, per-element
+// offsets).  With the covariant test functions v = DF^{-T} phi_s e_c,
+// J . v |J| = (adj(DF) J)_c phi_s, so per element: values a = adj(DF) J at the
+// (p+2)^3 Gauss points times q+2 Gauss points on each of the element's N_K
+// time sub-intervals, weighted and contracted with L_i of the sub-interval,
+// then projected on phi_s by three 1-D contractions.  The trilinear map of the
+// 8 vertices covers bricks and curved elements alike; p, q and N_K are the
+// element's own.
+void add_host_current(stm_ctx* c, double t0, double dt, std::vector<double>& hb) {
+  struct Rule {
+    std::vector<double> x, w, L;  // points, weights, L_j(x_g) at [g * n + j]
+  };
+  auto rule = [](int npts, int nfun) {
+    Rule r;
+    gauss01(npts, r.x, r.w);
+    r.L.resize((size_t)npts * nfun);
+    for (int g = 0; g < npts; ++g) legendre01(nfun, r.x[g], &r.L[(size_t)g * nfun]);
+    return r;
+  };
+  std::vector<Rule> space(8), time(kMaxQ + 1);
+  for (int P = 0; P < 8; ++P) space[P] = rule(P + 2, P + 1);
+  for (int q = 1; q <= kMaxQ; ++q) time[q] = rule(q + 2, q);
+  auto pts_of = [&](int64_t e) {
+    const int nq = c->h_p[e] + 2;
+    return (int64_t)(c->h_q[e] + 2) * c->h_nk[e] * nq * nq * nq;
+  };
+  std::vector<double> xtp, jv, adj, F, G1, G2;
+  for (int64_t e0 = 0; e0 < c->ne;) {
+    // a chunk of elements with about 2^20 space-time points
+    int64_t e1 = e0, np = 0;
+    std::vector<int64_t> start;
+    while (e1 < c->ne && (np == 0 || np + pts_of(e1) <= (1 << 20))) {
+      start.push_back(np);
+      np += pts_of(e1++);
+    }
+    xtp.resize(4 * np);
+    jv.resize(3 * np);
     for (int64_t e = e0; e < e1; ++e) {
+      const int P = c->h_p[e], q = c->h_q[e], nk = c->h_nk[e], nq = P + 2, nq3 = nq * nq * nq, nt = q + 2;
+      const Rule& sr = space[P];
+      const Rule& tr = time[q];
       const double* X = &c->h_X8[24 * e];
       for (int g = 0; g < nq3; ++g) {
-        const double xh[3] = {xq[g % nq], xq[(g / nq) % nq], xq[g / (nq * nq)]};
-        double x[3] = {0, 0, 0}, DF[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const double xh[3] = {sr.x[g % nq], sr.x[(g / nq) % nq], sr.x[g / (nq * nq)]};
+        double x[3] = {0, 0, 0};
+        for (int v = 0; v < 8; ++v) {
+          const int bit[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+          double Nv = 1.0;
+          for (int a = 0; a < 3; ++a) Nv *= bit[a] ? xh[a] : 1.0 - xh[a];
+          for (int i = 0; i < 3; ++i) x[i] += Nv * X[3 * v + i];
+        }
+        for (int k = 0; k < nk; ++k)
+          for (int tq = 0; tq < nt; ++tq) {
+            double* pt = &xtp[4 * (start[e - e0] + ((int64_t)k * nt + tq) * nq3 + g)];
+            pt[0] = x[0];
+            pt[1] = x[1];
+            pt[2] = x[2];
+            pt[3] = t0 + dt * (k + tr.x[tq]) / nk;
+          }
+      }
+    }
+    c->jfn(c->juser, np, xtp.data(), jv.data());
+    for (int64_t e = e0; e < e1; ++e) {
+      const int P = c->h_p[e], q = c->h_q[e], nk = c->h_nk[e], N = P + 1, N3 = N * N * N, nq = P + 2,
+                nq3 = nq * nq * nq, nt = q + 2, QE = nk * q;
+      const Rule& sr = space[P];
+      const Rule& tr = time[q];
+      const double* X = &c->h_X8[24 * e];
+      // adj(DF) = |J| DF^{-1} (cofactor transpose) at the spatial points
+      adj.resize(9 * (size_t)nq3);
+      for (int g = 0; g < nq3; ++g) {
+        const double xh[3] = {sr.x[g % nq], sr.x[(g / nq) % nq], sr.x[g / (nq * nq)]};
+        double DF[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         for (int v = 0; v < 8; ++v) {
           const int bit[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
           double fa[3], dfa[3];
@@ -586,15 +635,11 @@ void add_host_current(stm_ctx* c, double t0, double dt, const std::vector<double
             fa[a] = bit[a] ? xh[a] : 1.0 - xh[a];
             dfa[a] = bit[a] ? 1.0 : -1.0;
           }
-          const double Nv = fa[0] * fa[1] * fa[2];
           const double dN[3] = {dfa[0] * fa[1] * fa[2], fa[0] * dfa[1] * fa[2], fa[0] * fa[1] * dfa[2]};
-          for (int i = 0; i < 3; ++i) {
-            x[i] += Nv * X[3 * v + i];
+          for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) DF[i][j] += X[3 * v + i] * dN[j];
-          }
         }
-        // adj(DF) = |J| DF^{-1} (cofactor transpose)
-        double* A = &adj[9 * ((e - e0) * nq3 + g)];
+        double* A = &adj[9 * (size_t)g];
         A[0] = DF[1][1] * DF[2][2] - DF[1][2] * DF[2][1];
         A[1] = DF[0][2] * DF[2][1] - DF[0][1] * DF[2][2];
         A[2] = DF[0][1] * DF[1][2] - DF[0][2] * DF[1][1];
@@ -604,57 +649,52 @@ void add_host_current(stm_ctx* c, double t0, double dt, const std::vector<double
         A[6] = DF[1][0] * DF[2][1] - DF[1][1] * DF[2][0];
         A[7] = DF[0][1] * DF[2][0] - DF[0][0] * DF[2][1];
         A[8] = DF[0][0] * DF[1][1] - DF[0][1] * DF[1][0];
-        for (int tq = 0; tq < nt; ++tq) {
-          double* p = &xtp[4 * ((e - e0) * per_el + (int64_t)tq * nq3 + g)];
-          p[0] = x[0];
-          p[1] = x[1];
-          p[2] = x[2];
-          p[3] = t0 + dt * xt[tq];
-        }
       }
-    }
-    c->jfn(c->juser, ncnt * per_el, xtp.data(), jv.data());
-    for (int64_t e = e0; e < e1; ++e) {
-      std::fill(F.begin(), F.end(), 0.0);
-      for (int tq = 0; tq < nt; ++tq)
-        for (int g = 0; g < nq3; ++g) {
-          const double* J = &jv[3 * ((e - e0) * per_el + (int64_t)tq * nq3 + g)];
-          const double* A = &adj[9 * ((e - e0) * nq3 + g)];
-          const double w = dt * wt[tq] * wq[g % nq] * wq[(g / nq) % nq] * wq[g / (nq * nq)];
-          for (int cc = 0; cc < 3; ++cc) {
-            const double a = w * (A[3 * cc] * J[0] + A[3 * cc + 1] * J[1] + A[3 * cc + 2] * J[2]);
-            for (int i = 0; i < Q; ++i) F[((size_t)cc * Q + i) * nq3 + g] += Lt[tq * kMaxQ + i] * a;
+      // F[c][k q + i][g] = sum_tau w_tau (dt/N_K) L_i(tau) w_g (adj(DF) J)_c
+      F.assign(3 * (size_t)QE * nq3, 0.0);
+      for (int k = 0; k < nk; ++k)
+        for (int tq = 0; tq < nt; ++tq)
+          for (int g = 0; g < nq3; ++g) {
+            const double* J = &jv[3 * (start[e - e0] + ((int64_t)k * nt + tq) * nq3 + g)];
+            const double* A = &adj[9 * (size_t)g];
+            const double w = dt / nk * tr.w[tq] * sr.w[g % nq] * sr.w[(g / nq) % nq] * sr.w[g / (nq * nq)];
+            for (int cc = 0; cc < 3; ++cc) {
+              const double a = w * (A[3 * cc] * J[0] + A[3 * cc + 1] * J[1] + A[3 * cc + 2] * J[2]);
+              for (int i = 0; i < q; ++i)
+                F[((size_t)cc * QE + k * q + i) * nq3 + g] += tr.L[(size_t)tq * q + i] * a;
+            }
           }
-        }
       // project on phi_s = L_j(x^) L_k(y^) L_l(z^): contract x, then y, then z
-      for (int ci = 0; ci < 3 * Q; ++ci) {
+      for (int ci = 0; ci < 3 * QE; ++ci) {
         const double* f0 = &F[(size_t)ci * nq3];
         G1.assign((size_t)nq * nq * N, 0.0);
         for (int gz = 0; gz < nq; ++gz)
           for (int gy = 0; gy < nq; ++gy)
             for (int j = 0; j < N; ++j) {
               double acc = 0.0;
-              for (int gx = 0; gx < nq; ++gx) acc += f0[(gz * nq + gy) * nq + gx] * Lq[gx * N + j];
+              for (int gx = 0; gx < nq; ++gx) acc += f0[(gz * nq + gy) * nq + gx] * sr.L[(size_t)gx * N + j];
               G1[(gz * nq + gy) * N + j] = acc;
             }
         G2.assign((size_t)nq * N * N, 0.0);
         for (int gz = 0; gz < nq; ++gz)
-          for (int k = 0; k < N; ++k)
+          for (int kk = 0; kk < N; ++kk)
             for (int j = 0; j < N; ++j) {
               double acc = 0.0;
-              for (int gy = 0; gy < nq; ++gy) acc += G1[(gz * nq + gy) * N + j] * Lq[gy * N + k];
-              G2[(gz * N + k) * N + j] = acc;
+              for (int gy = 0; gy < nq; ++gy) acc += G1[(gz * nq + gy) * N + j] * sr.L[(size_t)gy * N + kk];
+              G2[(gz * N + kk) * N + j] = acc;
             }
-        double* row = &hb[(size_t)e * 6 * Q * N3 + (size_t)ci * N3];  // E rows: field 0, (comp, mode) = ci
+        // E rows of the element: field 0, (component, temporal index) = ci
+        double* row = &hb[(size_t)c->h_off_test[e] + (size_t)ci * N3];
         for (int l = 0; l < N; ++l)
-          for (int k = 0; k < N; ++k)
+          for (int kk = 0; kk < N; ++kk)
             for (int j = 0; j < N; ++j) {
               double acc = 0.0;
-              for (int gz = 0; gz < nq; ++gz) acc += G2[(gz * N + k) * N + j] * Lq[gz * N + l];
-              row[(l * N + k) * N + j] += acc;
+              for (int gz = 0; gz < nq; ++gz) acc += G2[(gz * N + kk) * N + j] * sr.L[(size_t)gz * N + l];
+              row[(l * N + kk) * N + j] += acc;
             }
       }
     }
+    e0 = e1;
   }
 }
 
@@ -664,7 +704,8 @@ void add_host_current(stm_ctx* c, double t0, double dt, const std::vector<double
 int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   *out = nullptr;
   if (c->srcs.empty() && !c->gfn && !c->jfn) return STM_OK;
-  if (c->hp) return fail(c, STM_EUNSUPPORTED, "sources and boundary data are handled on uniform (p, q) meshes only");
+  if (c->hp && (!c->srcs.empty() || c->gfn))
+    return fail(c, STM_EUNSUPPORTED, "Gaussian sources and boundary data are handled on uniform (p, q) meshes only");
   if (c->load_valid && c->load_t0 == t0 && c->load_dt == dt) {
     *out = c->load64;
     return STM_OK;
@@ -677,6 +718,20 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
       return fail(c, STM_ENOMEM, "load vector allocation failed");
     }
   }
+  if (c->hp) {  // uneven degrees or N_K: the host current only
+    std::vector<double> hb(n, 0.0);
+    add_host_current(c, t0, dt, hb);
+    STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    convert<float, double>(c->load32, c->load64, n, c->stream);
+    c->launches += 1;
+    STM_CK(cudaGetLastError());
+    STM_CK(cudaStreamSynchronize(c->stream));
+    c->load_valid = true;
+    c->load_t0 = t0;
+    c->load_dt = dt;
+    *out = c->load64;
+    return STM_OK;
+  }
   const int P = c->P, Q = c->Q, N = c->N, N3 = c->N3, nq = P + 2, nt = Q + 2;
   std::vector<double> xq, wq, xt, wt;
   gauss01(nq, xq, wq);
@@ -686,7 +741,7 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   for (int g = 0; g < nt; ++g) legendre01(Q, xt[g], &Lt[g * kMaxQ]);
   if (c->gfn || c->jfn) {
     std::vector<double> hb(n, 0.0);
-    if (c->jfn) add_host_current(c, t0, dt, xq, wq, xt, wt, Lq, Lt, hb);
+    if (c->jfn) add_host_current(c, t0, dt, hb);
     if (c->gfn) {
     // l_H(w) = -<n x g, w> on boundary faces; in the reference face (Nanson, covariant
     // transform) <n x g, w> = dt int int (n^ x g^) . w^ with g^ = DF^T g.

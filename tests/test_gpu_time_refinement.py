@@ -114,3 +114,51 @@ def test_unsupported(stm):
     m["nk"] = np.full(8, 3, dtype=np.uint8)
     with pytest.raises(stm.StmError):
         stm.Slab(m)
+
+
+def _mms(x, t):
+    """Manufactured solution of Sec. 6.1.2 (unit cube, eps = mu = 1, PEC): E, H and J."""
+    X, Z = x[..., 0], x[..., 2]
+    zero = np.zeros(np.broadcast(X, t).shape)
+    et = np.exp(t)
+    E = np.stack([zero, et * X * (X - 1) * Z * (1 - Z) + zero, zero], -1)
+    H = np.stack([et * X * (X - 1) * (1 - 2 * Z) + zero, zero, -et * (2 * X - 1) * Z * (1 - Z) + zero], -1)
+    J = np.stack([zero, et * (X * (X - 1) * Z * (1 - Z) + 2 * X * (X - 1) - 2 * Z * (1 - Z)) + zero, zero], -1)
+    return E, H, J
+
+
+def test_host_current_time_refined(stm):
+    """stm_set_source on a mesh with mixed N_K and q: the load uses each element's
+    sub-intervals; residual vs the oracle's (J, v)."""
+    m = _mesh("nk_q_mixed")
+    J = lambda x, t: _mms(x, t)[2] + np.stack(np.broadcast_arrays(0 * x[..., 0], np.sin(x[..., 0] + 3 * t), 0 * t), -1)
+    U = meshgen.random_coeffs(m, 27)
+    s = stm.Slab(m)
+    s.set_source(J)
+    R = np.empty(s.n_test)
+    s.residual_apply(U, R, 0.1, 0.07)
+    assert rel(R, stdg.Oracle(m).residual(U, 0.1, 0.07, src=J)) < 1e-12
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_mms_nodal_order_time_refined(stm, q):
+    """Sec. 6.1.2 on the CUDA path: Q_2 in space is exact for the fields, N_K in {1, 2}
+    mixed; the slab-end error converges with order 2q."""
+    m = meshgen.box_mesh(2, p=2, q=q)
+    m["nk"] = np.array([1, 2, 1, 2, 2, 1, 2, 1], dtype=np.uint8)
+    o = stdg.Oracle(m)
+    T = 0.4
+    ue = o.project(lambda x: _mms(x, T)[0], lambda x: _mms(x, T)[1])
+    errs = []
+    for ns in (2, 4):
+        s = stm.Slab(m, tol=1e-13, max_it=3000)
+        s.set_source(lambda x, t: _mms(x, t)[2])
+        s.set_initial(lambda x: _mms(x, 0.0)[0], lambda x: _mms(x, 0.0)[1])
+        for _ in range(ns):
+            rc, rep = s.slab_solve(T / ns)
+            assert rc == stm.STM_OK, rep
+        u, t = s.get_state()
+        assert abs(t - T) < 1e-12
+        errs.append(np.sqrt(2 * o.energy(u - ue)))
+    order = np.log2(errs[0] / errs[1])
+    assert abs(order - 2 * q) < 0.3, (errs, order)
