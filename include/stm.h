@@ -169,8 +169,9 @@ int32_t stm_set_initial(stm_ctx *ctx, double t, stm_field_fn E0, stm_field_fn H0
 /* Current density J of Eq. maxwell as a sum of Gaussian pulses (at most 8):
  *   J(x, t) = sum_k amp_k dir_k exp(-|x - centre_k|^2 / (2 sigma_x^2)) exp(-(t - t0_k)^2 / (2 sigma_t^2)).
  * It enters the load l_E(v) = (J, v) of Eq. bilinearform:C, integrated on the
- * device with p+2 Gauss points per direction and q+2 in time.  n_src = 0
- * removes all sources.  The array is copied. */
+ * device with p+2 Gauss points per direction and q+2 in time (on meshes with
+ * uneven degrees or N_K > 1: on the host, per element and sub-interval).
+ * n_src = 0 removes all sources.  The array is copied. */
 typedef struct {
   double centre[3], dir[3];
   double sigma_x, t0, sigma_t, amp;
@@ -180,8 +181,10 @@ int32_t stm_set_source_gauss(stm_ctx *ctx, const stm_gauss_src *src, int32_t n_s
 /* Boundary data g of Eq. maxwell (n x E = n x g): l_H(w) = -<n x g, w> on the
  * boundary faces (Eq. bilinearform:C).  The callback gets npts space-time
  * points x[k] = (x, y, z, t) and writes g there; it is called on the host once
- * per slab (p+2 Gauss points per face direction, q+2 in time).  NULL = PEC
- * (g = 0). */
+ * per slab (p+2 Gauss points per face direction, q+2 in time on each of the
+ * element's N_K sub-intervals, with each element's own p and q).  With the
+ * dissipative term (opts.c_diss > 0) g also enters the E rows through
+ * <alpha_E n x (E - g), n x v>.  NULL = PEC (g = 0). */
 typedef void (*stm_st_field_fn)(void *user, int64_t npts, const double *xt /*[npts][4]*/,
                                 double *out /*[npts][3]*/);
 int32_t stm_set_boundary(stm_ctx *ctx, stm_st_field_fn g, void *user);
@@ -191,8 +194,8 @@ int32_t stm_set_boundary(stm_ctx *ctx, stm_st_field_fn g, void *user);
  * time; the callback gets npts space-time points (x, y, z, t) and writes J.
  * Added to the Gaussian sources of stm_set_source_gauss.  Any mesh: on uneven
  * (p, q) or time-refined meshes each element uses its own degrees and N_K
- * sub-intervals (Gaussian sources and boundary data are uniform-mesh only
- * there); NULL removes it.  The library keeps the
+ * sub-intervals (there the Gaussian sources and the boundary data are
+ * assembled on the host the same way); NULL removes it.  The library keeps the
  * pointer; the caller keeps the callback alive while the context uses it. */
 int32_t stm_set_source(stm_ctx *ctx, stm_st_field_fn J, void *user);
 

@@ -563,7 +563,7 @@ int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* o
 // then projected on phi_s by three 1-D contractions.  The trilinear map of the
 // 8 vertices covers bricks and curved elements alike; p, q and N_K are the
 // element's own.
-void add_host_current(stm_ctx* c, double t0, double dt, std::vector<double>& hb) {
+void add_host_current(stm_ctx* c, double t0, double dt, stm_st_field_fn fn, void* user, std::vector<double>& hb) {
   struct Rule {
     std::vector<double> x, w, L;  // points, weights, L_j(x_g) at [g * n + j]
   };
@@ -616,7 +616,7 @@ void add_host_current(stm_ctx* c, double t0, double dt, std::vector<double>& hb)
           }
       }
     }
-    c->jfn(c->juser, np, xtp.data(), jv.data());
+    fn(user, np, xtp.data(), jv.data());
     for (int64_t e = e0; e < e1; ++e) {
       const int P = c->h_p[e], q = c->h_q[e], nk = c->h_nk[e], N = P + 1, N3 = N * N * N, nq = P + 2,
                 nq3 = nq * nq * nq, nt = q + 2, QE = nk * q;
@@ -698,14 +698,168 @@ void add_host_current(stm_ctx* c, double t0, double dt, std::vector<double>& hb)
   }
 }
 
+// l_H(w) = -<n x g, w> over I_n x F_b (Eq. bilinearform:C) for boundary data g
+// sampled on the host, added into the H rows of hb; with D_h (Sec. 4.2) also the
+// g part of <alpha_E n x (E - g), n x v> into the E rows.  In the reference face
+// (Nanson, covariant transform) <n x g, w> = int int (n^ x g^) . w^ with
+// g^ = DF^T g.  Per boundary face: (p+2)^2 Gauss points and q+2 in time on each
+// of the element's N_K sub-intervals, with the element's own p, q and N_K.
+void add_host_boundary(stm_ctx* c, double t0, double dt, std::vector<double>& hb) {
+  struct Rule {
+    std::vector<double> x, w, L;
+  };
+  auto rule = [](int npts, int nfun) {
+    Rule r;
+    gauss01(npts, r.x, r.w);
+    r.L.resize((size_t)npts * nfun);
+    for (int g = 0; g < npts; ++g) legendre01(nfun, r.x[g], &r.L[(size_t)g * nfun]);
+    return r;
+  };
+  std::vector<Rule> space(8), time(kMaxQ + 1);
+  for (int P = 0; P < 8; ++P) space[P] = rule(P + 2, P + 1);
+  for (int q = 1; q <= kMaxQ; ++q) time[q] = rule(q + 2, q);
+  std::vector<int64_t> faces;
+  for (int64_t e = 0; e < c->ne; ++e)
+    for (int f = 0; f < 6; ++f)
+      if (c->h_nbr[6 * e + f] == -1) faces.push_back(6 * e + f);
+  auto pts_of = [&](int64_t e) {
+    const int nq = c->h_p[e] + 2;
+    return (int64_t)(c->h_q[e] + 2) * c->h_nk[e] * nq * nq;
+  };
+  std::vector<double> xtp, gv, DFs;
+  for (size_t f0 = 0; f0 < faces.size();) {
+    size_t f1 = f0;
+    int64_t np = 0;
+    std::vector<int64_t> start;
+    while (f1 < faces.size() && (np == 0 || np + pts_of(faces[f1] / 6) <= (1 << 20))) {
+      start.push_back(np);
+      np += pts_of(faces[f1++] / 6);
+    }
+    xtp.resize(4 * np);
+    gv.resize(3 * np);
+    DFs.resize(9 * np);
+    for (size_t fi = f0; fi < f1; ++fi) {
+      const int64_t e = faces[fi] / 6;
+      const int f = (int)(faces[fi] % 6), d = f / 2, sd = f % 2;
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      const int nq = c->h_p[e] + 2, nt = c->h_q[e] + 2, nk = c->h_nk[e];
+      const Rule& sr = space[c->h_p[e]];
+      const Rule& tr = time[c->h_q[e]];
+      const double* X = &c->h_X8[24 * e];
+      for (int u = 0; u < nq; ++u)
+        for (int v = 0; v < nq; ++v) {
+          double xh[3];
+          xh[d] = sd;
+          xh[a1] = sr.x[u];
+          xh[a2] = sr.x[v];
+          double x[3] = {0, 0, 0}, DF[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          for (int vv = 0; vv < 8; ++vv) {
+            const int bit[3] = {vv & 1, (vv >> 1) & 1, (vv >> 2) & 1};
+            double fa[3], dfa[3];
+            for (int a = 0; a < 3; ++a) {
+              fa[a] = bit[a] ? xh[a] : 1.0 - xh[a];
+              dfa[a] = bit[a] ? 1.0 : -1.0;
+            }
+            const double Nv = fa[0] * fa[1] * fa[2];
+            const double dN[3] = {dfa[0] * fa[1] * fa[2], fa[0] * dfa[1] * fa[2], fa[0] * fa[1] * dfa[2]};
+            for (int i = 0; i < 3; ++i) {
+              x[i] += Nv * X[3 * vv + i];
+              for (int j = 0; j < 3; ++j) DF[3 * i + j] += X[3 * vv + i] * dN[j];
+            }
+          }
+          for (int k = 0; k < nk; ++k)
+            for (int tq = 0; tq < nt; ++tq) {
+              const int64_t idx = start[fi - f0] + (((int64_t)k * nt + tq) * nq + u) * nq + v;
+              xtp[4 * idx] = x[0];
+              xtp[4 * idx + 1] = x[1];
+              xtp[4 * idx + 2] = x[2];
+              xtp[4 * idx + 3] = t0 + dt * (k + tr.x[tq]) / nk;
+              std::copy(DF, DF + 9, &DFs[9 * idx]);
+            }
+        }
+    }
+    c->gfn(c->guser, np, xtp.data(), gv.data());
+    for (size_t fi = f0; fi < f1; ++fi) {
+      const int64_t e = faces[fi] / 6;
+      const int f = (int)(faces[fi] % 6), d = f / 2, sd = f % 2;
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      const int P = c->h_p[e], q = c->h_q[e], nk = c->h_nk[e], N = P + 1, N3 = N * N * N, nq = P + 2, nt = q + 2;
+      const int QE = nk * q;
+      const Rule& sr = space[P];
+      const Rule& tr = time[q];
+      double Lside[kMaxN];
+      legendre01(N, sd ? 1.0 : 0.0, Lside);
+      const double sgn = sd ? 1.0 : -1.0;  // n^ = sgn e_d
+      const double nv[3] = {d == 0 ? sgn : 0.0, d == 1 ? sgn : 0.0, d == 2 ? sgn : 0.0};
+      const int64_t off = c->h_off_test[e];
+      // adds wi * phi_s at the face point (u, v) to the rows (field fld, component cc, index ti)
+      auto lift = [&](int fld, int cc, int ti, double wi, int u, int v) {
+        double* row = &hb[off + ((int64_t)(fld * 3 + cc) * QE + ti) * N3];
+        for (int al = 0; al < N; ++al)
+          for (int j1 = 0; j1 < N; ++j1)
+            for (int j2 = 0; j2 < N; ++j2) {
+              int ix[3];
+              ix[d] = al;
+              ix[a1] = j1;
+              ix[a2] = j2;
+              row[(ix[2] * N + ix[1]) * N + ix[0]] += wi * Lside[al] * sr.L[(size_t)u * N + j1] * sr.L[(size_t)v * N + j2];
+            }
+      };
+      for (int k = 0; k < nk; ++k)
+        for (int tq = 0; tq < nt; ++tq)
+          for (int u = 0; u < nq; ++u)
+            for (int v = 0; v < nq; ++v) {
+              const int64_t idx = start[fi - f0] + (((int64_t)k * nt + tq) * nq + u) * nq + v;
+              const double* DF = &DFs[9 * idx];
+              const double* g = &gv[3 * idx];
+              double gh[3];
+              for (int cc = 0; cc < 3; ++cc) gh[cc] = DF[0 * 3 + cc] * g[0] + DF[1 * 3 + cc] * g[1] + DF[2 * 3 + cc] * g[2];
+              const double ng[3] = {nv[1] * gh[2] - nv[2] * gh[1], nv[2] * gh[0] - nv[0] * gh[2],
+                                    nv[0] * gh[1] - nv[1] * gh[0]};  // n^ x g^
+              const double w = dt / nk * tr.w[tq] * sr.w[u] * sr.w[v];
+              if (c->opts.c_diss > 0) {
+                for (int bc = 0; bc < 2; ++bc) {
+                  const int cc = (d == 0) ? bc + 1 : (d == 1 ? 2 * bc : bc);
+                  const double kg = c->h_kap[e * 24 + f * 2 + bc] * gh[cc];
+                  for (int i = 0; i < q; ++i) lift(0, cc, k * q + i, w * tr.L[(size_t)tq * q + i] * kg, u, v);
+                }
+              }
+              for (int cc = 0; cc < 3; ++cc) {
+                if (ng[cc] == 0.0) continue;
+                for (int i = 0; i < q; ++i) lift(1, cc, k * q + i, -w * tr.L[(size_t)tq * q + i] * ng[cc], u, v);
+              }
+            }
+    }
+    f0 = f1;
+  }
+}
+
+// Gaussian current pulses evaluated on the host (the load path of meshes with
+// uneven degrees or time refinement), as a space-time callback over the
+// context's sources.
+void gauss_sources_host(void* user, int64_t npts, const double* xt, double* out) {
+  const stm_ctx* c = static_cast<const stm_ctx*>(user);
+  for (int64_t k = 0; k < npts; ++k) {
+    double J[3] = {0, 0, 0};
+    for (const stm_gauss_src& sr : c->srcs) {
+      double r2 = 0.0;
+      for (int i = 0; i < 3; ++i) r2 += (xt[4 * k + i] - sr.centre[i]) * (xt[4 * k + i] - sr.centre[i]);
+      const double tt = xt[4 * k + 3] - sr.t0;
+      const double a = sr.amp * std::exp(-r2 / (2.0 * sr.sigma_x * sr.sigma_x)) *
+                       std::exp(-tt * tt / (2.0 * sr.sigma_t * sr.sigma_t));
+      for (int i = 0; i < 3; ++i) J[i] += a * sr.dir[i];
+    }
+    for (int i = 0; i < 3; ++i) out[3 * k + i] = J[i];
+  }
+}
+
 // Load vector b = L on the slab (t0, t0 + dt] (Eq. bilinearform:C): Gaussian
 // currents on the device, boundary data g on the host.  Returns null when no
 // source and no boundary data are set (L = 0).  Cached per (t0, dt).
 int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   *out = nullptr;
   if (c->srcs.empty() && !c->gfn && !c->jfn) return STM_OK;
-  if (c->hp && (!c->srcs.empty() || c->gfn))
-    return fail(c, STM_EUNSUPPORTED, "Gaussian sources and boundary data are handled on uniform (p, q) meshes only");
+
   if (c->load_valid && c->load_t0 == t0 && c->load_dt == dt) {
     *out = c->load64;
     return STM_OK;
@@ -718,9 +872,11 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
       return fail(c, STM_ENOMEM, "load vector allocation failed");
     }
   }
-  if (c->hp) {  // uneven degrees or N_K: the host current only
+  if (c->hp) {  // uneven degrees or N_K: every term assembled on the host, element by element
     std::vector<double> hb(n, 0.0);
-    add_host_current(c, t0, dt, hb);
+    if (c->jfn) add_host_current(c, t0, dt, c->jfn, c->juser, hb);
+    if (!c->srcs.empty()) add_host_current(c, t0, dt, gauss_sources_host, c, hb);
+    if (c->gfn) add_host_boundary(c, t0, dt, hb);
     STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     convert<float, double>(c->load32, c->load64, n, c->stream);
     c->launches += 1;
@@ -741,125 +897,8 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   for (int g = 0; g < nt; ++g) legendre01(Q, xt[g], &Lt[g * kMaxQ]);
   if (c->gfn || c->jfn) {
     std::vector<double> hb(n, 0.0);
-    if (c->jfn) add_host_current(c, t0, dt, hb);
-    if (c->gfn) {
-    // l_H(w) = -<n x g, w> on boundary faces; in the reference face (Nanson, covariant
-    // transform) <n x g, w> = dt int int (n^ x g^) . w^ with g^ = DF^T g.
-    std::vector<int64_t> faces;
-    for (int64_t e = 0; e < c->ne; ++e)
-      for (int f = 0; f < 6; ++f)
-        if (c->h_nbr[6 * e + f] < 0) faces.push_back(6 * e + f);
-    const int64_t per_face = (int64_t)nt * nq * nq;
-    const int64_t chunk = std::max<int64_t>(1, (1 << 20) / per_face);
-    std::vector<double> xtp, gv, DFs;
-    std::vector<double> L0(N), L1(N);
-    legendre01(N, 0.0, L0.data());
-    legendre01(N, 1.0, L1.data());
-    for (size_t f0 = 0; f0 < faces.size(); f0 += chunk) {
-      const size_t f1 = std::min(faces.size(), f0 + chunk);
-      const int64_t np = (int64_t)(f1 - f0) * per_face;
-      xtp.resize(4 * np);
-      gv.resize(3 * np);
-      DFs.resize(9 * (f1 - f0) * nq * nq);
-      for (size_t fi = f0; fi < f1; ++fi) {
-        const int64_t e = faces[fi] / 6;
-        const int f = (int)(faces[fi] % 6), d = f / 2, sd = f % 2;
-        const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
-        const double* X = &c->h_X8[24 * e];
-        for (int u = 0; u < nq; ++u)
-          for (int v = 0; v < nq; ++v) {
-            double xh[3];
-            xh[d] = sd;
-            xh[a1] = xq[u];
-            xh[a2] = xq[v];
-            double x[3] = {0, 0, 0};
-            double* DF = &DFs[(((fi - f0) * nq + u) * nq + v) * 9];
-            for (int k = 0; k < 9; ++k) DF[k] = 0.0;
-            for (int vv = 0; vv < 8; ++vv) {
-              const int bit[3] = {vv & 1, (vv >> 1) & 1, (vv >> 2) & 1};
-              double fa[3], dfa[3];
-              for (int a = 0; a < 3; ++a) {
-                fa[a] = bit[a] ? xh[a] : 1.0 - xh[a];
-                dfa[a] = bit[a] ? 1.0 : -1.0;
-              }
-              const double Nv = fa[0] * fa[1] * fa[2];
-              const double dN[3] = {dfa[0] * fa[1] * fa[2], fa[0] * dfa[1] * fa[2], fa[0] * fa[1] * dfa[2]};
-              for (int i = 0; i < 3; ++i) {
-                x[i] += Nv * X[3 * vv + i];
-                for (int j = 0; j < 3; ++j) DF[3 * i + j] += X[3 * vv + i] * dN[j];
-              }
-            }
-            for (int tq = 0; tq < nt; ++tq) {
-              const int64_t k = (((int64_t)(fi - f0) * nt + tq) * nq + u) * nq + v;
-              xtp[4 * k] = x[0];
-              xtp[4 * k + 1] = x[1];
-              xtp[4 * k + 2] = x[2];
-              xtp[4 * k + 3] = t0 + dt * xt[tq];
-            }
-          }
-      }
-      c->gfn(c->guser, np, xtp.data(), gv.data());
-      for (size_t fi = f0; fi < f1; ++fi) {
-        const int64_t e = faces[fi] / 6;
-        const int f = (int)(faces[fi] % 6), d = f / 2, sd = f % 2;
-        const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
-        const double sgn = sd ? 1.0 : -1.0;  // n^ = sgn e_d
-        const double* Lside = sd ? L1.data() : L0.data();
-        for (int tq = 0; tq < nt; ++tq)
-          for (int u = 0; u < nq; ++u)
-            for (int v = 0; v < nq; ++v) {
-              const int64_t k = (((int64_t)(fi - f0) * nt + tq) * nq + u) * nq + v;
-              const double* DF = &DFs[(((fi - f0) * nq + u) * nq + v) * 9];
-              const double* g = &gv[3 * k];
-              double gh[3];
-              for (int cc = 0; cc < 3; ++cc) gh[cc] = DF[0 * 3 + cc] * g[0] + DF[1 * 3 + cc] * g[1] + DF[2 * 3 + cc] * g[2];
-              double ng[3];  // n^ x g^
-              const double nv[3] = {d == 0 ? sgn : 0.0, d == 1 ? sgn : 0.0, d == 2 ? sgn : 0.0};
-              ng[0] = nv[1] * gh[2] - nv[2] * gh[1];
-              ng[1] = nv[2] * gh[0] - nv[0] * gh[2];
-              ng[2] = nv[0] * gh[1] - nv[1] * gh[0];
-              const double w = dt * wt[tq] * wq[u] * wq[v];
-              if (c->opts.c_diss > 0) {
-                // D_h on F_b: the g part of <alpha_E n x (E - g), n x v> moves into the load
-                for (int bc = 0; bc < 2; ++bc) {
-                  const int cc = (d == 0) ? bc + 1 : (d == 1 ? 2 * bc : bc);
-                  const double kg = c->h_kap[e * 24 + f * 2 + bc] * gh[cc];
-                  for (int i = 0; i < Q; ++i) {
-                    const double wi = w * Lt[tq * kMaxQ + i] * kg;
-                    double* row = &hb[((e * 2 + 0) * 3 + cc) * (int64_t)Q * N3 + (int64_t)i * N3];
-                    for (int al = 0; al < N; ++al)
-                      for (int j1 = 0; j1 < N; ++j1)
-                        for (int j2 = 0; j2 < N; ++j2) {
-                          int idx[3];
-                          idx[d] = al;
-                          idx[a1] = j1;
-                          idx[a2] = j2;
-                          row[(idx[2] * N + idx[1]) * N + idx[0]] += wi * Lside[al] * Lq[u * N + j1] * Lq[v * N + j2];
-                        }
-                  }
-                }
-              }
-              for (int cc = 0; cc < 3; ++cc) {
-                if (ng[cc] == 0.0) continue;
-                for (int i = 0; i < Q; ++i) {
-                  const double wi = -w * Lt[tq * kMaxQ + i] * ng[cc];
-                  double* row = &hb[((e * 2 + 1) * 3 + cc) * (int64_t)Q * N3 + (int64_t)i * N3];
-                  for (int al = 0; al < N; ++al)
-                    for (int j1 = 0; j1 < N; ++j1)
-                      for (int j2 = 0; j2 < N; ++j2) {
-                        int idx[3];
-                        idx[d] = al;
-                        idx[a1] = j1;
-                        idx[a2] = j2;
-                        row[(idx[2] * N + idx[1]) * N + idx[0]] +=
-                            wi * Lside[al] * Lq[u * N + j1] * Lq[v * N + j2];
-                      }
-                }
-              }
-            }
-      }
-    }
-    }
+    if (c->jfn) add_host_current(c, t0, dt, c->jfn, c->juser, hb);
+    if (c->gfn) add_host_boundary(c, t0, dt, hb);
     STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
   } else {

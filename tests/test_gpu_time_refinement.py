@@ -162,3 +162,30 @@ def test_mms_nodal_order_time_refined(stm, q):
         errs.append(np.sqrt(2 * o.energy(u - ue)))
     order = np.log2(errs[0] / errs[1])
     assert abs(order - 2 * q) < 0.3, (errs, order)
+
+
+@pytest.mark.parametrize("case", ["nk_q_mixed", "nk_p_mixed"])
+def test_sources_and_boundary_data_uneven(stm, case):
+    """Gaussian pulses and boundary data g on meshes with uneven degrees and N_K: the
+    load is assembled on the host element by element; residual vs the oracle's."""
+    m = _mesh(case)
+    srcs = [dict(centre=(0.5, 0.45, 0.55), dir=(0.0, 0.0, 1.0), sigma_x=0.15, t0=0.1, sigma_t=0.05, amp=1.0),
+            dict(centre=(0.3, 0.6, 0.4), dir=(0.6, 0.0, 0.8), sigma_x=0.1, t0=0.12, sigma_t=0.08, amp=2.5)]
+
+    def J(x, t):
+        out = 0.0
+        for sd in srcs:
+            r2 = np.sum((x - np.asarray(sd["centre"])) ** 2, axis=-1)
+            a = sd["amp"] * np.exp(-r2 / (2 * sd["sigma_x"] ** 2)) * np.exp(-(t - sd["t0"]) ** 2 / (2 * sd["sigma_t"] ** 2))
+            out = out + a[..., None] * np.asarray(sd["dir"])
+        return out
+
+    g = lambda x, t: np.stack(np.broadcast_arrays(np.sin(x[..., 1]) * (1 + t), x[..., 2] * x[..., 0] + 0 * t,
+                                                  np.cos(x[..., 0] + t)), -1)
+    U = meshgen.random_coeffs(m, 29)
+    s = stm.Slab(m)
+    s.set_source_gauss(srcs)
+    s.set_boundary(g)
+    R = np.empty(s.n_test)
+    s.residual_apply(U, R, 0.05, 0.06)
+    assert rel(R, stdg.Oracle(m).residual(U, 0.05, 0.06, src=J, g=g)) < 1e-12
