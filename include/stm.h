@@ -160,8 +160,10 @@ int32_t stm_get_state(stm_ctx *ctx, double *t, void *u, int32_t mem);
 /* L2 projection of E0(x), H0(x) onto the covariant spatial spaces (initial
  * data of Eq. maxwell), evaluated by the callback at p+2 Gauss points per
  * direction; becomes the state at time t.  Either callback may be NULL (0).
- * Built for STM_GEOM_BRICK; curved meshes return STM_EUNSUPPORTED (set the
- * state directly). */
+ * Bricks: the diagonal mass is inverted directly.  Trilinear meshes: the
+ * element systems with the metric mass (the same (p+2)^3 rule as the
+ * residual) are solved by conjugate gradients on the device to 1e-14
+ * relative residual; STM_EDEVICE / STM_ENOMEM on failure. */
 typedef void (*stm_field_fn)(void *user, int64_t npts, const double *x /*[npts][3]*/,
                              double *out /*[npts][3]*/);
 int32_t stm_set_initial(stm_ctx *ctx, double t, stm_field_fn E0, stm_field_fn H0, void *user);

@@ -1695,12 +1695,178 @@ int32_t stm_get_state(stm_ctx* c, double* t, void* u, int32_t mem) {
   return STM_OK;
 }
 
+}  // extern "C"
+
+// Covariant L2 projection on trilinear elements: mat_f M_G u = mat_f (F, v) per
+// element, with the metric mass M_G of the residual (G = |J| DF^{-1} DF^{-T} at the
+// (p+2)^3 Gauss points) and the right side (F, v) = sum_g w_g (adj(DF) F)_c phi_s by
+// the same rule.  The element systems are solved together by conjugate gradients
+// on the device (the metric-mass kernel as operator, the cell-mean blocks as
+// preconditioner); the result is the state.
+int project_curved(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, void* user) {
+  const int P = c->P, N = c->N, N3 = c->N3, nq = P + 2, nq3 = nq * nq * nq;
+  const int64_t n = c->n_state;
+  std::vector<double> xq, wq, Lq(nq * N);
+  gauss01(nq, xq, wq);
+  for (int g = 0; g < nq; ++g) legendre01(N, xq[g], &Lq[g * N]);
+  std::vector<double> rhs(n, 0.0), pts, val, adj, F(3 * (size_t)nq3), G1, G2;
+  const int64_t chunk = std::max<int64_t>(1, (1 << 20) / nq3);
+  for (int64_t e0 = 0; e0 < c->ne; e0 += chunk) {
+    const int64_t e1 = std::min<int64_t>(c->ne, e0 + chunk), cnt = e1 - e0;
+    pts.resize(3 * cnt * nq3);
+    val.resize(3 * cnt * nq3);
+    adj.resize(9 * cnt * nq3);
+    for (int64_t e = e0; e < e1; ++e) {
+      const double* X = &c->h_X8[24 * e];
+      for (int g = 0; g < nq3; ++g) {
+        const double xh[3] = {xq[g % nq], xq[(g / nq) % nq], xq[g / (nq * nq)]};
+        double x[3] = {0, 0, 0}, DF[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int v = 0; v < 8; ++v) {
+          const int bit[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+          double fa[3], dfa[3];
+          for (int a = 0; a < 3; ++a) {
+            fa[a] = bit[a] ? xh[a] : 1.0 - xh[a];
+            dfa[a] = bit[a] ? 1.0 : -1.0;
+          }
+          const double Nv = fa[0] * fa[1] * fa[2];
+          const double dN[3] = {dfa[0] * fa[1] * fa[2], fa[0] * dfa[1] * fa[2], fa[0] * fa[1] * dfa[2]};
+          for (int i = 0; i < 3; ++i) {
+            x[i] += Nv * X[3 * v + i];
+            for (int j = 0; j < 3; ++j) DF[i][j] += X[3 * v + i] * dN[j];
+          }
+        }
+        const int64_t k = (e - e0) * nq3 + g;
+        for (int i = 0; i < 3; ++i) pts[3 * k + i] = x[i];
+        double* A = &adj[9 * k];  // adj(DF) = |J| DF^{-1}
+        A[0] = DF[1][1] * DF[2][2] - DF[1][2] * DF[2][1];
+        A[1] = DF[0][2] * DF[2][1] - DF[0][1] * DF[2][2];
+        A[2] = DF[0][1] * DF[1][2] - DF[0][2] * DF[1][1];
+        A[3] = DF[1][2] * DF[2][0] - DF[1][0] * DF[2][2];
+        A[4] = DF[0][0] * DF[2][2] - DF[0][2] * DF[2][0];
+        A[5] = DF[0][2] * DF[1][0] - DF[0][0] * DF[1][2];
+        A[6] = DF[1][0] * DF[2][1] - DF[1][1] * DF[2][0];
+        A[7] = DF[0][1] * DF[2][0] - DF[0][0] * DF[2][1];
+        A[8] = DF[0][0] * DF[1][1] - DF[0][1] * DF[1][0];
+      }
+    }
+    for (int f = 0; f < 2; ++f) {
+      stm_field_fn fn = f == 0 ? E0 : H0;
+      if (!fn) continue;
+      fn(user, cnt * nq3, pts.data(), val.data());
+      for (int64_t e = e0; e < e1; ++e) {
+        const double mat = f == 0 ? c->h_eps[e] : c->h_mu[e];
+        for (int g = 0; g < nq3; ++g) {
+          const int64_t k = (e - e0) * nq3 + g;
+          const double* A = &adj[9 * k];
+          const double* v = &val[3 * k];
+          const double w = mat * wq[g % nq] * wq[(g / nq) % nq] * wq[g / (nq * nq)];
+          for (int cc = 0; cc < 3; ++cc) F[(size_t)cc * nq3 + g] = w * (A[3 * cc] * v[0] + A[3 * cc + 1] * v[1] + A[3 * cc + 2] * v[2]);
+        }
+        for (int cc = 0; cc < 3; ++cc) {  // three 1-D contractions onto phi_s
+          const double* f0 = &F[(size_t)cc * nq3];
+          G1.assign((size_t)nq * nq * N, 0.0);
+          for (int gz = 0; gz < nq; ++gz)
+            for (int gy = 0; gy < nq; ++gy)
+              for (int j = 0; j < N; ++j) {
+                double acc = 0.0;
+                for (int gx = 0; gx < nq; ++gx) acc += f0[(gz * nq + gy) * nq + gx] * Lq[gx * N + j];
+                G1[(gz * nq + gy) * N + j] = acc;
+              }
+          G2.assign((size_t)nq * N * N, 0.0);
+          for (int gz = 0; gz < nq; ++gz)
+            for (int kk = 0; kk < N; ++kk)
+              for (int j = 0; j < N; ++j) {
+                double acc = 0.0;
+                for (int gy = 0; gy < nq; ++gy) acc += G1[(gz * nq + gy) * N + j] * Lq[gy * N + kk];
+                G2[(gz * N + kk) * N + j] = acc;
+              }
+          double* row = &rhs[(size_t)c->h_off_state[e] + (size_t)(f * 3 + cc) * N3];
+          for (int l = 0; l < N; ++l)
+            for (int kk = 0; kk < N; ++kk)
+              for (int j = 0; j < N; ++j) {
+                double acc = 0.0;
+                for (int gz = 0; gz < nq; ++gz) acc += G2[(gz * N + kk) * N + j] * Lq[gz * N + l];
+                row[(l * N + kk) * N + j] = acc;
+              }
+        }
+      }
+    }
+  }
+  // CG on the device: x, r, p, Ap, z
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, 5 * (size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, STM_ENOMEM, "projection work vectors");
+  }
+  double *x = buf, *r = buf + n, *pv = buf + 2 * n, *Ap = buf + 3 * n, *z = buf + 4 * n;
+  auto dot = [&](const double* a, const double* b, double* out) -> int {
+    multidot<double>(a, b, 0, 1, false, n, c->red_partial, c->red_out, c->stream);
+    c->launches += 2;
+    STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    *out = c->h_pinned[0];
+    return STM_OK;
+  };
+  int rc = STM_OK;
+  do {
+    if (cudaMemsetAsync(x, 0, n * sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(r, rhs.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      rc = fail(c, STM_EDEVICE, "projection copies");
+      break;
+    }
+    double rr0;
+    if ((rc = dot(r, r, &rr0))) break;
+    precond_curved<double, double>(z, r, 0, 0, nullptr, c->Pinv64, N3, c->ne, false, c->stream);
+    STM_CK(cudaMemcpyAsync(pv, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    double rz;
+    if ((rc = dot(r, z, &rz))) break;
+    for (int it = 0; it < 1000 && rr0 > 0; ++it) {
+      const int em = launch_mass_curved<double>(P, 1, pv, 6LL * N3, N3, nullptr, 0, 0, c->Gw64, c->eps64, c->mu64,
+                                                c->ct, c->ne, Ap, c->stream);
+      c->launches += 1;
+      if (em) {
+        rc = fail(c, STM_EDEVICE, "projection mass launch");
+        break;
+      }
+      double pAp;
+      if ((rc = dot(pv, Ap, &pAp))) break;
+      const double alpha = rz / pAp;
+      Coef16 ca{}, cr{};
+      ca.c[0] = -alpha;
+      cr.c[0] = alpha;
+      axpy_norm<double>(x, pv, 0, 1, ca, n, c->red_partial, c->red_out, c->stream);  // x += alpha p
+      axpy_norm<double>(r, Ap, 0, 1, cr, n, c->red_partial, c->red_out, c->stream);  // r -= alpha Ap
+      c->launches += 4;
+      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      STM_CK(cudaStreamSynchronize(c->stream));
+      if (!(c->h_pinned[0] > 1e-28 * rr0)) break;  // |r| <= 1e-14 |b| (or not finite: stop)
+      precond_curved<double, double>(z, r, 0, 0, nullptr, c->Pinv64, N3, c->ne, false, c->stream);
+      c->launches += 1;
+      double rz1;
+      if ((rc = dot(r, z, &rz1))) break;
+      Coef16 cb{};
+      cb.c[0] = -rz1 / rz;
+      rz = rz1;
+      axpy_norm<double>(z, pv, 0, 1, cb, n, c->red_partial, c->red_out, c->stream);  // z += beta p
+      c->launches += 2;
+      std::swap(pv, z);
+    }
+    if (rc) break;
+    STM_CK(cudaMemcpyAsync(c->state, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    c->t = t;
+  } while (false);
+  cudaFree(buf);
+  return rc;
+}
+
+extern "C" {
+
 int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, void* user) {
   // Covariant L2 projection on a brick: u_c[s] = h_c int_K^ phi_s (F_c o F_K) dx^,
   // by the tensor Gauss rule with p+2 points per direction (per element degree).
   if (!c) return STM_EINVAL;
-  if (c->geometry == STM_GEOM_TRILINEAR)
-    return fail(c, STM_EUNSUPPORTED, "L2 projection on curved elements is not built; use stm_set_state");
+  if (c->geometry == STM_GEOM_TRILINEAR) return project_curved(c, t, E0, H0, user);
   std::vector<std::vector<double>> xg(9), wg(9), Lg(9);
   for (int P = 0; P <= 7; ++P) {
     const int nq = P + 2, N = P + 1;

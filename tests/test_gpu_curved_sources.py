@@ -224,3 +224,21 @@ def test_dof_layout(stm):
     assert np.array_equal(tr, meshgen.dof_offsets(m, "trial"))
     assert np.array_equal(te, meshgen.dof_offsets(m, "test"))
     assert st[-1] == s.n_state and tr[-1] == s.n_trial and te[-1] == s.n_test
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_projection_curved(stm, p):
+    """L2 projection of E0, H0 on trilinear hexes (metric mass solved by CG on the device)
+    against the oracle's element-wise dense projection."""
+    m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.8, 0.6), p=p, q=1, perturb=0.2)
+    meshgen.random_materials(m, 41, 42)
+    E0 = lambda x: np.stack([np.sin(3 * x[:, 0]) * x[:, 1], np.cos(2 * x[:, 2]) + x[:, 0], x[:, 0] * x[:, 1] * x[:, 2]], 1)
+    H0 = lambda x: np.stack([x[:, 2] ** 2, np.sin(x[:, 0] + x[:, 1]), np.exp(-x[:, 1])], 1)
+    o = stdg.Oracle(m)
+    uo = o.project(E0, H0)
+    s = stm.Slab(m)
+    s.set_initial(E0, H0, t=0.25)
+    ug, t = s.get_state()
+    assert t == 0.25
+    assert rel(ug, uo) < 1e-10
+    assert abs(s.energy() - o.energy(uo)) <= 1e-10 * o.energy(uo)
