@@ -134,8 +134,11 @@ typedef struct {
 
 /* Create a context on the current CUDA device.  Validates the mesh, copies
  * connectivity, degrees and materials to the device and precomputes the
- * element metric.  Returns STM_EUNSUPPORTED for non-uniform (p, q) or a
- * geometry this build does not handle. */
+ * element metric.  Returns STM_EINVAL for invalid input (degrees out of
+ * range, non-positive materials, bad ids) and STM_EUNSUPPORTED for a
+ * combination this build does not handle: uneven (p, q), 2:1 faces or N_K > 1
+ * on trilinear meshes; N_K > 1 together with 2:1 faces; the dissipative term
+ * with trilinear geometry, uneven q, 2:1 faces or N_K > 1. */
 int32_t stm_create(stm_ctx **ctx, const stm_mesh *mesh, const stm_opts *opts);
 int32_t stm_destroy(stm_ctx *ctx);
 const char *stm_last_error(stm_ctx *ctx);
