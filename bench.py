@@ -594,11 +594,16 @@ def run_ours(args):
     # DRAM bytes per k_apply launch from one ncu capture of the 32^3 case (2.444 GB), scaled by the
     # element count to this workload; valid for p=4, q=3 on 64^3 only
     traffic = 2.444e9 * ne / 32 ** 3 if (args.n, args.p, args.q) == (64, 4, 3) else None
+    try:  # context: the FP64 FMA rate this GPU reaches in a register-only kernel, measured live
+        probe = stm.fp64_probe()
+    except Exception:  # reported as missing, never replaced
+        probe = None
     roofline = {"kernel": f"k_apply<double,{args.p},{args.q}>", "bound": "alu", "achieved": ach, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 32^3 capture x 8 (bytes)",
                 "peak_source": "FP64 pipe: 2 FMA/clock/SM x 152 SMs x median SM clock under load (of derived)",
                 "launch_ms": apply_ms,
+                "fp64_probe_tflops": probe, "frac_of_probe": (ach / probe) if probe else None,
                 "prep": {"kernel": f"k_prep<double,{args.p},{args.q}>", "launch_ms": prep_ms,
                          "achieved": fl_prep * ne / (prep_ms / 1e3) / 1e12,
                          "frac": fl_prep * ne / (prep_ms / 1e3) / 1e12 / fp64_peak}}

@@ -233,6 +233,11 @@ int32_t stm_autotune(stm_ctx *ctx, double dt, int32_t reps, int32_t n_max, int32
 int32_t stm_host_alloc(void **ptr, int64_t bytes);
 int32_t stm_host_free(void *ptr);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (a register-only
+ * kernel of independent FMA chains, about 10 ms); the paper has no counterpart:
+ * it is the denominator against which a benchmark can put the FP64 residual. */
+int32_t stm_fp64_probe(double *tflops);
+
 /* Number of kernels this context has launched (residual, Krylov, energy). */
 int32_t stm_launch_count(stm_ctx *ctx, int64_t *n);
 

@@ -944,6 +944,24 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
   return STM_OK;
 }
 
+// Peak probe of the FP64 pipe: independent chains of dependent FMAs per thread
+// (enough to hide the pipe latency), no memory traffic; the result is stored so
+// the chains are not removed.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(256) k_fma_probe(double* out, int iters, double a) {
+  double v[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) v[k] = threadIdx.x * 1e-3 + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) v[k] = fma(v[k], a, 1e-7);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) acc += v[k];
+  out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = acc;
+}
+
 __global__ void k_init_guess(double* x, const double* state, int64_t q, int64_t n3, int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t blk = j / n3, s = j - blk * n3;
@@ -2234,6 +2252,36 @@ int32_t stm_host_free(void* ptr) {
     cudaGetLastError();
     return STM_EINVAL;
   }
+  return STM_OK;
+}
+
+int32_t stm_fp64_probe(double* tflops) {
+  if (!tflops) return STM_EINVAL;
+  *tflops = 0.0;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return STM_EDEVICE;
+  const int grid = sms * 8, block = 256, iters = 4096;
+  double* out = nullptr;
+  if (cudaMalloc(&out, (size_t)grid * block * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return STM_ENOMEM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_probe<<<grid, block>>>(out, iters, 1.0 + 1e-9);  // warm-up
+  cudaEventRecord(e0);
+  k_fma_probe<<<grid, block>>>(out, iters, 1.0 + 1e-9);
+  cudaEventRecord(e1);
+  const cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return STM_EDEVICE;
+  *tflops = 2.0 * kProbeChains * (double)iters * grid * block / (ms * 1e-3) / 1e12;
   return STM_OK;
 }
 

@@ -39,7 +39,7 @@ EXPORTS = (
     "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply",
     "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
-    "stm_set_source_gauss", "stm_set_boundary", "stm_set_source", "stm_dof_layout",
+    "stm_set_source_gauss", "stm_set_boundary", "stm_set_source", "stm_dof_layout", "stm_fp64_probe",
     "stm_server_create", "stm_server_submit", "stm_server_poll", "stm_server_wait", "stm_server_stats",
     "stm_server_destroy", "stm_autotune", "stm_host_alloc", "stm_host_free",
 )
@@ -127,6 +127,7 @@ def lib() -> C.CDLL:
         L.stm_set_source_gauss.argtypes = [vp, C.POINTER(stm_gauss_src), i32]
         L.stm_set_boundary.argtypes = [vp, ST_FIELD_FN, vp]
         L.stm_set_source.argtypes = [vp, ST_FIELD_FN, vp]
+        L.stm_fp64_probe.argtypes = [C.POINTER(C.c_double)]
         L.stm_dof_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         L.stm_server_create.argtypes = [C.POINTER(vp), C.POINTER(stm_server_opts)]
         L.stm_server_submit.argtypes = [vp, C.POINTER(stm_request), C.POINTER(i64)]
@@ -158,6 +159,15 @@ def residual_apply_noalloc(n_elem, p, q, dt, nbr, h, eps, mu, U, R, stream=None)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     return lib().stm_residual_apply_noalloc(n_elem, p, q, dt, *args, int(stream))
+
+
+def fp64_probe() -> float:
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    v = C.c_double()
+    rc = lib().stm_fp64_probe(C.byref(v))
+    if rc != STM_OK:
+        raise StmError(rc, "stm_fp64_probe failed")
+    return v.value
 
 
 class HostBuffer:
