@@ -670,16 +670,6 @@ class Oracle:
             out.append(np.concatenate(blk))
         return np.concatenate(out)
 
-    def evaluate(self, u, e, xh) -> np.ndarray:
-        """Physical (E, H) of spatial coefficients u at reference points xh of element e -> [2, P, 3]."""
-        p = int(self.p[e])
-        n3 = (p + 1) ** 3
-        o = int(np.sum(6 * (self.p[:e] + 1) ** 3))
-        blk = u[o:o + 6 * n3].reshape(2, 3, n3)
-        pts = _points(self.X8(e), p, np.atleast_2d(xh))
-        ref = np.einsum("fcs,ps->fpc", blk, pts.phi)
-        return np.einsum("pci,fpc->fpi", pts.DFinv, ref)
-
     def test_projection_in_time(self, U) -> np.ndarray:
         """pi U: the L2 projection of U onto the element's temporal test space, as
         coefficients of the test functions L_i on each sub-interval (test layout)."""
