@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra legs")
     ap.add_argument("--legs", default="hp_batch,curved,serving,inexact,dissipative,time_refinement",
-                    help="comma-separated extra legs to run")
+                    help="comma-separated extra legs to run (also, opt-in: serving_full = the full serving "
+                         "stream, 512 requests with n up to 48, both precisions; tm11_hp = the hp experiment of "
+                         "Sec. 6.1.1; iteration_study = GMRES iterations of the Sec. 5.3 resonator vs tolerance "
+                         "and initial guess)")
     ap.add_argument("--profile-case", default=None, choices=["apply", "curved", "solve"],
                     help="run a small fixed case for a profiler and exit (no JSON line): 'apply' = --steps "
                          "residual applies on --n^3 bricks (p, q), 'curved' = the same on trilinear hexes "
@@ -411,6 +414,116 @@ def leg_inexact():
     return out
 
 
+def tm_mode(mm, xy_only=True):
+    """The TM_mm cavity mode of the PEC box (Sec. 6.1.1 with m = n = mm): E = sin(mm pi x)
+    sin(mm pi y) cos(w t) e_z, H from mu H_t = -curl E, w = pi sqrt(2) mm (eps = mu = 1)."""
+    import numpy as np
+
+    w = math.pi * math.sqrt(2.0) * mm
+
+    def E(x, t):
+        z = np.zeros(x.shape[0])
+        return np.stack([z, z, np.sin(mm * math.pi * x[:, 0]) * np.sin(mm * math.pi * x[:, 1]) * math.cos(w * t)], 1)
+
+    def H(x, t):
+        f = -math.sin(w * t) / w * mm * math.pi
+        return np.stack([f * np.sin(mm * math.pi * x[:, 0]) * np.cos(mm * math.pi * x[:, 1]),
+                         -f * np.cos(mm * math.pi * x[:, 0]) * np.sin(mm * math.pi * x[:, 1]),
+                         np.zeros(x.shape[0])], 1)
+
+    return E, H, w
+
+
+def leg_tm11_hp(periods=20, p_mins=(1, 2, 3, 4)):
+    """The hp experiment of Sec. 6.1.1: the TM_11 mode in [0,1] x [0,1] x [0,1/5] on 5 x 5 x 1
+    hexahedra; from the boundary ring to the centre the elements take N_K = 1, 2, 4 local time
+    steps and degrees p = q = p_min, p_min + 1, p_min + 2.  Slab dt = h / (2 p_min + 1) with
+    h = 1/5.  Reports the spatial L2 error at the slab ends once per period, and the
+    L2(0,T; L2) error from those samples (trapezoid rule), for each p_min."""
+    import numpy as np
+
+    from paper_1307_5310_gb300 import meshgen, stm
+
+    E, H, w = tm_mode(1)
+    T_per = 2 * math.pi / w
+    out = {"workload": f"TM_11 in [0,1]^2 x [0,0.2], 5x5x1 hexahedra, rings N_K = 1/2/4 and p = q = p_min + "
+                       f"0/1/2, PEC, dt = 0.2/(2 p_min + 1), {periods} periods, FP64 GMRES(10) to 1e-10",
+           "runs": {}}
+    for pm in p_mins:
+        m = meshgen.box_mesh(5, 5, 1, hi=(1.0, 1.0, 0.2), p=1, q=1)
+        cen = m["vert"][m["hex"]].mean(axis=1)
+        i, j = np.floor(cen[:, 0] * 5).astype(int), np.floor(cen[:, 1] * 5).astype(int)
+        ring = np.minimum(np.minimum(i, j), np.minimum(4 - i, 4 - j))
+        m["p"] = (pm + ring).astype(np.uint8)
+        m["q"] = (pm + ring).astype(np.uint8)
+        m["nk"] = np.array([1, 2, 4])[ring].astype(np.uint8)
+        dt = 0.2 / (2 * pm + 1)
+        steps_per = max(1, int(round(T_per / dt)))
+        dt = T_per / steps_per  # whole periods
+        s = stm.Slab(m, tol=1e-10, max_it=4000, reorth=False)
+        aux = stm.Slab(m)
+        s.set_initial(lambda x: E(x, 0.0), lambda x: H(x, 0.0))
+
+        def err(t):
+            aux.set_initial(lambda x: E(x, t), lambda x: H(x, t))
+            ue, _ = aux.get_state()
+            u, _ = s.get_state()
+            aux.set_state(u - ue)
+            return math.sqrt(2.0 * aux.energy())
+
+        errs, its = [err(0.0)], 0
+        torch_sync()
+        a = time.perf_counter()
+        for k in range(periods):
+            for _ in range(steps_per):
+                rc, rep = s.slab_solve(dt)
+                if rc != stm.STM_OK:
+                    raise RuntimeError(f"slab solve returned {rc}")
+                its += rep["iterations"]
+            errs.append(err((k + 1) * T_per))
+        torch_sync()
+        ms = (time.perf_counter() - a) * 1e3
+        l2l2 = math.sqrt(sum(0.5 * (errs[k] ** 2 + errs[k + 1] ** 2) * T_per for k in range(periods)))
+        out["runs"][f"p_min{pm}"] = {"dt": dt, "slabs": periods * steps_per, "dofs": int(s.n_trial),
+                                     "gmres_iterations_per_slab": its / (periods * steps_per),
+                                     "error_per_period": errs, "l2_l2_error": l2l2, "ms": ms}
+        s.close()
+        aux.close()
+    e = [out["runs"][f"p_min{pm}"]["l2_l2_error"] for pm in p_mins]
+    out["log10_error_slope_per_p"] = float(np.polyfit(np.array(p_mins, float), np.log10(e), 1)[0])
+    return out
+
+
+def leg_iteration_study(slabs=40):
+    """GMRES(10) iterations per slab of the resonator of Sec. 5.3 (TM_mm mode, 8^3 bricks,
+    p = q = 1..6, dt = h/(2p+1), m = 1,1,2,2,3,3) for stop tolerances 1e-8 ... 1e-14 of the
+    relative true residual, from the initial guess u_1 = u_0 and from zero; the paper's exact
+    solves take 7.9, 24, 25, 20, 22, 18 iterations per slab."""
+    from paper_1307_5310_gb300 import meshgen, stm
+
+    out = {"paper_N_it": {"p1": 7.9, "p2": 24.0, "p3": 25.0, "p4": 20.0, "p5": 22.0, "p6": 18.0},
+           "workload": f"TM_mm mode, PEC unit cube, 8^3 bricks, p=q, dt=h/(2p+1), first {slabs} slabs, FP64 "
+                       "GMRES(10) right-preconditioned, stop on ||R(U^k)|| <= tol ||R(unknowns 0)||"}
+    for p in range(1, 7):
+        mm = (p + 1) // 2
+        E, H, _ = tm_mode(mm)
+        m = meshgen.box_mesh(8, p=p, q=p)
+        dt = (1.0 / 8) / (2 * p + 1)
+        row = {}
+        for zero in (False, True):
+            for tol in (1e-8, 1e-10, 1e-12, 1e-14):
+                s = stm.Slab(m, tol=tol, max_it=4000, reorth=False, zero_guess=zero)
+                s.set_initial(lambda x: E(x, 0.0), lambda x: H(x, 0.0))
+                it = 0
+                for _ in range(slabs):
+                    rc, rep = s.slab_solve(dt)
+                    it += rep["iterations"]
+                s.close()
+                row[f"{'zero' if zero else 'u0'}_tol{tol:g}"] = it / slabs
+        out[f"p{p}"] = row
+    return out
+
+
 def torch_sync():
     import torch
 
@@ -501,19 +614,18 @@ def leg_time_refinement(fp64_peak):
             "slab_solve_mixed": {"ms": solmx, "iterations": itmx, "rc": rcmx}}
 
 
-def leg_serving(n_req=48, rate=50.0, seed=1311):
-    """Poisson stream (mean `rate` req/s) of cavity/scattering requests, n^3 meshes with n
-    log-uniform in [8, 24] (multiples of 4), p ~ U{2..6}, q ~ U{1..3}, random eps/mu boxes and
-    Gaussian pulses, 10 slabs each to 1e-9, mixed precision."""
+def serving_stream(n_req, n_max, rate=50.0, seed=1311):
+    """The request stream of the serving workload: Poisson arrivals (mean `rate` req/s), n^3
+    unit-cube bricks with n log-uniform in [8, n_max] (multiples of 4), p ~ U{2..6},
+    q ~ U{1..3}, 1-4 eps/mu boxes U[1,4], 1-3 Gaussian pulses, cavity or scattering, 10 slabs
+    of dt = h/(2p+1) each."""
     import numpy as np
-
-    from paper_1307_5310_gb300 import stm
 
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, n_req)
     reqs = []
     for k in range(n_req):
-        n = int(4 * round(np.exp(rng.uniform(np.log(8), np.log(24))) / 4))
+        n = int(4 * round(np.exp(rng.uniform(np.log(8), np.log(n_max))) / 4))
         p, q = int(rng.integers(2, 7)), int(rng.integers(1, 4))
         boxes = []
         for _ in range(int(rng.integers(1, 5))):
@@ -528,11 +640,18 @@ def leg_serving(n_req=48, rate=50.0, seed=1311):
         kind = int(rng.integers(0, 2))
         reqs.append(dict(n=n, p=p, q=q, n_slabs=10, dt=(1.0 / n) / (2 * p + 1), kind=kind, boxes=boxes,
                          sources=srcs if kind == 1 else srcs[:1]))
-    srv = stm.Server(workers=8, precision=stm.STM_MIXED, tol=1e-9, max_it=2000)
+    return reqs, np.cumsum(gaps)
+
+
+def run_stream(reqs, arrivals, precision, workers=8):
+    """Submit the stream at its arrival times to a server and wait for every result."""
+    from paper_1307_5310_gb300 import stm
+
+    srv = stm.Server(workers=workers, precision=precision, tol=1e-9, max_it=2000)
     t0 = time.perf_counter()
     tickets = []
     for k, r in enumerate(reqs):
-        while time.perf_counter() - t0 < float(np.sum(gaps[:k + 1])):
+        while time.perf_counter() - t0 < float(arrivals[k]):
             time.sleep(0.0005)
         tickets.append(srv.submit(**r))
     res = [srv.wait(t)[0] for t in tickets]
@@ -540,12 +659,28 @@ def leg_serving(n_req=48, rate=50.0, seed=1311):
     st = srv.stats()
     srv.close()
     lat = sorted(r["latency_ms"] for r in res if r["status"] >= 0)
-    return {"requests": n_req, "offered_req_per_s": rate, "achieved_req_per_s": len(lat) / wall,
-            "completed": st["completed"], "failed": st["failed"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "slab_solves_per_s": st["solves_per_s"], "peak_admitted_gb": st["peak_admitted_bytes"] / 1e9,
-            "max_rel_residual": max(r["max_rel_residual"] for r in res), "workers": 8, "precision": "mixed",
-            "workload": "Poisson stream; n^3 unit-cube bricks, n log-uniform in [8,24] (x4), p~U{2..6}, q~U{1..3}, "
-                        "1-4 eps/mu boxes U[1,4], 1-3 Gaussian pulses, cavity or scattering, 10 slabs to 1e-9"}
+    solves = 10 * len(lat)
+    return {"achieved_req_per_s": len(lat) / wall, "completed": st["completed"], "failed": st["failed"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "slab_solves_per_s": solves / wall, "wall_s": wall,
+            "peak_admitted_gb": st["peak_admitted_bytes"] / 1e9,
+            "max_rel_residual": max(r["max_rel_residual"] for r in res),
+            "gmres_iterations": int(sum(r["iterations"] for r in res))}
+
+
+def leg_serving(n_req=48, n_max=24, rate=50.0, seed=1311):
+    """The serving workload in mixed precision and in plain FP64 (same stream, same 1e-9
+    target): solves/s, latency percentiles, and the mixed-over-FP64 throughput ratio."""
+    from paper_1307_5310_gb300 import stm
+
+    reqs, arrivals = serving_stream(n_req, n_max, rate, seed)
+    out = {"requests": n_req, "offered_req_per_s": rate, "workers": 8,
+           "workload": f"Poisson stream (mean {rate:g} req/s) of {n_req} requests; n^3 unit-cube bricks, n "
+                       f"log-uniform in [8,{n_max}] (x4), p~U{{2..6}}, q~U{{1..3}}, 1-4 eps/mu boxes U[1,4], "
+                       "1-3 Gaussian pulses, cavity or scattering, 10 slabs each to 1e-9 relative residual"}
+    for name, prec in (("mixed", stm.STM_MIXED), ("fp64", stm.STM_FP64)):
+        out[name] = run_stream(reqs, arrivals, prec)
+    out["mixed_over_fp64_solves_per_s"] = out["mixed"]["slab_solves_per_s"] / out["fp64"]["slab_solves_per_s"]
+    return out
 
 
 def dist_max(v, device="cuda"):
@@ -709,7 +844,9 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         for name, fn in (("hp_batch", lambda: leg_hp_batch(fp64_peak)), ("curved", lambda: leg_curved(fp64_peak)),
-                         ("serving", leg_serving), ("inexact", leg_inexact),
+                         ("serving", leg_serving), ("serving_full", lambda: leg_serving(512, 48)),
+                         ("inexact", leg_inexact), ("tm11_hp", leg_tm11_hp),
+                         ("iteration_study", leg_iteration_study),
                          ("dissipative", lambda: leg_dissipative(fp64_peak)),
                          ("time_refinement", lambda: leg_time_refinement(fp64_peak))):
             if name not in args.legs.split(","):

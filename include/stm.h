@@ -54,6 +54,11 @@ extern "C" {
 #define STM_ENOTCONV 1        /* solver stopped at max_it; best iterate kept     */
 
 #define STM_GEOM_BRICK 0     /* axis-aligned boxes (affine, diagonal DF)          */
+#define STM_GEOM_AFFINE 1    /* parallelepipeds: x = x_0 + DF x^ with a constant,
+                                general DF (vertex v at x_0 + DF (v&1, v>>1&1,
+                                v>>2&1)); the mass term uses the constant 3x3
+                                metric G = |J| DF^{-1} DF^{-T} (Sec. 5.2, "mass
+                                residual"); same face rule as TRILINEAR          */
 #define STM_GEOM_TRILINEAR 2 /* trilinear maps from the 8 vertices (curved); face 2d+1
                                 of e and face 2d of its neighbour must have the same
                                 four vertex ids in the same reference order         */
@@ -120,6 +125,9 @@ typedef struct {
                             (0: the non-dissipative method).  Brick meshes with one
                             q and no 2:1 faces; else stm_create returns
                             STM_EUNSUPPORTED                                        */
+  int32_t zero_guess;    /* 1: GMRES starts each slab from all unknowns 0; 0 (default):
+                            from u_1 = u_0, higher modes 0 (the field held constant
+                            over the slab).  The converged solution is the same     */
 } stm_opts;
 
 typedef struct {
@@ -165,8 +173,9 @@ int32_t stm_get_state(stm_ctx *ctx, double *t, void *u, int32_t mem);
  * direction; becomes the state at time t.  Either callback may be NULL (0).
  * Bricks: the diagonal mass is inverted directly.  Trilinear meshes: the
  * element systems with the metric mass (the same (p+2)^3 rule as the
- * residual) are solved by conjugate gradients on the device to 1e-14
- * relative residual; STM_EDEVICE / STM_ENOMEM on failure. */
+ * residual) are solved by conjugate gradients on the device, restarted from
+ * the true residual until that is below 1e-15 of the right side (at most
+ * three restarts); STM_EDEVICE / STM_ENOMEM on failure. */
 typedef void (*stm_field_fn)(void *user, int64_t npts, const double *x /*[npts][3]*/,
                              double *out /*[npts][3]*/);
 int32_t stm_set_initial(stm_ctx *ctx, double t, stm_field_fn E0, stm_field_fn H0, void *user);
@@ -314,17 +323,18 @@ int32_t stm_server_destroy(stm_server *srv);
  * counterpart; this is a service for callers that cannot call cudaMalloc,
  * e.g. code inside a CUDA graph being captured, or a host whose device memory
  * all belongs to its own pool).  Same result as stm_residual_apply with
- * prec = STM_FP64 on an STM_GEOM_BRICK mesh of uniform (p, q), with PEC and no
- * sources, but without a context: every argument is a device pointer the
- * caller owns.
+ * prec = STM_FP64 on an STM_GEOM_BRICK mesh of uniform (p, q), 0 <= p <= 7,
+ * 1 <= q <= 6, with PEC and no sources, but without a context: every argument
+ * is a device pointer the caller owns.
  *   nbr [n_elem][6] int32 face neighbours (as stm_mesh.nbr, -1 = boundary);
  *   h   [n_elem][3] edge lengths of the axis-aligned boxes;
  *   eps, mu [n_elem]; U trial layout, R test layout (both double).
  * Scratch lives in one static device array of STM_NOALLOC_SCRATCH_BYTES,
  * held by every GPU that loads the library until the process exits.  A call
  * needs 8 (6 + 6 q (p+1)^3 + 24 q (p+1)^2) bytes per element (each of the three
- * parts rounded up to 256 bytes); a larger request returns STM_EINVAL, with
- * a message on stderr, and launches nothing.  The first call on a device
+ * parts rounded up to 256 bytes); a larger request, degrees out of range or a
+ * null pointer return STM_EINVAL (the size case with a message on stderr)
+ * before any CUDA call, and nothing is launched.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share
  * the array, so calls that overlap on the GPU (different streams, or other

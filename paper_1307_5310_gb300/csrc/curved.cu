@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_mass_curved(const T* __restrict__ um, i
                                                      const T* __restrict__ u0, int64_t u0_es, int64_t u0_cs,
                                                      const T* __restrict__ Gw, const T* __restrict__ eps,
                                                      const T* __restrict__ mu, CTab<T> L, int64_t ne,
-                                                     T* __restrict__ R) {
+                                                     T* __restrict__ R, const int32_t* skip) {
+  if (skip && *skip) return;
   constexpr int N = P + 1, NQ = P + 2, N2 = N * N, N3 = N2 * N, NQ2 = NQ * NQ, NQ3 = NQ2 * NQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* g6 = reinterpret_cast<T*>(smem_raw);  // [6][NQ3]
@@ -190,7 +191,14 @@ __global__ void __launch_bounds__(256) k_mass_curved(const T* __restrict__ um, i
 
 template <typename S, typename X, bool Add>
 __global__ void k_precond_curved(X* __restrict__ out, const S* __restrict__ V, int64_t ldv, int k, Coef16 y,
-                                 const S* __restrict__ Pinv, int64_t qn3, int64_t ne) {
+                                 const S* __restrict__ Pinv, int64_t qn3, int64_t ne, const int32_t* skip,
+                                 const GmresState* st) {
+  if (skip && *skip) return;
+  if (st) {
+    k = st->k;
+    if (k <= 0) return;
+    for (int j = 0; j < kMaxDots; ++j) y.c[j] = st->yc[j];
+  }
   const int64_t items = ne * 2 * qn3;
   for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items;
        it += (int64_t)gridDim.x * blockDim.x) {
@@ -292,25 +300,30 @@ int launch_metric(int P, const double* X8, const double* eps, const double* mu, 
 
 template <typename T, int P, int Q>
 int mass_pq(const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_es, int64_t u0_cs, const T* Gw,
-            const T* eps, const T* mu, const CurvedTables& ct, int64_t ne, T* R, cudaStream_t s) {
+            const T* eps, const T* mu, const CurvedTables& ct, int64_t ne, T* R, cudaStream_t s,
+            const int32_t* skip) {
   constexpr int NQ3 = (P + 2) * (P + 2) * (P + 2);
   const size_t sm = sizeof(T) * 12 * NQ3;
-  static const bool configured = [&] {
+  static std::atomic<uint64_t> configured_devices{0};
+  once_per_device(configured_devices, [&] {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_mass_curved<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    return true;
-  }();
-  (void)configured;
-  const int grid = (int)(ne < (1 << 30) ? ne : (1 << 30));
-  k_mass_curved<T, P, Q><<<grid, 256, sm, s>>>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, ctab<T>(ct), ne, R);
+  });
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // grid-stride over elements, at most 16 CTAs per SM (a skipped launch costs one wave)
+  const int grid = (int)(ne < 16LL * sms ? ne : 16LL * sms);
+  k_mass_curved<T, P, Q><<<grid, 256, sm, s>>>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, ctab<T>(ct), ne, R,
+                                                skip);
   return (int)cudaGetLastError();
 }
 
 template <typename T>
 int launch_mass_curved(int P, int Q, const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_es,
                        int64_t u0_cs, const T* Gw, const T* eps, const T* mu, const CurvedTables& ct, int64_t ne, T* R,
-                       cudaStream_t s) {
+                       cudaStream_t s, const int32_t* skip) {
 #define STM_MQ(p, q) \
-  if (P == p && Q == q) return mass_pq<T, p, q>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, ct, ne, R, s);
+  if (P == p && Q == q) return mass_pq<T, p, q>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, ct, ne, R, s, skip);
 #define STM_MP(p) STM_MQ(p, 1) STM_MQ(p, 2) STM_MQ(p, 3) STM_MQ(p, 4) STM_MQ(p, 5) STM_MQ(p, 6)
   STM_MP(0) STM_MP(1) STM_MP(2) STM_MP(3) STM_MP(4) STM_MP(5) STM_MP(6) STM_MP(7)
 #undef STM_MP
@@ -320,13 +333,13 @@ int launch_mass_curved(int P, int Q, const T* um, int64_t um_es, int64_t um_cs, 
 
 template <typename S, typename X>
 void precond_curved(X* out, const S* V, int64_t ldv, int k, const double* y, const S* Pinv, int64_t qn3, int64_t ne,
-                    bool add, cudaStream_t s) {
+                    bool add, cudaStream_t s, const int32_t* skip, const GmresState* st) {
   Coef16 yc{};
   for (int j = 0; j < k && j < kMaxDots; ++j) yc.c[j] = y[j];
   const int64_t items = ne * 2 * qn3;
   const int grid = (int)((items + 255) / 256 < 4 * kRedBlocks ? (items + 255) / 256 : 4 * kRedBlocks);
-  if (add) k_precond_curved<S, X, true><<<grid, 256, 0, s>>>(out, V, ldv, k, yc, Pinv, qn3, ne);
-  else k_precond_curved<S, X, false><<<grid, 256, 0, s>>>(out, V, ldv, k, yc, Pinv, qn3, ne);
+  if (add) k_precond_curved<S, X, true><<<grid, 256, 0, s>>>(out, V, ldv, k, yc, Pinv, qn3, ne, skip, st);
+  else k_precond_curved<S, X, false><<<grid, 256, 0, s>>>(out, V, ldv, k, yc, Pinv, qn3, ne, skip, st);
 }
 
 int launch_energy_curved(int P, const double* u, const double* Gw, const double* eps, const double* mu,
@@ -344,15 +357,15 @@ int launch_energy_curved(int P, const double* u, const double* Gw, const double*
 
 template int launch_mass_curved<double>(int, int, const double*, int64_t, int64_t, const double*, int64_t, int64_t,
                                         const double*, const double*, const double*, const CurvedTables&, int64_t,
-                                        double*, cudaStream_t);
+                                        double*, cudaStream_t, const int32_t*);
 template int launch_mass_curved<float>(int, int, const float*, int64_t, int64_t, const float*, int64_t, int64_t,
                                        const float*, const float*, const float*, const CurvedTables&, int64_t, float*,
-                                       cudaStream_t);
+                                       cudaStream_t, const int32_t*);
 template void precond_curved<double, double>(double*, const double*, int64_t, int, const double*, const double*,
-                                             int64_t, int64_t, bool, cudaStream_t);
+                                             int64_t, int64_t, bool, cudaStream_t, const int32_t*, const GmresState*);
 template void precond_curved<float, float>(float*, const float*, int64_t, int, const double*, const float*, int64_t,
-                                           int64_t, bool, cudaStream_t);
+                                           int64_t, bool, cudaStream_t, const int32_t*, const GmresState*);
 template void precond_curved<float, double>(double*, const float*, int64_t, int, const double*, const float*, int64_t,
-                                            int64_t, bool, cudaStream_t);
+                                            int64_t, bool, cudaStream_t, const int32_t*, const GmresState*);
 
 }  // namespace stm

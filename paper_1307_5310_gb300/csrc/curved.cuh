@@ -33,13 +33,15 @@ int launch_metric(int P, const double* X8, const double* eps, const double* mu, 
 template <typename T>
 int launch_mass_curved(int P, int Q, const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_es,
                        int64_t u0_cs, const T* Gw, const T* eps, const T* mu, const CurvedTables& ct, int64_t ne, T* R,
-                       cudaStream_t s);
+                       cudaStream_t s, const int32_t* skip = nullptr);
 
 // z[e][f][c][i][s] = sum_d Pinv[e][f][c][d] v[e][f][d][i][s]   (add = false), or x += that (add = true);
 // with k > 0, v is the combination sum_{j<k} y[j] V[j] (ldv apart).
+// With skip non-null nothing is done while *skip is set; with st non-null k and y come
+// from the device state of the GMRES cycle.
 template <typename S, typename X>
 void precond_curved(X* out, const S* V, int64_t ldv, int k, const double* y, const S* Pinv, int64_t qn3, int64_t ne,
-                    bool add, cudaStream_t s);
+                    bool add, cudaStream_t s, const int32_t* skip = nullptr, const GmresState* st = nullptr);
 
 // Per-element energies 1/2 mat_f u^T M_G u of the state -> el[e].
 int launch_energy_curved(int P, const double* u, const double* Gw, const double* eps, const double* mu,

@@ -13,7 +13,9 @@ __device__ __forceinline__ void degrees(const uint8_t* pq, int64_t e, int& n3, i
 
 template <typename S>
 __global__ void k_precond_hp(S* __restrict__ z, const S* __restrict__ v, const S* __restrict__ inv,
-                             const int64_t* __restrict__ off, const uint8_t* __restrict__ pq, int64_t ne) {
+                             const int64_t* __restrict__ off, const uint8_t* __restrict__ pq, int64_t ne,
+                             const int32_t* skip) {
+  if (skip && *skip) return;
   for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
     // one (field, component) block per inverse mass entry: all temporal test functions
     const int64_t o = off[e];
@@ -25,7 +27,12 @@ __global__ void k_precond_hp(S* __restrict__ z, const S* __restrict__ v, const S
 template <typename S, typename X>
 __global__ void k_combine_hp(X* __restrict__ x, const S* __restrict__ V, int64_t ldv, int k, Coef16 y,
                              const S* __restrict__ inv, const int64_t* __restrict__ off,
-                             const uint8_t* __restrict__ pq, int64_t ne) {
+                             const uint8_t* __restrict__ pq, int64_t ne, const GmresState* st) {
+  if (st) {
+    k = st->k;
+    for (int j = 0; j < kMaxDots; ++j) y.c[j] = st->yc[j];
+  }
+  if (k <= 0) return;
   for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
     const int64_t o = off[e];
     const int blk = (int)((off[e + 1] - o) / 6);
@@ -91,6 +98,7 @@ __global__ void k_energy_hp(const double* __restrict__ u, const double* __restri
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_hang(HangArgs<T> H) {
+  if (H.skip && *H.skip) return;
   for (int64_t slot = blockIdx.x; slot < H.n_slots; slot += gridDim.x) {
     const int e = H.elem[slot], face = H.face[slot], a = face >> 1;
     int n3, q;
@@ -132,14 +140,14 @@ inline int egrid(int64_t ne) { return (int)(ne < 65536 ? ne : 65536); }
 
 template <typename S>
 void precond_hp(S* z, const S* v, const S* inv, const int64_t* off_test, const uint8_t* pq, int64_t ne,
-                cudaStream_t s) {
-  k_precond_hp<S><<<egrid(ne), 256, 0, s>>>(z, v, inv, off_test, pq, ne);
+                cudaStream_t s, const int32_t* skip) {
+  k_precond_hp<S><<<egrid(ne), 256, 0, s>>>(z, v, inv, off_test, pq, ne, skip);
 }
 
 template <typename S, typename X>
 void combine_hp(X* x, const S* V, int64_t ldv, int k, const Coef16& y, const S* inv, const int64_t* off_test,
-                const uint8_t* pq, int64_t ne, cudaStream_t s) {
-  k_combine_hp<S, X><<<egrid(ne), 256, 0, s>>>(x, V, ldv, k, y, inv, off_test, pq, ne);
+                const uint8_t* pq, int64_t ne, cudaStream_t s, const GmresState* st) {
+  k_combine_hp<S, X><<<egrid(ne), 256, 0, s>>>(x, V, ldv, k, y, inv, off_test, pq, ne, st);
 }
 
 void init_guess_hp(double* x, const double* state, const int64_t* off_test, const int64_t* off_state,
@@ -165,12 +173,12 @@ template void launch_hang<double>(const HangArgs<double>&, cudaStream_t);
 template void launch_hang<float>(const HangArgs<float>&, cudaStream_t);
 
 template void precond_hp<double>(double*, const double*, const double*, const int64_t*, const uint8_t*, int64_t,
-                                 cudaStream_t);
+                                 cudaStream_t, const int32_t*);
 template void precond_hp<float>(float*, const float*, const float*, const int64_t*, const uint8_t*, int64_t,
-                                cudaStream_t);
+                                cudaStream_t, const int32_t*);
 template void combine_hp<double, double>(double*, const double*, int64_t, int, const Coef16&, const double*,
-                                         const int64_t*, const uint8_t*, int64_t, cudaStream_t);
+                                         const int64_t*, const uint8_t*, int64_t, cudaStream_t, const GmresState*);
 template void combine_hp<float, double>(double*, const float*, int64_t, int, const Coef16&, const float*,
-                                        const int64_t*, const uint8_t*, int64_t, cudaStream_t);
+                                        const int64_t*, const uint8_t*, int64_t, cudaStream_t, const GmresState*);
 
 }  // namespace stm

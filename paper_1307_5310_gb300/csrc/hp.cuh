@@ -15,12 +15,13 @@ namespace stm {
 // z = P^{-1} v (diagonal brick mass; test layout).
 template <typename S>
 void precond_hp(S* z, const S* v, const S* inv, const int64_t* off_test, const uint8_t* pq, int64_t ne,
-                cudaStream_t s);
+                cudaStream_t s, const int32_t* skip = nullptr);
 
-// x += P^{-1} sum_{j<k} y[j] V[j]  (test layout).
+// x += P^{-1} sum_{j<k} y[j] V[j]  (test layout); with st non-null k and y come from the
+// device state of the GMRES cycle.
 template <typename S, typename X>
 void combine_hp(X* x, const S* V, int64_t ldv, int k, const Coef16& y, const S* inv, const int64_t* off_test,
-                const uint8_t* pq, int64_t ne, cudaStream_t s);
+                const uint8_t* pq, int64_t ne, cudaStream_t s, const GmresState* st = nullptr);
 
 // x: mode 1 (first unknown) of every temporal sub-interval = state, higher modes 0.
 void init_guess_hp(double* x, const double* state, const int64_t* off_test, const int64_t* off_state,
@@ -57,6 +58,7 @@ struct HangArgs {
   const int64_t* hoff;      // [slot] offset of the slot's output
   T* hbuf;
   T Tm[2][8][8];
+  const int32_t* skip = nullptr;  // non-null: nothing is done while *skip is set
 };
 
 template <typename T>

@@ -82,7 +82,8 @@ struct Unroll {
 template <typename S, int K>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const S* __restrict__ w, const S* __restrict__ V,
                                                           int64_t ldv, int with_norm, int64_t n,
-                                                          double* __restrict__ partial) {
+                                                          double* __restrict__ partial, const int32_t* skip) {
+  if (skip && *skip) return;
   using VT = typename Vec<S>::T;
   constexpr int W = Vec<S>::W, U = Unroll<K>::U;
   __shared__ double sh[32];
@@ -138,13 +139,15 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const S* __restrict__ 
 
 template <typename S, int K>
 __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(S* __restrict__ w, const S* __restrict__ V, int64_t ldv,
-                                                           Coef16 c, int64_t n, double* __restrict__ partial) {
+                                                           Coef16 c, int64_t n, double* __restrict__ partial,
+                                                           const int32_t* skip, const double* cdev) {
+  if (skip && *skip) return;
   using VT = typename Vec<S>::T;
   constexpr int W = Vec<S>::W, U = Unroll<K>::U;
   __shared__ double sh[32];
   S cc[K > 0 ? K : 1];
 #pragma unroll
-  for (int i = 0; i < K; ++i) cc[i] = (S)c.c[i];
+  for (int i = 0; i < K; ++i) cc[i] = (S)(cdev ? cdev[i] : c.c[i]);
   Acc<S> acc;
   const int64_t nv = n / W;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
@@ -207,7 +210,8 @@ __device__ __forceinline__ int64_t block_of(int64_t j, int64_t blk) {
 
 template <typename S, bool Small>
 __global__ void k_precond(S* __restrict__ z, const S* __restrict__ v, const S* __restrict__ inv, int64_t blk,
-                          int64_t n) {
+                          int64_t n, const int32_t* skip) {
+  if (skip && *skip) return;
   using VT = typename Vec<S>::T;
   constexpr int W = Vec<S>::W;
   const int64_t nv = n / W;
@@ -225,14 +229,18 @@ __global__ void k_precond(S* __restrict__ z, const S* __restrict__ v, const S* _
 
 template <typename S, typename X, int K, bool Small>
 __global__ void k_precond_combine(X* __restrict__ x, const S* __restrict__ V, int64_t ldv, Coef16 y,
-                                  const S* __restrict__ inv, int64_t blk, int64_t n) {
+                                  const S* __restrict__ inv, int64_t blk, int64_t n, const GmresState* st) {
+  // with st: k and the coefficients come from the device state (K is the largest k)
+  const int kk = st ? st->k : K;
+  if (kk <= 0) return;
   S yy[K > 0 ? K : 1];
 #pragma unroll
-  for (int i = 0; i < K; ++i) yy[i] = (S)y.c[i];
+  for (int i = 0; i < K; ++i) yy[i] = (S)(st ? st->yc[i] : y.c[i]);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     S v = S(0);
 #pragma unroll
-    for (int i = 0; i < K; ++i) v = fma(yy[i], V[i * ldv + j], v);
+    for (int i = 0; i < K; ++i)
+      if (i < kk) v = fma(yy[i], V[i * ldv + j], v);
     x[j] = (X)x[j] + (X)(v * inv[block_of<Small>(j, blk)]);
   }
 }
@@ -251,9 +259,166 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(const double* __restrict
 }
 
 template <typename D, typename S>
-__global__ void k_convert(D* __restrict__ d, const S* __restrict__ s, int64_t n) {
+__global__ void k_convert(D* __restrict__ d, const S* __restrict__ s, int64_t n, const int32_t* skip) {
+  if (skip && *skip) return;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
     d[j] = (D)s[j];
+}
+
+
+// ---- device-side GMRES control -------------------------------------------------------------
+// One block of kCtrlThreads threads: the fixed-order reduction of kRedBlocks partial sums per
+// value (warp i % warps sums value i lane-strided, then a shuffle tree), then thread 0 runs
+// the scalar logic of the restart cycle on the state in device memory.
+constexpr int kCtrlThreads = 512;
+
+__device__ void reduce_values(const double* __restrict__ partial, int m, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < m; i += kCtrlThreads / 32) {
+    double v = 0.0;
+    for (int b = lane; b < kRedBlocks; b += 32) v += partial[i * kRedBlocks + b];
+    v = warp_sum(v);
+    if (lane == 0) out[i] = v;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCtrlThreads) k_gm_reduce(const double* __restrict__ partial, GmresState* st,
+                                                             int slot, const int32_t* skip) {
+  if (skip && *skip) return;
+  __shared__ double v[1];
+  reduce_values(partial, 1, v);
+  if (threadIdx.x == 0) st->red[slot] = v[0];
+}
+
+__global__ void k_gm_slab_start(GmresState* st, double tol, int max_it, int inexact) {
+  st->ref = sqrt(st->red[0]);
+  st->tol = tol;
+  st->max_it = max_it;
+  st->inexact = inexact;
+  st->iters = 0;
+  st->cycles = 0;
+  st->status = 0;
+  st->outer_done = 0;
+  st->skip = 0;
+  st->skip_reo = 1;
+  st->k = 0;
+  st->rel = 0.0;
+  st->phi = 0.0;
+  st->res = 0.0;
+}
+
+__global__ void k_gm_outer_check(GmresState* st) {
+  st->k = 0;
+  st->skip_reo = 1;
+  const double beta = sqrt(st->red[0]);
+  const double ref = st->ref;
+  st->rel = ref > 0 ? beta / ref : beta;
+  if (!isfinite(st->rel)) {
+    st->status = -5;  // STM_ENAN
+    st->skip = 1;
+    return;
+  }
+  bool done;
+  if (st->inexact) {
+    st->phi = sqrt(st->red[1]);
+    done = st->phi <= st->tol;
+  } else {
+    done = st->rel <= st->tol;
+  }
+  if (done) st->outer_done = 1;
+  st->skip = (done || st->iters >= st->max_it || beta == 0.0) ? 1 : 0;
+}
+
+__global__ void k_gm_cycle_init(GmresState* st, int slot_start, double floor_rel) {
+  if (st->skip) return;
+  const double b0 = sqrt(st->red[slot_start]);
+  if (!(b0 > 0.0)) {
+    st->skip = 1;
+    return;
+  }
+  st->cycles += 1;
+  // v_0 = V[0] / alpha_0 with V[0] = R = -r: alpha_0 = -|start|
+  st->alpha[0] = -b0;
+  st->g[0] = b0;
+  const double target = st->inexact ? st->tol : st->tol * st->ref;
+  st->tol_abs = fmax(target, floor_rel * b0);
+}
+
+__global__ void __launch_bounds__(kCtrlThreads) k_gm_gs(const double* __restrict__ partial, GmresState* st, int j,
+                                                         int second) {
+  if (second ? st->skip_reo : st->skip) return;
+  __shared__ double v[kMaxDots + 1];
+  reduce_values(partial, second ? j + 1 : j + 2, v);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i <= j; ++i) {
+      st->cc[i] = v[i] / (st->alpha[i] * st->alpha[i]);
+      const double h = v[i] / (st->alpha[i] * st->alpha[j]);
+      st->H[i * kMaxDots + j] = second ? st->H[i * kMaxDots + j] + h : h;
+    }
+    if (!second) st->before = v[j + 1];
+  }
+}
+
+__global__ void __launch_bounds__(kCtrlThreads) k_gm_after(const double* __restrict__ partial, GmresState* st,
+                                                            int reorth) {
+  if (st->skip) {
+    st->skip_reo = 1;
+    return;
+  }
+  __shared__ double v[1];
+  reduce_values(partial, 1, v);
+  if (threadIdx.x == 0) {
+    st->after = v[0];
+    st->skip_reo = (reorth && v[0] < 0.5 * st->before) ? 0 : 1;
+  }
+}
+
+__global__ void __launch_bounds__(kCtrlThreads) k_gm_givens(const double* __restrict__ partial, GmresState* st, int j,
+                                                             int m, int reo_mode) {
+  if (st->skip) return;
+  __shared__ double v[1];
+  const bool fresh = reo_mode ? !st->skip_reo : true;  // uniform over the block
+  if (fresh) reduce_values(partial, 1, v);
+  if (threadIdx.x != 0) return;
+  const double after = fresh ? v[0] : st->after;
+  double* H = st->H;
+  if (!isfinite(after) || !isfinite(st->before)) {
+    st->status = -5;  // STM_ENAN
+    st->skip = 1;
+    return;
+  }
+  const double nw = sqrt(after);
+  st->alpha[j + 1] = st->alpha[j] < 0 ? -nw : nw;
+  H[(j + 1) * kMaxDots + j] = nw / fabs(st->alpha[j]);
+  for (int i = 0; i < j; ++i) {
+    const double x = H[i * kMaxDots + j], y = H[(i + 1) * kMaxDots + j];
+    H[i * kMaxDots + j] = st->cs[i] * x + st->sn[i] * y;
+    H[(i + 1) * kMaxDots + j] = -st->sn[i] * x + st->cs[i] * y;
+  }
+  const double x = H[j * kMaxDots + j], y = H[(j + 1) * kMaxDots + j];
+  const double r = hypot(x, y);
+  st->cs[j] = r > 0 ? x / r : 1.0;
+  st->sn[j] = r > 0 ? y / r : 0.0;
+  H[j * kMaxDots + j] = r;
+  H[(j + 1) * kMaxDots + j] = 0.0;
+  st->g[j + 1] = -st->sn[j] * st->g[j];
+  st->g[j] = st->cs[j] * st->g[j];
+  st->iters += 1;
+  st->k = j + 1;
+  if (fabs(st->g[j + 1]) <= st->tol_abs || nw == 0.0 || st->iters >= st->max_it || j + 1 >= m) st->skip = 1;
+}
+
+__global__ void k_gm_backsub(GmresState* st) {
+  const int k = st->k;
+  double y[kMaxDots];
+  for (int i = k - 1; i >= 0; --i) {
+    double t = st->g[i];
+    for (int l = i + 1; l < k; ++l) t -= st->H[i * kMaxDots + l] * y[l];
+    y[i] = t / st->H[i * kMaxDots + i];
+  }
+  for (int i = 0; i < kMaxDots; ++i) st->yc[i] = i < k ? y[i] / st->alpha[i] : 0.0;
+  st->res = fabs(st->g[k]);
 }
 
 inline int grid_for(int64_t n) {
@@ -264,19 +429,22 @@ inline int grid_for(int64_t n) {
 inline bool small(int64_t n) { return n <= (int64_t)0xffffffffLL; }
 
 template <typename S, int K>
-void multidot_k(const S* w, const S* V, int64_t ldv, bool with_norm, int64_t n, double* partial, cudaStream_t s) {
-  k_multidot<S, K><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, with_norm ? 1 : 0, n, partial);
+void multidot_k(const S* w, const S* V, int64_t ldv, bool with_norm, int64_t n, double* partial, cudaStream_t s,
+                const int32_t* skip) {
+  k_multidot<S, K><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, with_norm ? 1 : 0, n, partial, skip);
 }
 
 template <typename S, int K>
-void axpy_k(S* w, const S* V, int64_t ldv, const Coef16& c, int64_t n, double* partial, cudaStream_t s) {
-  k_axpy_norm<S, K><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, c, n, partial);
+void axpy_k(S* w, const S* V, int64_t ldv, const Coef16& c, int64_t n, double* partial, cudaStream_t s,
+            const int32_t* skip, const double* cdev) {
+  k_axpy_norm<S, K><<<kRedBlocks, kRedThreads, 0, s>>>(w, V, ldv, c, n, partial, skip, cdev);
 }
 
 template <typename S, typename X, int K>
-void combine_k(X* x, const S* V, int64_t ldv, const Coef16& y, const S* inv, int64_t blk, int64_t n, cudaStream_t s) {
-  if (small(n)) k_precond_combine<S, X, K, true><<<grid_for(n), kRedThreads, 0, s>>>(x, V, ldv, y, inv, blk, n);
-  else k_precond_combine<S, X, K, false><<<grid_for(n), kRedThreads, 0, s>>>(x, V, ldv, y, inv, blk, n);
+void combine_k(X* x, const S* V, int64_t ldv, const Coef16& y, const S* inv, int64_t blk, int64_t n, cudaStream_t s,
+               const GmresState* st) {
+  if (small(n)) k_precond_combine<S, X, K, true><<<grid_for(n), kRedThreads, 0, s>>>(x, V, ldv, y, inv, blk, n, st);
+  else k_precond_combine<S, X, K, false><<<grid_for(n), kRedThreads, 0, s>>>(x, V, ldv, y, inv, blk, n, st);
 }
 
 #define STM_SWITCH_K(k, CALL)  \
@@ -303,32 +471,32 @@ void combine_k(X* x, const S* V, int64_t ldv, const Coef16& y, const S* inv, int
 
 template <typename S>
 void multidot(const S* w, const S* V, int64_t ldv, int k, bool with_norm, int64_t n, double* partial, double* out,
-              cudaStream_t s) {
-#define STM_MD(K) multidot_k<S, K>(w, V, ldv, with_norm, n, partial, s)
+              cudaStream_t s, const int32_t* skip) {
+#define STM_MD(K) multidot_k<S, K>(w, V, ldv, with_norm, n, partial, s, skip)
   STM_SWITCH_K(k, STM_MD)
 #undef STM_MD
-  k_finish<<<1, 512, 0, s>>>(partial, k + (with_norm ? 1 : 0), kRedBlocks, out);
+  if (out) k_finish<<<1, 512, 0, s>>>(partial, k + (with_norm ? 1 : 0), kRedBlocks, out);
 }
 
 template <typename S>
 void axpy_norm(S* w, const S* V, int64_t ldv, int k, const Coef16& c, int64_t n, double* partial, double* out,
-               cudaStream_t s) {
-#define STM_AX(K) axpy_k<S, K>(w, V, ldv, c, n, partial, s)
+               cudaStream_t s, const int32_t* skip, const double* cdev) {
+#define STM_AX(K) axpy_k<S, K>(w, V, ldv, c, n, partial, s, skip, cdev)
   STM_SWITCH_K(k, STM_AX)
 #undef STM_AX
-  k_finish<<<1, 32, 0, s>>>(partial, 1, kRedBlocks, out);
+  if (out) k_finish<<<1, 32, 0, s>>>(partial, 1, kRedBlocks, out);
 }
 
 template <typename S>
-void precond_apply(S* z, const S* v, const S* inv, int64_t blk, int64_t n, cudaStream_t s) {
-  if (small(n)) k_precond<S, true><<<grid_for(n), kRedThreads, 0, s>>>(z, v, inv, blk, n);
-  else k_precond<S, false><<<grid_for(n), kRedThreads, 0, s>>>(z, v, inv, blk, n);
+void precond_apply(S* z, const S* v, const S* inv, int64_t blk, int64_t n, cudaStream_t s, const int32_t* skip) {
+  if (small(n)) k_precond<S, true><<<grid_for(n), kRedThreads, 0, s>>>(z, v, inv, blk, n, skip);
+  else k_precond<S, false><<<grid_for(n), kRedThreads, 0, s>>>(z, v, inv, blk, n, skip);
 }
 
 template <typename S, typename X>
 void precond_combine(X* x, const S* V, int64_t ldv, int k, const Coef16& y, const S* inv, int64_t blk, int64_t n,
-                     cudaStream_t s) {
-#define STM_CB(K) combine_k<S, X, K>(x, V, ldv, y, inv, blk, n, s)
+                     cudaStream_t s, const GmresState* st) {
+#define STM_CB(K) combine_k<S, X, K>(x, V, ldv, y, inv, blk, n, s, st)
   STM_SWITCH_K(k, STM_CB)
 #undef STM_CB
 }
@@ -341,27 +509,54 @@ void energy_brick(const double* u, const double* mass, int64_t n3, int64_t n, do
 }
 
 template <typename D, typename S>
-void convert(D* dst, const S* src, int64_t n, cudaStream_t s) {
-  k_convert<D, S><<<grid_for(n), kRedThreads, 0, s>>>(dst, src, n);
+void convert(D* dst, const S* src, int64_t n, cudaStream_t s, const int32_t* skip) {
+  k_convert<D, S><<<grid_for(n), kRedThreads, 0, s>>>(dst, src, n, skip);
+}
+
+
+void gmres_reduce(const double* partial, GmresState* st, int slot, cudaStream_t s, const int32_t* skip) {
+  k_gm_reduce<<<1, kCtrlThreads, 0, s>>>(partial, st, slot, skip);
+}
+void gmres_slab_start(GmresState* st, double tol, int max_it, int inexact, cudaStream_t s) {
+  k_gm_slab_start<<<1, 1, 0, s>>>(st, tol, max_it, inexact);
+}
+void gmres_outer_check(GmresState* st, cudaStream_t s) { k_gm_outer_check<<<1, 1, 0, s>>>(st); }
+void gmres_cycle_init(GmresState* st, int slot_start, double floor_rel, cudaStream_t s) {
+  k_gm_cycle_init<<<1, 1, 0, s>>>(st, slot_start, floor_rel);
+}
+void gmres_gs(const double* partial, GmresState* st, int j, int second, cudaStream_t s) {
+  k_gm_gs<<<1, kCtrlThreads, 0, s>>>(partial, st, j, second);
+}
+void gmres_after(const double* partial, GmresState* st, int reorth, cudaStream_t s) {
+  k_gm_after<<<1, kCtrlThreads, 0, s>>>(partial, st, reorth);
+}
+void gmres_givens(const double* partial, GmresState* st, int j, int m, int reo_mode, cudaStream_t s) {
+  k_gm_givens<<<1, kCtrlThreads, 0, s>>>(partial, st, j, m, reo_mode);
+}
+void gmres_backsub(GmresState* st, int m, cudaStream_t s) {
+  (void)m;
+  k_gm_backsub<<<1, 1, 0, s>>>(st);
 }
 
 template void multidot<double>(const double*, const double*, int64_t, int, bool, int64_t, double*, double*,
-                               cudaStream_t);
+                               cudaStream_t, const int32_t*);
 template void multidot<float>(const float*, const float*, int64_t, int, bool, int64_t, double*, double*,
-                              cudaStream_t);
+                              cudaStream_t, const int32_t*);
 template void axpy_norm<double>(double*, const double*, int64_t, int, const Coef16&, int64_t, double*, double*,
-                                cudaStream_t);
+                                cudaStream_t, const int32_t*, const double*);
 template void axpy_norm<float>(float*, const float*, int64_t, int, const Coef16&, int64_t, double*, double*,
-                               cudaStream_t);
-template void precond_apply<double>(double*, const double*, const double*, int64_t, int64_t, cudaStream_t);
-template void precond_apply<float>(float*, const float*, const float*, int64_t, int64_t, cudaStream_t);
+                               cudaStream_t, const int32_t*, const double*);
+template void precond_apply<double>(double*, const double*, const double*, int64_t, int64_t, cudaStream_t,
+                                    const int32_t*);
+template void precond_apply<float>(float*, const float*, const float*, int64_t, int64_t, cudaStream_t,
+                                   const int32_t*);
 template void precond_combine<double, double>(double*, const double*, int64_t, int, const Coef16&, const double*,
-                                              int64_t, int64_t, cudaStream_t);
+                                              int64_t, int64_t, cudaStream_t, const GmresState*);
 template void precond_combine<float, double>(double*, const float*, int64_t, int, const Coef16&, const float*,
-                                             int64_t, int64_t, cudaStream_t);
+                                             int64_t, int64_t, cudaStream_t, const GmresState*);
 template void precond_combine<float, float>(float*, const float*, int64_t, int, const Coef16&, const float*, int64_t,
-                                            int64_t, cudaStream_t);
-template void convert<float, double>(float*, const double*, int64_t, cudaStream_t);
-template void convert<double, float>(double*, const float*, int64_t, cudaStream_t);
+                                            int64_t, cudaStream_t, const GmresState*);
+template void convert<float, double>(float*, const double*, int64_t, cudaStream_t, const int32_t*);
+template void convert<double, float>(double*, const float*, int64_t, cudaStream_t, const int32_t*);
 
 }  // namespace stm

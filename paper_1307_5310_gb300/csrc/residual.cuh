@@ -39,11 +39,17 @@
 // bilinearform:S), 2:1 faces (equivalent traces from k_hang), local
 // refinement in time (TR: N_K sub-intervals per element, temporal transfer to
 // neighbours with another partition), the dissipative term D_h of Sec. 4.2
-// (kap), and the preconditioner on load in k_fused (pinv).
+// (kap), and the block-diagonal preconditioner applied on load (pinv: the launch
+// computes A P^{-1} v).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
+#include <type_traits>
+
+#include "per_device.h"
 
 namespace stm {
 
@@ -102,11 +108,27 @@ struct ApplyArgs {
   int nk = 1;
   const uint8_t* nkl = nullptr;
   const T* tmat = nullptr;
-  // uniform brick meshes, single-pass FP32 kernel: non-null means um holds a Krylov vector v
-  // and the launch applies A P^{-1} v, with pinv[e][f][c] = 1 / (mat G_c) the inverse of the
-  // block-diagonal preconditioner P = I (x) mass (Eq. preconditioner) scaling modes >= 1 on load
+  // brick meshes: non-null means um holds a Krylov vector v and the launch applies A P^{-1} v,
+  // with pinv[e][f][c] = 1 / (mat G_c) the inverse of the block-diagonal preconditioner
+  // P = I (x) mass (Eq. preconditioner) scaling the unknown modes on load
   const T* pinv = nullptr;
+  // non-null: the launch does nothing while *skip is set (device-driven GMRES cycles)
+  const int32_t* skip = nullptr;
+  // general affine elements (uniform meshes): mass3[e][f][6] = mat_f G with the constant
+  // metric G = |J| DF^{-1} DF^{-T} in the order xx, yy, zz, xy, xz, yz; mass is then null
+  const T* mass3 = nullptr;
 };
+
+// Runs f() once per CUDA device: the first time it is called with that device current.
+template <typename F>
+void once_per_device(std::atomic<uint64_t>& done, F&& f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = -1;
+  }
+  once_for_device(done, dev, f);
+}
 
 __host__ __device__ constexpr int tmat_index(int r, int o) { return (r == 2 ? 0 : (r == 4 ? 2 : 6)) + o; }
 
@@ -144,12 +166,19 @@ __host__ __device__ constexpr bool b_nz(int i, int m) {
 // Nonzero pattern of D.
 __host__ __device__ constexpr bool d_nz(int a, int b) { return a < b && ((b - a) & 1); }
 
-// x with its sign bit xor-ed with m (m = 0 or 0x80000000): a negation on the
-// integer pipe, so the FP64 pipe only sees the products of the residual.
-__device__ __forceinline__ double flip_sign(double x, unsigned m) {
-  return __hiloint2double(__double2hiint(x) ^ (int)m, __double2loint(x));
+// Row c of a symmetric 3x3 matrix stored as (xx, yy, zz, xy, xz, yz).
+template <typename T>
+__device__ __forceinline__ void sym3_row(const T* m, int c, T r[3]) {
+  if (c == 0) { r[0] = m[0]; r[1] = m[3]; r[2] = m[4]; }
+  else if (c == 1) { r[0] = m[3]; r[1] = m[1]; r[2] = m[5]; }
+  else { r[0] = m[4]; r[1] = m[5]; r[2] = m[2]; }
 }
-__device__ __forceinline__ float flip_sign(float x, unsigned m) { return __int_as_float(__float_as_int(x) ^ (int)m); }
+
+// -x by flipping the sign bit on the integer pipe (keeps the FP64 pipe for the products).
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+__device__ __forceinline__ float neg_bits(float x) { return __int_as_float(__float_as_int(x) ^ (int)0x80000000u); }
 
 // Line of the N^3 tensor along axis a at transverse position t (the spatial
 // index with the a-coordinate removed, order preserved).
@@ -163,6 +192,7 @@ __device__ __forceinline__ void line_geom(int a, int t, int& base, int& stride) 
 // TR: the mesh has elements with N_K > 1 (HP only); false compiles the one-sub-interval code
 template <typename T, int P, int Q, bool HP, bool TR = false>
 __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
+  if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
@@ -179,6 +209,12 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
       else u[0] = A.um[ad.um + fc * ad.um_cs + (k - 1) * Q * N3 + s];
 #pragma unroll
       for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (k * Q + m - 1) * N3 + s];
+      if (A.pinv) {  // A P^{-1} v: the unknown modes scaled by the inverse block-diagonal mass on load
+        const T sc = A.pinv[ad.e * 6 + fc];
+        if (k > 0) u[0] *= sc;
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) u[m] *= sc;
+      }
       T* yg = A.y + ad.R + fc * (int64_t)(QE * N3) + k * Q * N3 + s;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -296,6 +332,31 @@ __device__ __forceinline__ int64_t test_ofs(int64_t rk, int f, int w, int QE) {
   return rk + (int64_t)(f * 3 + cc) * QE * N3 + (w - cc * Q * N3);
 }
 
+// Line passes of k_apply: pass k handles, for output component c, the derivative axis
+// a = (k == 0 ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2)).  The line's term carries the sign
+// s_F eps_{cab} (s_E = -1, s_H = +1), negative exactly when (f == 0) == ((c, a) cyclic).
+// curl_combo maps the combination index cb (NF fields x 3 components) to (field slot fl,
+// component c) with the positive lines first, and returns the sign.
+template <int NF>
+__device__ __forceinline__ void curl_combo(int k, int f0, int cb, int& fl, int& c, bool& neg) {
+  if constexpr (NF == 2) {
+    // pass 0: positive (f, c) = (0,1) (1,0) (1,2), negative (0,0) (0,2) (1,1); pass 1: the reverse
+    constexpr int ord[2][6] = {{1, 3, 5, 0, 2, 4}, {0, 2, 4, 1, 3, 5}};
+    const int fc = ord[k][cb];
+    fl = fc / 3;
+    c = fc - 3 * fl;
+    neg = cb >= 3;
+  } else {
+    // one field per pass: (f, pass) = (0,0) and (1,1) have one positive line set, c = 1;
+    // (1,0) and (0,1) have two, c = 0 and 2
+    fl = 0;
+    const bool one = (f0 == k);
+    constexpr int ord1[3] = {1, 0, 2}, ord2[3] = {0, 2, 1};
+    c = one ? ord1[cb] : ord2[cb];
+    neg = one ? cb >= 1 : cb >= 2;
+  }
+}
+
 // Shared memory per k_apply pass: y of the other field and the residual rows;
 // both fields in one pass when that fits in ~110 KB, else one field per pass.
 template <typename T, int P, int Q>
@@ -308,6 +369,7 @@ struct ApplyShape {
 
 template <typename T, int P, int Q, bool HP, bool TR = false>
 __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
+  if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   constexpr int NF = ApplyShape<T, P, Q>::NF;
   constexpr int FB = 3 * Q * N3;           // one field's block
@@ -333,44 +395,100 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
     for (int f0 = 0; f0 < 2; f0 += NF) {
       for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
         const int fl = NF == 1 ? 0 : it / FB;
-        const int f = f0 + fl, fp = 1 - f;
-        const int w = it - fl * FB;
-        ys[it] = A.y[test_ofs<Q, N3, TR>(rk, fp, w, QE)];
-        const int cc = w / (Q * N3);
-        const int r = w - cc * (Q * N3);
-        const int i = r / N3, s = r - i * N3;
-        const int fc = f * 3 + cc;
-        T v;
-        if (A.mass) {
+        ys[it] = A.y[test_ofs<Q, N3, TR>(rk, 1 - (f0 + fl), it - fl * FB, QE)];
+      }
+      // mass rows: items (field, component, s), the temporal modes unrolled; the variant
+      // (mode 0 of the sub-interval, preconditioned input, load) is chosen once per pass so
+      // no FP64 instruction is predicated
+      auto mass_rows = [&](auto prevc, auto prec, auto loadc) {
+        constexpr int PREV = decltype(prevc)::value;  // 0: none, 1: previous sub-interval, 2: u0
+        constexpr bool PRE = decltype(prec)::value, LOAD = decltype(loadc)::value;
+        for (int it = threadIdx.x; it < NF * 3 * N3; it += blockDim.x) {
+          const int fcl = it / N3, s = it - fcl * N3;
+          const int fl = NF == 1 ? 0 : fcl / 3, cc = fcl - 3 * fl;
+          const int fc = (f0 + fl) * 3 + cc;
           const T mc = A.mass[e * 6 + fc];
-          v = mc * A.um[ad.um + fc * ad.um_cs + (sk * Q + i) * N3 + s];
-          if (i == 0) {
-            // minus mode 0 of the sub-interval: the slab start or the previous sub-interval's end
-            if (sk > 0) v = fma(-mc, A.um[ad.um + fc * ad.um_cs + (sk - 1) * Q * N3 + s], v);
-            else if (A.u0) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
+          const T* uc = A.um + ad.um + fc * ad.um_cs + (int64_t)sk * Q * N3 + s;
+          T* Rr = Rs + fl * FB + cc * Q * N3 + s;
+          // with PRE (A P^{-1} v) the mass block times P^{-1} is the identity: the term is v
+          {  // mode 0: minus mode 0 of the sub-interval (previous sub-interval's end or slab start)
+            T v = PRE ? uc[0] : mc * uc[0];
+            if constexpr (PREV == 1) v = PRE ? v - uc[-Q * N3] : fma(-mc, uc[-Q * N3], v);
+            if constexpr (PREV == 2) v = fma(-mc, A.u0[ad.u0 + fc * ad.u0_cs + s], v);
+            if constexpr (LOAD) v -= A.b[test_ofs<Q, N3, TR>(rk, f0 + fl, cc * Q * N3 + s, QE)];
+            Rr[0] = v;
           }
-        } else {
-          v = A.R[test_ofs<Q, N3, TR>(rk, f, w, QE)];
+#pragma unroll 1
+          for (int i = 1; i < Q; ++i) {
+            T v = PRE ? uc[i * N3] : mc * uc[i * N3];
+            if constexpr (LOAD) v -= A.b[test_ofs<Q, N3, TR>(rk, f0 + fl, (cc * Q + i) * N3 + s, QE)];
+            Rr[i * N3] = v;
+          }
         }
-        if (A.b) v -= A.b[test_ofs<Q, N3, TR>(rk, f, w, QE)];
-        Rs[it] = v;
+      };
+      if (A.mass) {
+        const int prev = sk > 0 ? 1 : (A.u0 ? 2 : 0);
+        const bool pre = A.pinv != nullptr, load = A.b != nullptr;
+        using I0 = std::integral_constant<int, 0>;
+        using I1 = std::integral_constant<int, 1>;
+        using I2 = std::integral_constant<int, 2>;
+        auto with_prev = [&](auto pc, auto prc) {
+          if (load) mass_rows(pc, prc, std::true_type{});
+          else mass_rows(pc, prc, std::false_type{});
+        };
+        auto with_pre = [&](auto prc) {
+          if (prev == 1) with_prev(I1{}, prc);
+          else if (prev == 2) with_prev(I2{}, prc);
+          else with_prev(I0{}, prc);
+        };
+        if (pre) with_pre(std::true_type{});
+        else with_pre(std::false_type{});
+      } else if (A.mass3) {
+        // general affine elements: the constant 3x3 metric couples the components
+        for (int it = threadIdx.x; it < NF * 3 * N3; it += blockDim.x) {
+          const int fcl = it / N3, s = it - fcl * N3;
+          const int fl = NF == 1 ? 0 : fcl / 3, cc = fcl - 3 * fl, f = f0 + fl;
+          T mr[3];
+          sym3_row(A.mass3 + (e * 2 + f) * 6, cc, mr);
+          const T* uf = A.um + ad.um + (int64_t)(f * 3) * ad.um_cs + s;
+          T* Rr = Rs + fl * FB + cc * Q * N3 + s;
+#pragma unroll 1
+          for (int i = 0; i < Q; ++i) {
+            T v = mr[0] * uf[i * N3];
+            v = fma(mr[1], uf[ad.um_cs + i * N3], v);
+            v = fma(mr[2], uf[2 * ad.um_cs + i * N3], v);
+            if (i == 0 && A.u0) {
+              const T* u0f = A.u0 + ad.u0 + (int64_t)(f * 3) * ad.u0_cs + s;
+              v = fma(-mr[0], u0f[0], v);
+              v = fma(-mr[1], u0f[ad.u0_cs], v);
+              v = fma(-mr[2], u0f[2 * ad.u0_cs], v);
+            }
+            if (A.b) v -= A.b[test_ofs<Q, N3, TR>(rk, f, (cc * Q + i) * N3 + s, QE)];
+            Rr[i * N3] = v;
+          }
+        }
+      } else {
+        // curved elements: R already holds the mass term (k_mass_curved)
+        for (int it = threadIdx.x; it < NF * FB; it += blockDim.x) {
+          const int fl = NF == 1 ? 0 : it / FB;
+          const int w = it - fl * FB;
+          const int64_t o = test_ofs<Q, N3, TR>(rk, f0 + fl, w, QE);
+          Rs[it] = A.b ? A.R[o] - A.b[o] : A.R[o];
+        }
       }
       __syncthreads();
 #pragma unroll 1
       for (int k = 0; k < 2; ++k) {
         for (int it = threadIdx.x; it < NF * 3 * Q * N2; it += blockDim.x) {
-          int r = it;
-          const int t = r % N2; r /= N2;
-          const int i = r % Q; r /= Q;
-          const int c = r % 3;
-          const int fl = r / 3;
+          // lines ordered by the sign of their curl term, so that a warp rarely holds both
+          const int cb = it / (Q * N2), r = it - cb * (Q * N2);
+          const int i = r / N2, t = r - i * N2;
+          int fl, c;
+          bool neg;
+          curl_combo<NF>(k, f0, cb, fl, c, neg);
           const int f = f0 + fl, fp = 1 - f;
           const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
           const int b = 3 - c - a;
-          // eps_{c a b}: +1 for cyclic (c, a, b); the sign s_F eps_{cab} is applied by
-          // flipping sign bits of the inputs (integer pipe), not by multiplies
-          const bool cyc = ((a - c + 3) % 3 == 1);
-          const unsigned flip = ((f == 0) == cyc) ? 0x80000000u : 0u;
           const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
           int base, stride;
           line_geom<N>(a, t, base, stride);
@@ -381,61 +499,73 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           const T xm = tre[so * N2 + t];
           const T xp = tre[(so + 2 * QE) * N2 + t];
           const int ep = nb[2 * a + 1], em = nb[2 * a];
-          T jp, jm;
-          if (ep >= 0) jp = xp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, fp, a, bi, i, t, sk, fcs, 2 * a + 1);
-          else if (HP && ep == -2) jp = xp - A.hbuf[fcs.off[2 * a + 1] + ((fp * 2 + bi) * Q + i) * N2 + t];
-          else jp = (fp == 0) ? xp + xp : T(0);
-          if (em >= 0) jm = xm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, fp, a, bi, i, t, sk, fcs, 2 * a);
-          else if (HP && em == -2) jm = xm - A.hbuf[fcs.off[2 * a] + ((fp * 2 + bi) * Q + i) * N2 + t];
-          else jm = (fp == 0) ? xm + xm : T(0);
-          const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
+          // the other side's trace: the neighbour's, or on a PEC face the mirror value (E: -own,
+          // so the jump is 2 own; H: +own, jump 0) chosen by integer ops; one subtraction each
+          T op, om;
+          if (ep >= 0) op = nbr_trace<T, N, Q, HP, TR>(A, ep, 0, fp, a, bi, i, t, sk, fcs, 2 * a + 1);
+          else if (HP && ep == -2) op = A.hbuf[fcs.off[2 * a + 1] + ((fp * 2 + bi) * Q + i) * N2 + t];
+          else op = (fp == 0) ? neg_bits(xp) : xp;
+          if (em >= 0) om = nbr_trace<T, N, Q, HP, TR>(A, em, 1, fp, a, bi, i, t, sk, fcs, 2 * a);
+          else if (HP && em == -2) om = A.hbuf[fcs.off[2 * a] + ((fp * 2 + bi) * Q + i) * N2 + t];
+          else om = (fp == 0) ? neg_bits(xm) : xm;
+          const T jp = xp - op, jm = xm - om;
+          const T sp = jp + jm, dm = jp - jm;
           T yv[N];
 #pragma unroll
-          for (int j = 0; j < N; ++j) yv[j] = flip_sign(yl[j * stride], flip);
+          for (int j = 0; j < N; ++j) yv[j] = yl[j * stride];
           T* Rl = Rs + fl * FB + (c * Q + i) * N3 + base;
-          if (A.kap) {
-            // D_h: alpha-weighted jumps of component c of the same field f on the two
-            // faces normal to a, lifted with L_al(1) and L_al(0) = (-1)^al L_al(1);
-            // on a PEC face the E jump is the own trace (E - g, g in the load)
-            const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
-            const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * QE + sk * Q + i;
-            const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * QE) * N2 + t];
-            const T gp = (ep >= 0) ? zp - nbr_trace<T, N, Q, HP, TR>(A, ep, 0, f, a, bc, i, t, sk, fcs, 2 * a + 1)
-                                   : (f == 0 ? zp : T(0));
-            const T gm = (em >= 0) ? zm - nbr_trace<T, N, Q, HP, TR>(A, em, 1, f, a, bc, i, t, sk, fcs, 2 * a)
-                                   : (f == 0 ? zm : T(0));
-            const T* kp = A.kap + e * 24 + f * 12 + 4 * a + bc;
-            const T dp = A.dt_k * kp[2] * gp, dn = A.dt_k * kp[0] * gm;
-            // the central-flux lift hf[al] = (dt/2) lv[al] shares the factor lv[al]
-            const T zev = fma(-A.tb.hf[0], dm, dp + dn), zod = fma(-A.tb.hf[0], sp, dp - dn);
+          // the sign s_F eps_{cab} of the line's curl and flux terms is a compile-time constant
+          // of each branch, carried by the table operands of the FMAs (no extra instruction)
+          auto body = [&](auto negc) {
+            constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
+            if (A.kap) {
+              // D_h: alpha-weighted jumps of component c of the same field f on the two
+              // faces normal to a, lifted with L_al(1) and L_al(0) = (-1)^al L_al(1);
+              // on a PEC face the E jump is the own trace (E - g, g in the load)
+              const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
+              const int64_t sc = ((((int64_t)f * 3 + a) * 2) * 2 + bc) * QE + sk * Q + i;
+              const T zm = tre[sc * N2 + t], zp = tre[(sc + 2 * QE) * N2 + t];
+              // other side: the neighbour's trace; on a PEC face 0 for E (jump = own) and own for H
+              const T gop = (ep >= 0) ? nbr_trace<T, N, Q, HP, TR>(A, ep, 0, f, a, bc, i, t, sk, fcs, 2 * a + 1)
+                                      : (f == 0 ? T(0) : zp);
+              const T gom = (em >= 0) ? nbr_trace<T, N, Q, HP, TR>(A, em, 1, f, a, bc, i, t, sk, fcs, 2 * a)
+                                      : (f == 0 ? T(0) : zm);
+              const T gp = zp - gop, gm = zm - gom;
+              const T* kp = A.kap + e * 24 + f * 12 + 4 * a + bc;
+              const T dp = A.dt_k * kp[2] * gp, dn = A.dt_k * kp[0] * gm;
+              // the central-flux lift hf[al] = (dt/2) lv[al] shares the factor lv[al]
+              const T zev = fma(-sg * A.tb.hf[0], dm, dp + dn), zod = fma(-sg * A.tb.hf[0], sp, dp - dn);
 #pragma unroll
-            for (int al = 0; al < N; ++al) {
-              T r2 = Rl[al * stride];
-              r2 = fma(A.tb.lv[al], (al & 1) ? zod : zev, r2);
+              for (int al = 0; al < N; ++al) {
+                T r2 = Rl[al * stride];
+                r2 = fma(A.tb.lv[al], (al & 1) ? zod : zev, r2);
 #pragma unroll
-              for (int be = 0; be < N; ++be)
-                if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
-              Rl[al * stride] = r2;
+                for (int be = 0; be < N; ++be)
+                  if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+                Rl[al * stride] = r2;
+              }
+            } else {
+              // Dt[a][b] = 2 dt L_a(1) L_b(1) and hf[a] = dt/2 L_a(1) share the factor L_a(1), so
+              // the lift -hf[a] X of every row a but the last equals Dt[a][B] X kq[B] with B the
+              // largest index of the other parity (which every such row's curl sum reaches):
+              // folded into y[B] once per line instead of one FMA per row
+              constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2;  // largest odd index: even rows, X = dm
+              constexpr int B1 = ((N - 1) & 1) ? N - 2 : N - 1;  // largest even index: odd rows, X = sp
+              if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+              if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+#pragma unroll
+              for (int al = 0; al < N; ++al) {
+                T r2 = Rl[al * stride];
+                if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+                for (int be = 0; be < N; ++be)
+                  if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+                Rl[al * stride] = r2;
+              }
             }
-          } else {
-            // Dt[a][b] = 2 dt L_a(1) L_b(1) and hf[a] = dt/2 L_a(1) share the factor L_a(1), so
-            // the lift -hf[a] X of every row a but the last equals Dt[a][B] X kq[B] with B the
-            // largest index of the other parity (which every such row's curl sum reaches):
-            // folded into y[B] once per line instead of one FMA per row
-            constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2;  // largest odd index: even rows, X = dm
-            constexpr int B1 = ((N - 1) & 1) ? N - 2 : N - 1;  // largest even index: odd rows, X = sp
-            if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
-            if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
-#pragma unroll
-            for (int al = 0; al < N; ++al) {
-              T r2 = Rl[al * stride];
-              if (al == N - 1) r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
-#pragma unroll
-              for (int be = 0; be < N; ++be)
-                if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
-              Rl[al * stride] = r2;
-            }
-          }
+          };
+          if (neg) body(std::true_type{});
+          else body(std::false_type{});
         }
         __syncthreads();
       }
@@ -455,22 +585,34 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
 // coefficients (face neighbours sit close in memory, so these reads mostly hit
 // L2), forms its own traces in registers inside the line loop, and writes R.
 // No y or trace scratch goes through HBM.
+//
+// Work split: (a) all threads form y = B u and the mass rows of the element in
+// shared memory, (b) all threads form the neighbour traces, then (c) every warp
+// owns whole residual planes (field, component, test mode): it runs both line
+// passes of a plane (one per derivative axis) with only warp synchronisation
+// and stores the finished plane to HBM.  Two CTA barriers per element.
 template <typename T, int P, int Q, bool PRE>
 __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
+  if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
-  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3]
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3] temporal contraction
+  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3] residual planes
   T* nt = Rs + 6 * Q * N3;                  // [6 faces][2 fields][2 comps][Q][N2] neighbour traces
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int um_cs = (int)A.um_cs, u0_cs = (int)A.u0_cs;
   for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
     const int32_t* nb = A.nbr + e * 6;
+    const T* ume = A.um + e * A.um_es;
+    const T* u0e = A.u0 ? A.u0 + e * A.u0_es : nullptr;
+    const int64_t re = e * (int64_t)(6 * Q * N3);
     // (a) own coefficients: temporal contraction and the mass term
     for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
       const int fc = it / N3, s = it - fc * N3;
-      T u[Q + 1];
-      u[0] = A.u0 ? A.u0[e * A.u0_es + fc * A.u0_cs + s] : T(0);
+      T u[Q + 1], v[Q];
+      u[0] = u0e ? u0e[fc * u0_cs + s] : T(0);
 #pragma unroll
-      for (int m = 1; m <= Q; ++m) u[m] = A.um[e * A.um_es + fc * A.um_cs + (m - 1) * N3 + s];
+      for (int m = 1; m <= Q; ++m) u[m] = v[m - 1] = ume[fc * um_cs + (m - 1) * N3 + s];
       if constexpr (PRE) {
         const T sc = A.pinv[e * 6 + fc];
 #pragma unroll
@@ -488,47 +630,74 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
             first = false;
           }
         }
-        ys[(fc * Q + i) * N3 + s] = acc;
-        T v;
+        const int o = (fc * Q + i) * N3 + s;
+        ys[o] = acc;
+        T w;
         if (A.mass) {
-          v = mc * u[i + 1];
-          if (i == 0) v = fma(-mc, u[0], v);
+          // with PRE the mass block times P^{-1} is the identity: the term is v itself
+          w = PRE ? v[i] : mc * u[i + 1];
+          if (i == 0 && u0e) w = fma(-mc, u[0], w);
+        } else if (A.mass3) {
+          // general affine elements: the constant 3x3 metric couples the components
+          const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f;
+          T mr[3];
+          sym3_row(A.mass3 + (e * 2 + f) * 6, c, mr);
+          const T* uf = ume + (f * 3) * um_cs + i * N3 + s;
+          w = mr[0] * uf[0];
+          w = fma(mr[1], uf[um_cs], w);
+          w = fma(mr[2], uf[2 * um_cs], w);
+          if (i == 0 && u0e) {
+            const T* u0f = u0e + (f * 3) * u0_cs + s;
+            w = fma(-mr[0], u0f[0], w);
+            w = fma(-mr[1], u0f[u0_cs], w);
+            w = fma(-mr[2], u0f[2 * u0_cs], w);
+          }
         } else {
-          v = A.R[e * (int64_t)(6 * Q * N3) + (fc * Q + i) * N3 + s];
+          w = A.R[re + o];  // curved elements: the mass term is already in R
         }
-        if (A.b) v -= A.b[e * (int64_t)(6 * Q * N3) + (fc * Q + i) * N3 + s];
-        Rs[(fc * Q + i) * N3 + s] = v;
+        if (A.b) w -= A.b[re + o];
+        Rs[o] = w;
       }
     }
     // (b) neighbour traces on the shared faces: items (face, field, comp, t)
     for (int it = threadIdx.x; it < 24 * N2; it += blockDim.x) {
-      int r = it;
-      const int t = r % N2; r /= N2;
-      const int bi = r % 2; r /= 2;
-      const int fld = r % 2;
-      const int face = r / 2;
+      const int t = it % N2, r = it / N2;
+      const int bi = r & 1, fld = (r >> 1) & 1, face = r >> 2;
       const int a = face >> 1, side = face & 1;
       const int64_t en = nb[face];
       if (en < 0) continue;
       const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
       int base, stride;
       line_geom<N>(a, t, base, stride);
-      // the neighbour across face (a, side) meets it with its face (a, 1 - side)
+      // the neighbour across face (a, side) meets it with its face (a, 1 - side):
+      // L_j(0) = (-1)^j L_j(1) for side 1, L_j(1) for side 0
+      const T* un = A.um + en * A.um_es + (fld * 3 + b) * um_cs + base;
       T tu[Q + 1];
+      tu[0] = T(0);
+      if (A.u0) {
+        const T* u0n = A.u0 + en * A.u0_es + (fld * 3 + b) * u0_cs + base;
+        T ev = T(0), od = T(0);
 #pragma unroll
-      for (int m = 0; m <= Q; ++m) {
-        const T* ul = (m == 0) ? (A.u0 ? A.u0 + en * A.u0_es + (fld * 3 + b) * A.u0_cs : nullptr)
-                               : A.um + en * A.um_es + (fld * 3 + b) * A.um_cs + (m - 1) * N3;
-        T acc = T(0);
-        if (ul) {
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const T lj = (side == 1 && (j & 1)) ? -A.tb.lv[j] : A.tb.lv[j];  // L_j(0) for side 1, L_j(1) for side 0
-            acc = fma(lj, ul[base + j * stride], acc);
-          }
+        for (int j = 0; j < N; ++j) {
+          if (j & 1) od = fma(A.tb.lv[j], u0n[j * stride], od);
+          else ev = fma(A.tb.lv[j], u0n[j * stride], ev);
         }
-        if constexpr (PRE) tu[m] = m > 0 ? acc * A.pinv[en * 6 + fld * 3 + b] : acc;
-        else tu[m] = acc;
+        tu[0] = side ? ev - od : ev + od;
+      }
+#pragma unroll
+      for (int m = 1; m <= Q; ++m) {
+        T ev = T(0), od = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          if (j & 1) od = fma(A.tb.lv[j], un[(m - 1) * N3 + j * stride], od);
+          else ev = fma(A.tb.lv[j], un[(m - 1) * N3 + j * stride], ev);
+        }
+        tu[m] = side ? ev - od : ev + od;
+      }
+      if constexpr (PRE) {
+        const T sc = A.pinv[en * 6 + fld * 3 + b];
+#pragma unroll
+        for (int m = 1; m <= Q; ++m) tu[m] *= sc;
       }
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -536,64 +705,66 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
 #pragma unroll
         for (int m = 0; m <= Q; ++m)
           if (b_nz(i, m)) acc = fma(A.tb.B[i][m], tu[m], acc);
-        nt[(((face * 2 + fld) * 2 + bi) * Q + i) * N2 + t] = acc;
+        nt[(r * Q + i) * N2 + t] = acc;
       }
     }
     __syncthreads();
-#pragma unroll 1
-    for (int k = 0; k < 2; ++k) {
-      for (int it = threadIdx.x; it < 6 * Q * N2; it += blockDim.x) {
-        int r = it;
-        const int t = r % N2; r /= N2;
-        const int i = r % Q; r /= Q;
-        const int c = r % 3;
-        const int f = r / 3;
+    // (c) residual planes (f, c, i), one warp each at a time
+    for (int pl = warp; pl < 6 * Q; pl += nwarp) {
+      const int fc = pl / Q, i = pl - fc * Q;
+      const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f, fp = 1 - f;
+      T* Rp = Rs + pl * N3;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
         const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
         const int b = 3 - c - a;
-        const bool cyc = ((a - c + 3) % 3 == 1);
-        const unsigned flip = ((f == 0) == cyc) ? 0x80000000u : 0u;
-        const int fp = 1 - f;
         const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
-        int base, stride;
-        line_geom<N>(a, t, base, stride);
-        const T* yl = ys + ((fp * 3 + b) * Q + i) * N3 + base;
-        T yv[N];
-        T ev = T(0), od = T(0);
+        // sign s_F eps_{cab} of the plane's terms along a (warp-uniform)
+        const bool neg = ((f == 0) == (((a - c + 3) % 3) == 1));
+        const T* yb = ys + ((fp * 3 + b) * Q + i) * N3;
+        const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
+        const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q + i) * N2;
+        const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q + i) * N2;
+        for (int t = lane; t < N2; t += 32) {
+          int base, stride;
+          line_geom<N>(a, t, base, stride);
+          T yv[N];
+          T ev = T(0), od = T(0);
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          yv[j] = yl[j * stride];
-          if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
-          else ev = fma(A.tb.lv[j], yv[j], ev);
+          for (int j = 0; j < N; ++j) {
+            yv[j] = yb[base + j * stride];
+            if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
+            else ev = fma(A.tb.lv[j], yv[j], ev);
+          }
+          const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
+          const T jp = hasp ? xp - ntp[t] : ((fp == 0) ? xp + xp : T(0));
+          const T jm = hasm ? xm - ntm[t] : ((fp == 0) ? xm + xm : T(0));
+          const T sp = jp + jm, dm = jp - jm;
+          T* Rl = Rp + base;
+          auto body = [&](auto negc) {
+            constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
+            // flux lift folded into the curl operand as in k_apply
+            constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
+            if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+            if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+#pragma unroll
+            for (int al = 0; al < N; ++al) {
+              T r2 = Rl[al * stride];
+              if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+              for (int be = 0; be < N; ++be)
+                if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+              Rl[al * stride] = r2;
+            }
+          };
+          if (neg) body(std::true_type{});
+          else body(std::false_type{});
         }
-        const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
-        const int ep = nb[2 * a + 1], em = nb[2 * a];
-        T jp, jm;
-        if (ep >= 0) jp = xp - nt[((((2 * a + 1) * 2 + fp) * 2 + bi) * Q + i) * N2 + t];
-        else jp = (fp == 0) ? xp + xp : T(0);
-        if (em >= 0) jm = xm - nt[((((2 * a) * 2 + fp) * 2 + bi) * Q + i) * N2 + t];
-        else jm = (fp == 0) ? xm + xm : T(0);
-        const T sp = flip_sign(jp + jm, flip), dm = flip_sign(jp - jm, flip);
-#pragma unroll
-        for (int j = 0; j < N; ++j) yv[j] = flip_sign(yv[j], flip);
-        T* Rl = Rs + ((f * 3 + c) * Q + i) * N3 + base;
-        // flux lift folded into the curl operand as in k_apply
-        constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
-        if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
-        if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
-#pragma unroll
-        for (int al = 0; al < N; ++al) {
-          T r2 = Rl[al * stride];
-          if (al == N - 1) r2 = fma(-A.tb.hf[al], (al & 1) ? sp : dm, r2);
-#pragma unroll
-          for (int be = 0; be < N; ++be)
-            if (d_nz(al, be)) r2 = fma(A.tb.Dt[al][be], yv[be], r2);
-          Rl[al * stride] = r2;
-        }
+        __syncwarp();
       }
-      __syncthreads();
+      T* Rg = A.R + re + pl * N3;
+      for (int s2 = lane; s2 < N3; s2 += 32) Rg[s2] = Rp[s2];
     }
-    T* Rg = A.R + e * (int64_t)(6 * Q * N3);
-    for (int it = threadIdx.x; it < 6 * Q * N3; it += blockDim.x) Rg[it] = Rs[it];
     __syncthreads();
   }
 }
@@ -612,8 +783,9 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   const size_t sm_prep = sizeof(T) * 6 * Q * N3;
   const size_t sm_apply = ApplyShape<T, P, Q>::smem;
   const size_t sm_fused = 2 * sm_prep + sizeof(T) * 24 * Q * N2;
-  // thread-safe one-time set-up (function-local static initialisation)
-  static const bool configured = [&] {
+  // kernel attributes are per device: set them once on every device this instantiation launches on
+  static std::atomic<uint64_t> configured_devices{0};
+  once_per_device(configured_devices, [&] {
     if (sm_prep > 48 * 1024) {
       cudaFuncSetAttribute(k_prep<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
       cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
@@ -630,9 +802,7 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
         cudaFuncSetAttribute(k_fused<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
       }
     }
-    return true;
-  }();
-  (void)configured;
+  });
   const bool hp = args.elist != nullptr;
   if constexpr (sizeof(T) == 4) {
     if (!hp && !args.kap) {

@@ -150,6 +150,7 @@ using namespace stm;
 
 struct stm_ctx {
   int device = 0;
+  int sms = 1;  // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int64_t ne = 0;
@@ -159,6 +160,7 @@ struct stm_ctx {
   stm_opts opts{};
   std::string err;
   std::vector<double> h_x0, h_h, h_mass;  // [ne][3], [ne][3], [ne][6]
+  std::vector<double> h_mass3;             // general affine: [ne][2][6]
   std::vector<double> h_eps, h_mu;         // [ne]
   // dissipative term D_h (Sec. 4.2): per element [field][face][tangential comp] coefficients
   double* kap64 = nullptr;
@@ -234,12 +236,12 @@ struct stm_ctx {
   int block = 256;
   cudaStream_t cap_stream = nullptr;
   struct GraphKey {
-    int prec, um_layout, u0_layout;
+    int prec, um_layout, u0_layout, pre;
     const void *um, *u0, *b, *R;
     double dt;
     bool operator<(const GraphKey& o) const {
-      return std::tie(prec, um_layout, u0_layout, um, u0, b, R, dt) <
-             std::tie(o.prec, o.um_layout, o.u0_layout, o.um, o.u0, o.b, o.R, o.dt);
+      return std::tie(prec, um_layout, u0_layout, pre, um, u0, b, R, dt) <
+             std::tie(o.prec, o.um_layout, o.u0_layout, o.pre, o.um, o.u0, o.b, o.R, o.dt);
     }
   };
   std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -250,6 +252,8 @@ struct stm_ctx {
   float* Gw32 = nullptr;
   double* Pinv64 = nullptr;  // [ne][2][9]
   float* Pinv32 = nullptr;
+  double* mass3_64 = nullptr;  // general affine elements: [ne][2][6] mat * G (constant metric)
+  float* mass3_32 = nullptr;
   double* el = nullptr;      // per-element energies (curved)
   CurvedTables ct{};
   // load vector L (Gaussian currents, boundary data g), cached per (t0, dt)
@@ -262,6 +266,16 @@ struct stm_ctx {
   float* load32 = nullptr;
   bool load_valid = false;
   double load_t0 = 0.0, load_dt = 0.0;
+  // device-side GMRES control (Sec. 5.4): state in device memory, a pinned copy for the
+  // one host read per restart cycle, and CUDA graphs of whole cycles keyed by
+  // (precision, dt, load pointer)
+  GmresState* gst = nullptr;
+  GmresState* h_gst = nullptr;
+  struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+  };
+  std::map<std::tuple<int, double, const void*>, CycleGraph> cycle_graphs;
   // instrumentation: kernel launch count, optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -269,6 +283,9 @@ struct stm_ctx {
   size_t ev_used = 0;
   struct Timed { cudaEvent_t a, b, c; int prec; };
   std::vector<Timed> timed;
+  // while profiling: index into `timed` at the start of each GMRES iteration of the current
+  // cycle (the entries of iterations the device skipped are dropped after the cycle)
+  std::vector<size_t> it_marks;
 };
 
 #define STM_CK(call)                                                                              \
@@ -396,9 +413,15 @@ const T* kap_ptr(stm_ctx* c) {
   else return c->kap32;
 }
 
+// Grid of the residual kernels (grid-stride loops over elements): at most 16 CTAs per SM,
+// so a launch that the device-side GMRES control skips costs a single wave.
+int res_grid(const stm_ctx* c, int64_t count) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(count, 16LL * c->sms));
+}
+
 template <typename T>
 int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R,
-          bool pre = false) {
+          bool pre = false, const int32_t* skip = nullptr) {
   T *y = nullptr, *tr = nullptr;
   if (sizeof(T) == 8 || c->hp || c->kap64) {  // the uniform FP32 kernel is single-pass and needs no scratch
     int rc = scratch<T>(c, &y, &tr);
@@ -413,8 +436,8 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   a.mass = mass_ptr<T>(c);
   a.kap = kap_ptr<T>(c);
   a.dt_k = (T)dt;
-  // the fused preconditioner exists in the single-pass FP32 kernel only (callers check)
   a.pinv = pre ? pinv_ptr<T>(c) : nullptr;
+  a.skip = skip;
   const int N3 = c->N3, Q = c->Q;
   if (c->hp) {
     a.um = um;
@@ -428,8 +451,11 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
     a.pq = c->pq;
     a.nkl = c->nkl;
     a.tmat = tmat_ptr<T>(c);
-    const bool use_graph = c->opts.graph && !c->profiling;
-    typename stm_ctx::GraphKey key{sizeof(T) == 8 ? 0 : 1, um_layout, u0_layout, um, u0, b, R, dt};
+    // no graph of its own inside a capture of a whole GMRES cycle (captures do not nest)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    STM_CK(cudaStreamIsCapturing(c->stream, &cap));
+    const bool use_graph = c->opts.graph && !c->profiling && cap == cudaStreamCaptureStatusNone && !skip;
+    typename stm_ctx::GraphKey key{sizeof(T) == 8 ? 0 : 1, um_layout, u0_layout, pre ? 1 : 0, um, u0, b, R, dt};
     if (use_graph) {
       auto it = c->graphs.find(key);
       if (it != c->graphs.end()) {
@@ -463,6 +489,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         h.quad = c->s_quad;
         h.hoff = c->hoff;
         h.hbuf = const_cast<T*>(hbuf_ptr<T>(c));
+        h.skip = skip;
         for (int u = 0; u < 2; ++u)
           for (int j = 0; j < 8; ++j)
             for (int nn = 0; nn < 8; ++nn) h.Tm[u][j][nn] = (T)c->Tm[u][j][nn];
@@ -479,7 +506,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         if (phase == 1 && k == 0) e2.start = ev.start;
         if (phase == 1 && k + 1 == c->classes.size()) e2.mid = ev.mid;
         if (phase == 2 && k + 1 == c->classes.size()) e2.stop = ev.stop;
-        const int grid = (int)std::min<int64_t>(cl.count, 1 << 30);
+        const int grid = res_grid(c, cl.count);
         const int e = launch_residual_ph<T>(cl.P, cl.Q, a, ls, grid, e2, phase, cl.block);
         c->launches += 1;
         if (e) {
@@ -515,18 +542,23 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   a.u0 = u0;
   a.u0_es = u0_layout == L_STATE ? 6LL * N3 : 6LL * (Q + 1) * N3;
   a.u0_cs = u0_layout == L_STATE ? (int64_t)N3 : (int64_t)(Q + 1) * N3;
+  if (c->geometry == STM_GEOM_AFFINE) {
+    a.mass = nullptr;  // the constant 3x3 metric mass, inside the residual kernels
+    if constexpr (sizeof(T) == 8) a.mass3 = c->mass3_64;
+    else a.mass3 = c->mass3_32;
+  }
   if (c->geometry == STM_GEOM_TRILINEAR) {
     // curved: the metric-dependent mass term goes first into R; the residual kernels add the rest
     const int em = launch_mass_curved<T>(c->P, c->Q, a.um, a.um_es, a.um_cs, a.u0, a.u0_es, a.u0_cs,
                                          curved_ptr<T>(c, 0), curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne,
-                                         R, c->stream);
+                                         R, c->stream, skip);
     c->launches += 1;
     if (em) return fail(c, STM_EDEVICE, std::string("curved mass launch: ") + cudaGetErrorString((cudaError_t)em));
     a.mass = nullptr;
   }
   a.n_elem = c->ne;
   a.tb = make_tables<T>(c->P, c->Q, dt);
-  const int grid = (int)std::min<int64_t>(c->ne, 1 << 30);
+  const int grid = res_grid(c, c->ne);
   LaunchEvents ev;
   int rc = record_events<T>(c, ev);
   if (rc) return rc;
@@ -538,15 +570,15 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
 
 // Linear operator on the unknowns (Krylov layout, modes 1..q), no u0, no load.
 template <typename T>
-int linop(stm_ctx* c, double dt, const T* xin, T* out) {
-  return apply<T>(c, dt, xin, L_TEST, nullptr, L_STATE, nullptr, out);
+int linop(stm_ctx* c, double dt, const T* xin, T* out, const int32_t* skip = nullptr) {
+  return apply<T>(c, dt, xin, L_TEST, nullptr, L_STATE, nullptr, out, false, skip);
 }
 
 // A P^{-1} v in one residual launch (uniform brick meshes): the kernels scale v by the
 // inverse block-diagonal mass on load instead of a separate preconditioner pass
 template <typename T>
-int linop_pre(stm_ctx* c, double dt, const T* v, T* out) {
-  return apply<T>(c, dt, v, L_TEST, nullptr, L_STATE, nullptr, out, true);
+int linop_pre(stm_ctx* c, double dt, const T* v, T* out, const int32_t* skip = nullptr) {
+  return apply<T>(c, dt, v, L_TEST, nullptr, L_STATE, nullptr, out, true, skip);
 }
 
 // R(U) = A U - b with mode 0 = state (FP64), modes 1..q = xin and the load b (or none).
@@ -1048,102 +1080,62 @@ const float* sw_ptr<float>(stm_ctx* c) { return c->sw32; }
 
 // v <- S v (per-block weights), in place
 template <typename S>
-void scale_blocks(stm_ctx* c, S* v, const S* w, int64_t n) {
-  if (c->hp) precond_hp<S>(v, v, w, c->off_test, c->pq, c->ne, c->stream);
-  else precond_apply<S>(v, v, w, (int64_t)c->Q * c->N3, n, c->stream);
+void scale_blocks(stm_ctx* c, S* v, const S* w, int64_t n, const int32_t* skip = nullptr) {
+  if (c->hp) precond_hp<S>(v, v, w, c->off_test, c->pq, c->ne, c->stream, skip);
+  else precond_apply<S>(v, v, w, (int64_t)c->Q * c->N3, n, c->stream, skip);
   c->launches += 1;
 }
 
+// The m iterations of one restart cycle of right-preconditioned GMRES (Sec. 5.4) on the
+// unknowns, launched without any host synchronisation: the Gram-Schmidt coefficients,
+// the Hessenberg column, the Givens rotations and the stop test live in the device
+// state c->gst, and every kernel of an iteration is skipped once the cycle has stopped.
+// The basis is kept unnormalised: v_i = V_i / alpha_i (alpha_i signed), V[0] holds the
+// start vector (set up by gmres_cycle_init).  Classical Gram-Schmidt (one fused dot pass,
+// one fused update + norm pass), with an optional second pass when the norm drops below
+// 1/sqrt(2) of its value before the update.  At the end st->yc holds the coefficients
+// such that the correction is P^{-1} sum_{i<k} yc[i] V[i].
 template <typename S>
-int gmres_cycle(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n, double a0, double tol_abs, int max_iters,
-                int* k_out, Coef16* yc, double* res, int* iters) {
+int gmres_iterations(stm_ctx* c, double dt, S* V, int64_t ldv, S* z, int64_t n) {
   const int m = c->opts.restart;
   const int64_t qn3 = (int64_t)c->Q * c->N3;
-  std::vector<double> H((m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), alpha(m + 1), yv(m);
-  alpha[0] = a0;
-  g[0] = std::fabs(a0);
-  int k = 0, rc;
-  for (int j = 0; j < m && *iters < max_iters; ++j) {
+  GmresState* st = c->gst;
+  const int32_t* skip = &st->skip;
+  int rc;
+  c->it_marks.assign(m + 1, c->timed.size());
+  for (int j = 0; j < m; ++j) {
+    c->it_marks[j] = c->timed.size();
     S* W = V + (size_t)(j + 1) * ldv;
-    if (c->geometry == STM_GEOM_TRILINEAR) {
-      precond_curved<S, S>(z, V + (size_t)j * ldv, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream);
+    const S* Vj = V + (size_t)j * ldv;
+    if (c->geometry != STM_GEOM_BRICK) {  // 3x3 blocks of the (cell-mean) metric mass
+      precond_curved<S, S>(z, Vj, 0, 0, nullptr, curved_ptr<S>(c, 3), qn3, c->ne, false, c->stream, skip);
       c->launches += 1;
-      if ((rc = linop<S>(c, dt, z, W))) return rc;
-    } else if (c->hp) {
-      precond_hp<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), c->off_test, c->pq, c->ne, c->stream);
-      c->launches += 1;
-      if ((rc = linop<S>(c, dt, z, W))) return rc;
-    } else if (sizeof(S) == 4 && !c->kap64) {
-      // FP32 single-pass kernel (memory-bound): P^{-1} on load saves a pass over the basis vector
-      if ((rc = linop_pre<S>(c, dt, V + (size_t)j * ldv, W))) return rc;
+      if ((rc = linop<S>(c, dt, z, W, skip))) return rc;
     } else {
-      // FP64: the residual kernels are bound by the FP64 pipe, where the scaling costs more
-      // than the separate (memory-bound) preconditioner pass
-      precond_apply<S>(z, V + (size_t)j * ldv, inv_ptr<S>(c), qn3, n, c->stream);
-      c->launches += 1;
-      if ((rc = linop<S>(c, dt, z, W))) return rc;
+      // bricks: P^{-1} on load inside the residual kernels (one multiply per unknown in the
+      // temporal contraction; the mass term of A P^{-1} v is v itself), no separate pass
+      if ((rc = linop_pre<S>(c, dt, Vj, W, skip))) return rc;
     }
-    if (c->opts.eta_tol > 0) scale_blocks<S>(c, W, sw_ptr<S>(c), n);  // residual space weighted by S
-    multidot<S>(W, V, ldv, j + 1, true, n, c->red_partial, c->red_out, c->stream);
-    c->launches += 2;
-    STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    STM_CK(cudaStreamSynchronize(c->stream));
-    const double before = c->h_pinned[j + 1];
-    Coef16 cc{};
-    for (int i = 0; i <= j; ++i) {
-      cc.c[i] = c->h_pinned[i] / (alpha[i] * alpha[i]);
-      H[i * m + j] = c->h_pinned[i] / (alpha[i] * alpha[j]);
+    if (c->opts.eta_tol > 0) scale_blocks<S>(c, W, sw_ptr<S>(c), n, skip);  // residual space weighted by S
+    multidot<S>(W, V, ldv, j + 1, true, n, c->red_partial, nullptr, c->stream, skip);
+    gmres_gs(c->red_partial, st, j, 0, c->stream);
+    axpy_norm<S>(W, V, ldv, j + 1, Coef16{}, n, c->red_partial, nullptr, c->stream, skip, st->cc);
+    c->launches += 4;
+    if (c->opts.reorth) {
+      const int32_t* skip2 = &st->skip_reo;
+      gmres_after(c->red_partial, st, 1, c->stream);
+      multidot<S>(W, V, ldv, j + 1, false, n, c->red_partial, nullptr, c->stream, skip2);
+      gmres_gs(c->red_partial, st, j, 1, c->stream);
+      axpy_norm<S>(W, V, ldv, j + 1, Coef16{}, n, c->red_partial, nullptr, c->stream, skip2, st->cc);
+      c->launches += 4;
     }
-    axpy_norm<S>(W, V, ldv, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
-    c->launches += 2;
-    STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    STM_CK(cudaStreamSynchronize(c->stream));
-    double after = c->h_pinned[0];
-    if (c->opts.reorth && after < 0.5 * before) {
-      multidot<S>(W, V, ldv, j + 1, false, n, c->red_partial, c->red_out, c->stream);
-      c->launches += 2;
-      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      STM_CK(cudaStreamSynchronize(c->stream));
-      for (int i = 0; i <= j; ++i) {
-        cc.c[i] = c->h_pinned[i] / (alpha[i] * alpha[i]);
-        H[i * m + j] += c->h_pinned[i] / (alpha[i] * alpha[j]);
-      }
-      axpy_norm<S>(W, V, ldv, j + 1, cc, n, c->red_partial, c->red_out, c->stream);
-      c->launches += 2;
-      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      STM_CK(cudaStreamSynchronize(c->stream));
-      after = c->h_pinned[0];
-    }
-    if (!std::isfinite(after) || !std::isfinite(before)) return fail(c, STM_ENAN, "non-finite value in GMRES");
-    const double nw = std::sqrt(after);
-    alpha[j + 1] = (alpha[j] < 0 ? -nw : nw);
-    H[(j + 1) * m + j] = nw / std::fabs(alpha[j]);
-    for (int i = 0; i < j; ++i) {
-      const double x = H[i * m + j], y = H[(i + 1) * m + j];
-      H[i * m + j] = cs[i] * x + sn[i] * y;
-      H[(i + 1) * m + j] = -sn[i] * x + cs[i] * y;
-    }
-    const double x = H[j * m + j], y = H[(j + 1) * m + j];
-    const double r = std::hypot(x, y);
-    cs[j] = r > 0 ? x / r : 1.0;
-    sn[j] = r > 0 ? y / r : 0.0;
-    H[j * m + j] = r;
-    H[(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    ++*iters;
-    k = j + 1;
-    if (std::fabs(g[j + 1]) <= tol_abs || nw == 0.0) break;
+    gmres_givens(c->red_partial, st, j, m, c->opts.reorth ? 1 : 0, c->stream);
+    c->launches += 1;
   }
-  for (int i = k - 1; i >= 0; --i) {
-    double t = g[i];
-    for (int l = i + 1; l < k; ++l) t -= H[i * m + l] * yv[l];
-    yv[i] = t / H[i * m + i];
-  }
-  for (int i = 0; i < kMaxDots; ++i) yc->c[i] = 0.0;
-  for (int i = 0; i < k; ++i) yc->c[i] = yv[i] / alpha[i];
-  *k_out = k;
-  *res = std::fabs(g[k]);
+  c->it_marks[m] = c->timed.size();
+  gmres_backsub(st, m, c->stream);
+  c->launches += 1;
+  STM_CK(cudaGetLastError());
   return STM_OK;
 }
 
@@ -1158,6 +1150,105 @@ int ensure_buf(stm_ctx* c, T** p, int64_t* have, int64_t need) {
     return fail(c, STM_ENOMEM, "solver workspace allocation failed");
   }
   *have = need;
+  return STM_OK;
+}
+
+// One restart cycle of the slab solve: the true FP64 residual R(u0, x) and the slab's stop
+// test, then (unless it holds) m GMRES iterations and x += P^{-1} sum yc V; no host
+// synchronisation.  Mixed precision: the FP32 inner cycle works on the rounded FP64
+// residual and the FP64 residual of the next cycle refines it (iterative refinement).
+int launch_cycle(stm_ctx* c, double dt, const double* b, bool mixed, int64_t ldv) {
+  const int m = c->opts.restart;
+  const int64_t n = c->n_test;
+  const int64_t qn3 = (int64_t)c->Q * c->N3;
+  const bool curved = c->geometry != STM_GEOM_BRICK;  // trilinear or general affine: 3x3 blocks
+  const bool inexact = c->opts.eta_tol > 0;
+  GmresState* st = c->gst;
+  int rc;
+  double* R64 = mixed ? c->z : c->V;
+  if ((rc = resid64(c, dt, c->x, b, R64))) return rc;
+  axpy_norm<double>(R64, R64, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream);
+  gmres_reduce(c->red_partial, st, 0, c->stream);
+  c->launches += 2;
+  if (inexact) {  // GMRES then works on the weighted residual S R
+    scale_blocks<double>(c, R64, c->sw64, n);
+    axpy_norm<double>(R64, R64, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream);
+    gmres_reduce(c->red_partial, st, 1, c->stream);
+    c->launches += 2;
+  }
+  gmres_outer_check(st, c->stream);
+  c->launches += 1;
+  if (!mixed) {
+    // V[0] = R = -r, so v_0 = V[0] / (-beta)
+    gmres_cycle_init(st, inexact ? 1 : 0, 0.0, c->stream);
+    c->launches += 1;
+    if ((rc = gmres_iterations<double>(c, dt, c->V, ldv, c->z, n))) return rc;
+    if (curved) precond_curved<double, double>(c->x, c->V, ldv, 0, nullptr, c->Pinv64, qn3, c->ne, true, c->stream,
+                                               nullptr, st);
+    else if (c->hp) combine_hp<double, double>(c->x, c->V, ldv, m, Coef16{}, c->inv64, c->off_test, c->pq, c->ne,
+                                               c->stream, st);
+    else precond_combine<double, double>(c->x, c->V, ldv, m, Coef16{}, c->inv64, qn3, n, c->stream, st);
+  } else {
+    // FP32 inner GMRES(m) cycle on A d = r, started from the rounded FP64 residual; the inner
+    // target is the outer one or what FP32 can resolve (1e-6 of the start), whichever is larger
+    convert<float, double>(c->V32, R64, n, c->stream, &st->skip);
+    axpy_norm<float>(c->V32, c->V32, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream, &st->skip);
+    gmres_reduce(c->red_partial, st, 2, c->stream, &st->skip);
+    gmres_cycle_init(st, 2, 1e-6, c->stream);
+    c->launches += 4;
+    if ((rc = gmres_iterations<float>(c, dt, c->V32, ldv, c->z32, n))) return rc;
+    if (curved) precond_curved<float, double>(c->x, c->V32, ldv, 0, nullptr, c->Pinv32, qn3, c->ne, true, c->stream,
+                                              nullptr, st);
+    else if (c->hp) combine_hp<float, double>(c->x, c->V32, ldv, m, Coef16{}, c->inv32, c->off_test, c->pq, c->ne,
+                                              c->stream, st);
+    else precond_combine<float, double>(c->x, c->V32, ldv, m, Coef16{}, c->inv32, qn3, n, c->stream, st);
+  }
+  c->launches += 1;
+  STM_CK(cudaGetLastError());
+  return STM_OK;
+}
+
+void drop_cycle_graphs(stm_ctx* c) {
+  for (auto& kv : c->cycle_graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->cycle_graphs.clear();
+}
+
+// Runs one restart cycle: captured once per (precision, dt, load pointer) into a CUDA graph
+// on the capture stream and replayed on the context stream (directly launched while
+// profiling, whose events are recorded around individual kernels).
+int run_cycle(stm_ctx* c, double dt, const double* b, bool mixed, int64_t ldv) {
+  if (c->profiling) return launch_cycle(c, dt, b, mixed, ldv);
+  const auto key = std::make_tuple(mixed ? 1 : 0, dt, (const void*)b);
+  auto it = c->cycle_graphs.find(key);
+  if (it == c->cycle_graphs.end()) {
+    if (!c->cap_stream) STM_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (c->cycle_graphs.size() >= 16) drop_cycle_graphs(c);
+    const int64_t l0 = c->launches;
+    cudaStream_t orig = c->stream;
+    STM_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    c->stream = c->cap_stream;
+    const int rc = launch_cycle(c, dt, b, mixed, ldv);
+    c->stream = orig;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+    const int64_t count = c->launches - l0;
+    c->launches = l0;
+    if (rc || ee != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc ? rc : fail(c, STM_EDEVICE, std::string("cycle capture: ") + cudaGetErrorString(ee));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(c, STM_EDEVICE, std::string("cycle graph: ") + cudaGetErrorString(ie));
+    stm_ctx::CycleGraph cg;
+    cg.exec = ex;
+    cg.launches = count;
+    it = c->cycle_graphs.emplace(key, cg).first;
+  }
+  c->launches += it->second.launches;
+  STM_CK(cudaGraphLaunch(it->second.exec, c->stream));
   return STM_OK;
 }
 
@@ -1215,8 +1306,11 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       if (m->nbr[k] == -2) return bad(STM_EUNSUPPORTED, "the dissipative term is not built for 2:1 faces");
   }
   if (m->n_hang < 0 || (m->n_hang > 0 && !m->hang)) return bad(STM_EINVAL, "bad hang list");
-  if (m->geometry != STM_GEOM_BRICK && m->geometry != STM_GEOM_TRILINEAR) return bad(STM_EINVAL, "unknown geometry");
-  const bool curved = m->geometry == STM_GEOM_TRILINEAR;
+  if (m->geometry != STM_GEOM_BRICK && m->geometry != STM_GEOM_AFFINE && m->geometry != STM_GEOM_TRILINEAR)
+    return bad(STM_EINVAL, "unknown geometry");
+  // trilinear and general affine elements share the vertex-based set-up (metric, faces)
+  const bool curved = m->geometry != STM_GEOM_BRICK;
+  const bool affine = m->geometry == STM_GEOM_AFFINE;
   c->geometry = m->geometry;
   c->N = c->P + 1;
   c->N2 = c->N * c->N;
@@ -1276,6 +1370,38 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
         c->h_h[3 * e + d] = h[d];
         c->h_mass[6 * e + d] = 1.0;
         c->h_mass[6 * e + 3 + d] = 1.0;
+      }
+      if (affine) {
+        // parallelepiped: DF = [x_1 - x_0, x_2 - x_0, x_4 - x_0] and x_v = x_0 + DF bits(v)
+        double DF[3][3];
+        for (int d = 0; d < 3; ++d)
+          for (int k = 0; k < 3; ++k) DF[d][k] = m->vert[3 * hv[1 << k] + d] - v0[d];
+        double scale = 0.0;
+        for (int d = 0; d < 3; ++d)
+          for (int k = 0; k < 3; ++k) scale = std::max(scale, std::fabs(DF[d][k]));
+        for (int v = 0; v < 8; ++v)
+          for (int d = 0; d < 3; ++d) {
+            const double x = v0[d] + DF[d][0] * (v & 1) + DF[d][1] * ((v >> 1) & 1) + DF[d][2] * ((v >> 2) & 1);
+            if (std::fabs(m->vert[3 * hv[v] + d] - x) > 1e-10 * scale)
+              return bad(STM_EUNSUPPORTED, "element is not a parallelepiped (use STM_GEOM_TRILINEAR)");
+          }
+        // G = |J| DF^{-1} DF^{-T} = adj(DF) adj(DF)^T / J, J = det DF
+        double A[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+            A[j][i] = DF[i1][j1] * DF[i2][j2] - DF[i1][j2] * DF[i2][j1];  // cofactor transpose
+          }
+        const double J = DF[0][0] * A[0][0] + DF[0][1] * A[1][0] + DF[0][2] * A[2][0];
+        if (!(J > 0)) return bad(STM_EINVAL, "element map with non-positive Jacobian");
+        const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+        double g[6];
+        for (int k = 0; k < 6; ++k) {
+          const int a = pr[k][0], b = pr[k][1];
+          g[k] = (A[a][0] * A[b][0] + A[a][1] * A[b][1] + A[a][2] * A[b][2]) / J;
+        }
+        for (int k = 0; k < 6; ++k) c->h_mass3.push_back(m->eps[e] * g[k]);
+        for (int k = 0; k < 6; ++k) c->h_mass3.push_back(m->mu[e] * g[k]);
       }
       continue;
     }
@@ -1410,6 +1536,8 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       }
   }
   if (cudaGetDevice(&c->device) != cudaSuccess) return bad(STM_EDEVICE, "no CUDA device");
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
+    return bad(STM_EDEVICE, "device attribute query failed");
   // 0 is the CUDA default stream, so work is ordered with a caller that uses it
   c->stream = (cudaStream_t)(intptr_t)c->opts.stream;
   std::vector<float> m32(c->h_mass.begin(), c->h_mass.end());
@@ -1477,6 +1605,15 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       int bad_h = 0;
       cudaMemcpy(&bad_h, bad_d, sizeof(int), cudaMemcpyDeviceToHost);
       cudaFree(bad_d);
+      if (affine) {
+        std::vector<float> m3(c->h_mass3.begin(), c->h_mass3.end());
+        ok = cudaMalloc(&c->mass3_64, c->h_mass3.size() * sizeof(double)) == cudaSuccess &&
+             cudaMalloc(&c->mass3_32, m3.size() * sizeof(float)) == cudaSuccess;
+        if (ok) {
+          cudaMemcpy(c->mass3_64, c->h_mass3.data(), c->h_mass3.size() * sizeof(double), cudaMemcpyHostToDevice);
+          cudaMemcpy(c->mass3_32, m3.data(), m3.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+      }
       if (bad_h) {
         stm_destroy(c);
         fprintf(stderr, "stm_create: an element map has a non-positive Jacobian\n");
@@ -1633,7 +1770,8 @@ int32_t stm_destroy(stm_ctx* c) {
                   c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
                   c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
-                  c->sw64,    c->sw32,    c->kap64,  c->kap32, c->nkl,    c->tmat64, c->tmat32};
+                  c->sw64,    c->sw32,    c->kap64,  c->kap32, c->nkl,    c->tmat64, c->tmat32,
+                  c->mass3_64, c->mass3_32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1646,6 +1784,9 @@ int32_t stm_destroy(stm_ctx* c) {
     if (k.elist) cudaFree(k.elist);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  drop_cycle_graphs(c);
+  if (c->gst) cudaFree(c->gst);
+  if (c->h_gst) cudaFreeHost(c->h_gst);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1810,13 +1951,15 @@ int project_curved(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, void*
       }
     }
   }
-  // CG on the device: x, r, p, Ap, z
+  // CG on the device: x, r, p, Ap, z and the right side b; restarted from the true residual
+  // b - M x (at most three times) until that is below 1e-15 |b| (the recursively updated
+  // residual of CG drifts away from the true one near round-off)
   double* buf = nullptr;
-  if (cudaMalloc(&buf, 5 * (size_t)n * sizeof(double)) != cudaSuccess) {
+  if (cudaMalloc(&buf, 6 * (size_t)n * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, STM_ENOMEM, "projection work vectors");
   }
-  double *x = buf, *r = buf + n, *pv = buf + 2 * n, *Ap = buf + 3 * n, *z = buf + 4 * n;
+  double *x = buf, *r = buf + n, *pv = buf + 2 * n, *Ap = buf + 3 * n, *z = buf + 4 * n, *bd = buf + 5 * n;
   auto dot = [&](const double* a, const double* b, double* out) -> int {
     multidot<double>(a, b, 0, 1, false, n, c->red_partial, c->red_out, c->stream);
     c->launches += 2;
@@ -1825,49 +1968,63 @@ int project_curved(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, void*
     *out = c->h_pinned[0];
     return STM_OK;
   };
+  auto mass = [&](const double* in, double* out) -> int {
+    const int em = launch_mass_curved<double>(P, 1, in, 6LL * N3, N3, nullptr, 0, 0, c->Gw64, c->eps64, c->mu64,
+                                              c->ct, c->ne, out, c->stream);
+    c->launches += 1;
+    return em ? fail(c, STM_EDEVICE, "projection mass launch") : STM_OK;
+  };
   int rc = STM_OK;
   do {
     if (cudaMemsetAsync(x, 0, n * sizeof(double), c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(r, rhs.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+        cudaMemcpyAsync(bd, rhs.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(r, bd, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
       rc = fail(c, STM_EDEVICE, "projection copies");
       break;
     }
     double rr0;
     if ((rc = dot(r, r, &rr0))) break;
-    precond_curved<double, double>(z, r, 0, 0, nullptr, c->Pinv64, N3, c->ne, false, c->stream);
-    STM_CK(cudaMemcpyAsync(pv, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    double rz;
-    if ((rc = dot(r, z, &rz))) break;
-    for (int it = 0; it < 1000 && rr0 > 0; ++it) {
-      const int em = launch_mass_curved<double>(P, 1, pv, 6LL * N3, N3, nullptr, 0, 0, c->Gw64, c->eps64, c->mu64,
-                                                c->ct, c->ne, Ap, c->stream);
-      c->launches += 1;
-      if (em) {
-        rc = fail(c, STM_EDEVICE, "projection mass launch");
-        break;
+    for (int restart = 0; restart < 4 && rr0 > 0 && !rc; ++restart) {
+      if (restart > 0) {  // true residual r = b - M x
+        if ((rc = mass(x, Ap))) break;
+        STM_CK(cudaMemcpyAsync(r, bd, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        Coef16 cm{};
+        cm.c[0] = 1.0;
+        axpy_norm<double>(r, Ap, 0, 1, cm, n, c->red_partial, c->red_out, c->stream);
+        c->launches += 2;
+        STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        STM_CK(cudaStreamSynchronize(c->stream));
+        if (!(c->h_pinned[0] > 1e-30 * rr0)) break;  // |b - M x| <= 1e-15 |b|
       }
-      double pAp;
-      if ((rc = dot(pv, Ap, &pAp))) break;
-      const double alpha = rz / pAp;
-      Coef16 ca{}, cr{};
-      ca.c[0] = -alpha;
-      cr.c[0] = alpha;
-      axpy_norm<double>(x, pv, 0, 1, ca, n, c->red_partial, c->red_out, c->stream);  // x += alpha p
-      axpy_norm<double>(r, Ap, 0, 1, cr, n, c->red_partial, c->red_out, c->stream);  // r -= alpha Ap
-      c->launches += 4;
-      STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      STM_CK(cudaStreamSynchronize(c->stream));
-      if (!(c->h_pinned[0] > 1e-28 * rr0)) break;  // |r| <= 1e-14 |b| (or not finite: stop)
       precond_curved<double, double>(z, r, 0, 0, nullptr, c->Pinv64, N3, c->ne, false, c->stream);
-      c->launches += 1;
-      double rz1;
-      if ((rc = dot(r, z, &rz1))) break;
-      Coef16 cb{};
-      cb.c[0] = -rz1 / rz;
-      rz = rz1;
-      axpy_norm<double>(z, pv, 0, 1, cb, n, c->red_partial, c->red_out, c->stream);  // z += beta p
-      c->launches += 2;
-      std::swap(pv, z);
+      STM_CK(cudaMemcpyAsync(pv, z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      double rz;
+      if ((rc = dot(r, z, &rz))) break;
+      for (int it = 0; it < 1000; ++it) {
+        if ((rc = mass(pv, Ap))) break;
+        double pAp;
+        if ((rc = dot(pv, Ap, &pAp))) break;
+        const double alpha = rz / pAp;
+        Coef16 ca{}, cr{};
+        ca.c[0] = -alpha;
+        cr.c[0] = alpha;
+        axpy_norm<double>(x, pv, 0, 1, ca, n, c->red_partial, c->red_out, c->stream);  // x += alpha p
+        axpy_norm<double>(r, Ap, 0, 1, cr, n, c->red_partial, c->red_out, c->stream);  // r -= alpha Ap
+        c->launches += 4;
+        STM_CK(cudaMemcpyAsync(c->h_pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        STM_CK(cudaStreamSynchronize(c->stream));
+        if (!(c->h_pinned[0] > 1e-32 * rr0)) break;  // |r| <= 1e-16 |b| (or not finite: stop)
+        precond_curved<double, double>(z, r, 0, 0, nullptr, c->Pinv64, N3, c->ne, false, c->stream);
+        c->launches += 1;
+        double rz1;
+        if ((rc = dot(r, z, &rz1))) break;
+        Coef16 cb{};
+        cb.c[0] = -rz1 / rz;
+        rz = rz1;
+        axpy_norm<double>(z, pv, 0, 1, cb, n, c->red_partial, c->red_out, c->stream);  // z += beta p
+        c->launches += 2;
+        std::swap(pv, z);
+      }
     }
     if (rc) break;
     STM_CK(cudaMemcpyAsync(c->state, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -1884,7 +2041,7 @@ int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, 
   // Covariant L2 projection on a brick: u_c[s] = h_c int_K^ phi_s (F_c o F_K) dx^,
   // by the tensor Gauss rule with p+2 points per direction (per element degree).
   if (!c) return STM_EINVAL;
-  if (c->geometry == STM_GEOM_TRILINEAR) return project_curved(c, t, E0, H0, user);
+  if (c->geometry != STM_GEOM_BRICK) return project_curved(c, t, E0, H0, user);
   std::vector<std::vector<double>> xg(9), wg(9), Lg(9);
   for (int P = 0; P <= 7; ++P) {
     const int nq = P + 2, N = P + 1;
@@ -1949,7 +2106,7 @@ int32_t stm_set_initial(stm_ctx* c, double t, stm_field_fn E0, stm_field_fn H0, 
 
 int32_t stm_energy(stm_ctx* c, double* energy) {
   if (!c || !energy) return STM_EINVAL;
-  if (c->geometry == STM_GEOM_TRILINEAR || c->hp) {
+  if (c->geometry != STM_GEOM_BRICK || c->hp) {
     if (c->hp) {
       energy_hp(c->state, c->mass64, c->off_state, c->pq, c->ne, c->el, c->stream);
     } else {
@@ -1980,7 +2137,6 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   if (!mixed && c->opts.precision != STM_FP64) return fail(c, STM_EINVAL, "opts.precision must be FP64 or MIXED");
   const int m = c->opts.restart;
   const int64_t n = c->n_test;
-  const int64_t qn3 = (int64_t)c->Q * c->N3;
   int rc;
   // FP64 buffers: x (unknowns), z (work / residual); basis in FP64 or FP32
   // basis columns start on 16-byte (here 512-byte) boundaries for vector loads
@@ -1993,86 +2149,69 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   } else if ((rc = ensure_buf<double>(c, &c->V, &c->V_len, (m + 1) * ldv))) {
     return rc;
   }
+  if (!c->gst) {
+    if (cudaMalloc((void**)&c->gst, sizeof(GmresState)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_gst, sizeof(GmresState)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, STM_ENOMEM, "GMRES state allocation failed");
+    }
+    STM_CK(cudaMemsetAsync(c->gst, 0, sizeof(GmresState), c->stream));
+  }
+  if (mixed && (c->hp || c->kap64)) {  // FP32 residual scratch, allocated before any capture
+    float *y32 = nullptr, *tr32 = nullptr;
+    if ((rc = scratch<float>(c, &y32, &tr32))) return rc;
+  }
   const double* b = nullptr;
   if ((rc = build_load(c, c->t, dt, &b))) return rc;
-  const bool curved = c->geometry == STM_GEOM_TRILINEAR;
-  // reference: ||R(U^(0))|| with all unknowns zero (R6)
-  STM_CK(cudaMemsetAsync(c->x, 0, n * sizeof(double), c->stream));
-  if ((rc = resid64(c, dt, c->x, b, c->z))) return rc;
-  double ref;
-  if ((rc = norm2<double>(c, c->z, n, &ref))) return rc;
-  ref = std::sqrt(ref);
-  // initial guess: u_1 = u_0, higher modes 0
-  if (c->hp) init_guess_hp(c->x, c->state, c->off_test, c->off_state, c->pq, c->ne, c->stream);
-  else k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
-  c->launches += 1;
-  int iters = 0, cycles = 0;
-  double rel = 0.0, phi = 0.0;
-  const double tol = c->opts.tol;
   // inexact solve: stop when this slab's share of eta_it (Sec. 5.3) is below eta_tol / sqrt(slabs)
   const bool inexact = c->opts.eta_tol > 0;
-  double budget = 0.0;
+  double target = c->opts.tol;
   if (inexact) {
-    if (curved) return fail(c, STM_EUNSUPPORTED, "the inexact solve is built for brick meshes");
+    if (c->geometry != STM_GEOM_BRICK) return fail(c, STM_EUNSUPPORTED, "the inexact solve is built for brick meshes");
     for (const auto& k : c->classes)  // the bound needs one temporal degree everywhere
       if (k.Q != c->classes[0].Q) return fail(c, STM_EUNSUPPORTED, "the inexact solve needs a uniform q");
     if (c->ltr) return fail(c, STM_EUNSUPPORTED, "the inexact solve needs N_K = 1 (no local refinement in time)");
     if (!(c->opts.t_final > 0)) return fail(c, STM_EINVAL, "opts.t_final must be positive for the inexact solve");
     if ((rc = build_eta_weights(c, dt))) return rc;
     const double nslab = std::max(1.0, std::round(c->opts.t_final / dt));
-    budget = c->opts.eta_tol / std::sqrt(nslab);
+    target = c->opts.eta_tol / std::sqrt(nslab);
   }
-  bool done = false;
-  for (;;) {
-    // true FP64 residual R(u0, x)
-    double* R64 = mixed ? c->z : c->V;
-    if ((rc = resid64(c, dt, c->x, b, R64))) return rc;
-    double beta2;
-    if ((rc = norm2<double>(c, R64, n, &beta2))) return rc;
-    double beta = std::sqrt(beta2);
-    rel = ref > 0 ? beta / ref : beta;
-    if (!std::isfinite(rel)) return fail(c, STM_ENAN, "non-finite residual in slab solve");
-    if (inexact) {
-      scale_blocks<double>(c, R64, c->sw64, n);
-      double p2;
-      if ((rc = norm2<double>(c, R64, n, &p2))) return rc;
-      phi = std::sqrt(p2);
-      beta = phi;  // GMRES works on the weighted residual S R
-      done = phi <= budget;
-    } else {
-      done = rel <= tol;
-    }
-    if (done || iters >= c->opts.max_it || beta == 0.0) break;
-    const double cyc_tol = inexact ? budget : tol * ref;
-    int k = 0;
-    Coef16 yc{};
-    double res = 0.0;
-    if (!mixed) {
-      // V[0] = R = -r, so v_0 = V[0] / (-beta)
-      if ((rc = gmres_cycle<double>(c, dt, c->V, ldv, c->z, n, -beta, cyc_tol, c->opts.max_it, &k, &yc, &res,
-                                    &iters)))
-        return rc;
-      if (curved) precond_curved<double, double>(c->x, c->V, ldv, k, yc.c, c->Pinv64, qn3, c->ne, true, c->stream);
-      else if (c->hp) combine_hp<double, double>(c->x, c->V, ldv, k, yc, c->inv64, c->off_test, c->pq, c->ne, c->stream);
-      else precond_combine<double, double>(c->x, c->V, ldv, k, yc, c->inv64, qn3, n, c->stream);
-    } else {
-      // FP32 inner GMRES(m) cycle on A d = r, started from the rounded FP64 residual;
-      // the inner target is the outer one or what FP32 can resolve, whichever is larger
-      convert<float, double>(c->V32, R64, n, c->stream);
-      c->launches += 1;
-      double b32;
-      if ((rc = norm2<float>(c, c->V32, n, &b32))) return rc;
-      b32 = std::sqrt(b32);
-      const double tin = std::max(cyc_tol, 1e-6 * b32);
-      if ((rc = gmres_cycle<float>(c, dt, c->V32, ldv, c->z32, n, -b32, tin, c->opts.max_it, &k, &yc, &res, &iters)))
-        return rc;
-      if (curved) precond_curved<float, double>(c->x, c->V32, ldv, k, yc.c, c->Pinv32, qn3, c->ne, true, c->stream);
-      else if (c->hp) combine_hp<float, double>(c->x, c->V32, ldv, k, yc, c->inv32, c->off_test, c->pq, c->ne, c->stream);
-      else precond_combine<float, double>(c->x, c->V32, ldv, k, yc, c->inv32, qn3, n, c->stream);
-    }
+  GmresState* st = c->gst;
+  // reference: ||R(U^(0))|| with all unknowns zero (R6), kept on the device
+  STM_CK(cudaMemsetAsync(c->x, 0, n * sizeof(double), c->stream));
+  if ((rc = resid64(c, dt, c->x, b, c->z))) return rc;
+  axpy_norm<double>(c->z, c->z, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream);
+  gmres_reduce(c->red_partial, st, 0, c->stream);
+  gmres_slab_start(st, target, c->opts.max_it, inexact ? 1 : 0, c->stream);
+  c->launches += 3;
+  // initial guess: u_1 = u_0, higher modes 0 (or all unknowns 0: x is already zero)
+  if (!c->opts.zero_guess) {
+    if (c->hp) init_guess_hp(c->x, c->state, c->off_test, c->off_state, c->pq, c->ne, c->stream);
+    else k_init_guess<<<grid1(n), 256, 0, c->stream>>>(c->x, c->state, c->Q, c->N3, n);
     c->launches += 1;
-    ++cycles;
-    if (k == 0) break;
+  }
+  // restart cycles, each one launch sequence (a replayed CUDA graph unless profiling) and one
+  // read of the device state: the stop test, the iteration count and the error status
+  bool done = false;
+  const int max_cycles = c->opts.max_it + 2;  // every cycle but the last makes >= 1 iteration
+  for (int cyc = 0; cyc < max_cycles; ++cyc) {
+    if ((rc = run_cycle(c, dt, b, mixed, ldv))) return rc;
+    STM_CK(cudaMemcpyAsync(c->h_gst, st, sizeof(GmresState), cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    const GmresState& h = *c->h_gst;
+    if (c->profiling && c->it_marks.size() == (size_t)m + 1) {
+      // the residual launches of iterations the device skipped did no work: not timed
+      const size_t k = (size_t)std::max(0, std::min(h.k, m));
+      c->timed.erase(c->timed.begin() + (std::ptrdiff_t)c->it_marks[k],
+                     c->timed.begin() + (std::ptrdiff_t)c->it_marks[m]);
+      c->it_marks.clear();
+    }
+    if (h.status < 0) return fail(c, h.status, "non-finite value in the slab solve");
+    if (h.outer_done) {
+      done = true;
+      break;
+    }
+    if (h.k == 0) break;  // no progress possible: iteration cap or a zero start vector
   }
   if (c->hp) extract_end_hp(c->state, c->x, c->off_test, c->off_state, c->pq, c->ne, c->stream);
   else k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);
@@ -2082,11 +2221,11 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   double en = 0.0;
   if ((rc = stm_energy(c, &en))) return rc;
   if (rep) {
-    rep->iterations = iters;
-    rep->restarts = cycles;
-    rep->rel_residual = rel;
+    rep->iterations = c->h_gst->iters;
+    rep->restarts = c->h_gst->cycles;
+    rep->rel_residual = c->h_gst->rel;
     rep->energy = en;
-    rep->eta2 = inexact ? phi * phi : 0.0;
+    rep->eta2 = inexact ? c->h_gst->phi * c->h_gst->phi : 0.0;
   }
   return done ? STM_OK : STM_ENOTCONV;
 }
@@ -2189,7 +2328,7 @@ int autotune_prec(stm_ctx* c, double dt, int reps, std::vector<double>& best_ms)
           a.kap = kap_ptr<T>(c);
           a.dt_k = (T)dt;
           a.tb = make_tables<T>(cl.P, kMaxQ, dt / cl.NK);
-          const int grid = (int)std::min<int64_t>(cl.count, 1 << 30);
+          const int grid = res_grid(c, cl.count);
           LaunchEvents none;
           if (launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, none, 1, cb) ||
               launch_residual_ph<T>(cl.P, cl.Q, a, c->stream, grid, none, 2, cb))
@@ -2226,6 +2365,7 @@ int32_t stm_autotune(stm_ctx* c, double dt, int32_t reps, int32_t n_max, int32_t
   std::vector<double> best;
   int rc = autotune_prec<double>(c, dt, reps, best);
   if (rc) return rc;
+  drop_cycle_graphs(c);  // captured cycles hold the old block sizes
   const int ncl = c->hp ? (int)c->classes.size() : 1;
   if (n_out) *n_out = ncl;
   for (int k = 0; k < ncl && k < n_max; ++k) {

@@ -76,17 +76,27 @@ __global__ void k_noalloc_mass(const double* __restrict__ h, const double* __res
 extern "C" int32_t stm_residual_apply_noalloc(int64_t n_elem, int32_t p, int32_t q, double dt, const int32_t* nbr,
                                               const double* h, const double* eps, const double* mu, const double* U,
                                               double* R, int64_t stream) {
-  if (n_elem <= 0 || p < 0 || p > 7 || q < 1 || q > 4 || !(dt > 0) || !nbr || !h || !eps || !mu || !U || !R)
+  if (n_elem <= 0 || p < 0 || p > 7 || q < 1 || q > stm::kMaxQ || !(dt > 0) || !nbr || !h || !eps || !mu || !U ||
+      !R)
     return STM_EINVAL;
   const int64_t n = p + 1, n2 = n * n, n3 = n2 * n;
-  const size_t need_mass = round256(sizeof(double) * 6 * (size_t)n_elem);
-  const size_t need_y = round256(sizeof(double) * 6 * (size_t)q * n3 * n_elem);
-  const size_t need_tr = round256(sizeof(double) * 24 * (size_t)q * n2 * n_elem);
-  if (need_mass + need_y + need_tr > (size_t)STM_NOALLOC_SCRATCH_BYTES) {
+  // bound the element count before forming any product: past this count the scratch
+  // cannot fit, and below it none of the sums below can overflow
+  const size_t per_elem = sizeof(double) * (6 + 6 * (size_t)q * n3 + 24 * (size_t)q * n2);
+  const size_t cap = (size_t)STM_NOALLOC_SCRATCH_BYTES;
+  size_t need = 0;
+  size_t need_mass = 0, need_y = 0;
+  if ((uint64_t)n_elem <= cap / per_elem) {
+    need_mass = round256(sizeof(double) * 6 * (size_t)n_elem);
+    need_y = round256(sizeof(double) * 6 * (size_t)q * n3 * (size_t)n_elem);
+    const size_t need_tr = round256(sizeof(double) * 24 * (size_t)q * n2 * (size_t)n_elem);
+    need = need_mass + need_y + need_tr;
+  }
+  if (need == 0 || need > cap) {
     fprintf(stderr,
-            "stm_residual_apply_noalloc: %lld elements of degree (p=%d, q=%d) need %zu bytes of scratch, more than "
-            "the fixed %zu bytes (STM_NOALLOC_SCRATCH_BYTES)\n",
-            (long long)n_elem, p, q, need_mass + need_y + need_tr, (size_t)STM_NOALLOC_SCRATCH_BYTES);
+            "stm_residual_apply_noalloc: %lld elements of degree (p=%d, q=%d) need %zu bytes of scratch per element, "
+            "more in total than the fixed %zu bytes (STM_NOALLOC_SCRATCH_BYTES)\n",
+            (long long)n_elem, p, q, per_elem, cap);
     return STM_EINVAL;
   }
   void* base = nullptr;

@@ -55,6 +55,7 @@ def box_mesh(
     perturb: float = 0.0,
     eps=None,
     mu=None,
+    affine=None,
 ) -> dict:
     """Uniform nx*ny*nz hexahedral grid of the box [lo, hi].
 
@@ -66,6 +67,11 @@ def box_mesh(
 
     ``order`` = "lex" numbers cells with x fastest; "morton" numbers them along
     the Z-order curve (face neighbours then sit close in memory).
+
+    ``affine`` (a 3x3 matrix A with det A > 0) maps every vertex x to
+    lo + A (x - lo) after the grid is built: all elements are then the same
+    kind of parallelepiped (geometry "affine": constant Jacobian, not
+    axis-aligned).
     """
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
@@ -76,6 +82,13 @@ def box_mesh(
     gz = np.linspace(lo[2], hi[2], nz + 1)
     Z, Y, X = np.meshgrid(gz, gy, gx, indexing="ij")
     vert = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).copy()
+    if affine is not None:
+        A = np.asarray(affine, dtype=np.float64).reshape(3, 3)
+        if not np.linalg.det(A) > 0:
+            raise ValueError("affine map must have a positive determinant")
+        if perturb:
+            raise ValueError("affine and perturb exclude each other")
+        vert = lo + (vert - lo) @ A.T
     if perturb:
         h = float(np.min((hi - lo) / np.array([nx, ny, nz])))
         u = (vert - lo) / (hi - lo)
@@ -124,7 +137,7 @@ def box_mesh(
         "q": np.full(ne, q, dtype=np.uint8),
         "eps": np.ones(ne) if eps is None else np.broadcast_to(np.asarray(eps, dtype=np.float64), (ne,)).copy(),
         "mu": np.ones(ne) if mu is None else np.broadcast_to(np.asarray(mu, dtype=np.float64), (ne,)).copy(),
-        "geometry": "trilinear" if perturb else "brick",
+        "geometry": "trilinear" if perturb else ("affine" if affine is not None else "brick"),
         "cell": np.stack([ii, jj, kk], axis=1),
         "dims": (nx, ny, nz),
     }

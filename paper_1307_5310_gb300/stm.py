@@ -27,6 +27,7 @@ STM_EUNSUPPORTED = -6
 STM_ENOTCONV = 1
 
 STM_GEOM_BRICK = 0
+STM_GEOM_AFFINE = 1
 STM_GEOM_TRILINEAR = 2
 STM_FP64 = 0
 STM_FP32 = 1
@@ -59,7 +60,8 @@ class stm_mesh(C.Structure):
 class stm_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32),
                 ("deterministic", C.c_int32), ("stream", C.c_int64), ("reorth", C.c_int32), ("graph", C.c_int32),
-                ("eta_tol", C.c_double), ("t_final", C.c_double), ("c_diss", C.c_double)]
+                ("eta_tol", C.c_double), ("t_final", C.c_double), ("c_diss", C.c_double),
+                ("zero_guess", C.c_int32)]
 
 
 class stm_solve_report(C.Structure):
@@ -223,7 +225,7 @@ class Slab:
 
     def __init__(self, mesh: dict, precision=STM_FP64, tol=1e-12, restart=10, max_it=500,
                  deterministic=True, stream=None, reorth=True, graph=True, eta_tol=0.0, t_final=0.0,
-                 c_diss=0.0):
+                 c_diss=0.0, zero_guess=False):
         L = lib()
         self._keep = {}
         ne = mesh["hex"].shape[0]
@@ -239,7 +241,8 @@ class Slab:
                                          dtype=np.int64),
             "nk": np.ascontiguousarray(np.asarray(mesh.get("nk", np.ones(ne))).reshape(ne), dtype=np.uint8),
         }
-        geom = {"brick": STM_GEOM_BRICK, "trilinear": STM_GEOM_TRILINEAR}[mesh.get("geometry", "brick")]
+        geom = {"brick": STM_GEOM_BRICK, "affine": STM_GEOM_AFFINE,
+                "trilinear": STM_GEOM_TRILINEAR}[mesh.get("geometry", "brick")]
         m = stm_mesh(ne, arr["vert"].shape[0],
                      arr["vert"].ctypes.data_as(C.POINTER(C.c_double)),
                      arr["hex"].ctypes.data_as(C.POINTER(C.c_int64)),
@@ -255,7 +258,7 @@ class Slab:
 
             stream = torch.cuda.current_stream().cuda_stream
         o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream), 1 if reorth else 0,
-                     1 if graph else 0, eta_tol, t_final, c_diss)
+                     1 if graph else 0, eta_tol, t_final, c_diss, 1 if zero_guess else 0)
         h = C.c_void_p()
         rc = L.stm_create(C.byref(h), C.byref(m), C.byref(o))
         if rc != STM_OK:

@@ -82,11 +82,11 @@ def test_slab_solve_curved(stm, precision):
     dt = 0.25 / 5
     uo = o.end_state(o.slab_solve(u0, 0.0, dt))
     prec = stm.STM_FP64 if precision == "fp64" else stm.STM_MIXED
-    s = stm.Slab(m, precision=prec, tol=1e-13 if precision == "fp64" else 1e-11, max_it=4000)
+    s = stm.Slab(m, precision=prec, tol=1e-14 if precision == "fp64" else 1e-11, max_it=4000)
     s.set_state(u0)
     rc, rep = s.slab_solve(dt)
     assert rc == stm.STM_OK, rep
-    assert rel(s.get_state()[0], uo) < (1e-11 if precision == "fp64" else 1e-9)
+    assert rel(s.get_state()[0], uo) < (1e-12 if precision == "fp64" else 1e-9)
 
 
 @pytest.mark.parametrize("curved", [False, True])
@@ -122,7 +122,7 @@ def test_source_slab_solve(stm):
     s.set_state(np.zeros(s.n_state), t=0.08)
     rc, rep = s.slab_solve(dt)
     assert rc == stm.STM_OK
-    assert rel(s.get_state()[0], uo) < 1e-11
+    assert rel(s.get_state()[0], uo) < 1e-12
 
 
 @pytest.mark.parametrize("curved", [False, True])
@@ -240,5 +240,5 @@ def test_projection_curved(stm, p):
     s.set_initial(E0, H0, t=0.25)
     ug, t = s.get_state()
     assert t == 0.25
-    assert rel(ug, uo) < 1e-10
-    assert abs(s.energy() - o.energy(uo)) <= 1e-10 * o.energy(uo)
+    assert rel(ug, uo) < 1e-12
+    assert abs(s.energy() - o.energy(uo)) <= 1e-12 * o.energy(uo)

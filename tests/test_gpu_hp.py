@@ -82,4 +82,4 @@ def test_slab_solve_hp(stm, precision):
     s.set_state(u0)
     rc, rep = s.slab_solve(dt)
     assert rc == stm.STM_OK, rep
-    assert rel(s.get_state()[0], uo) < (1e-11 if precision == "fp64" else 1e-9)
+    assert rel(s.get_state()[0], uo) < (1e-12 if precision == "fp64" else 1e-9)

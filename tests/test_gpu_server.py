@@ -31,7 +31,7 @@ BOX = [(0.2, 0.2, 0.2, 0.6, 0.7, 0.5, 2.5, 1.5)]
 
 
 def test_server_matches_oracle(stm):
-    srv = stm.Server(workers=2, tol=1e-13)
+    srv = stm.Server(workers=2, tol=1e-14)
     t = srv.submit(2, 2, 1, 3, 0.05, kind=0)
     res, state = srv.wait(t, with_state=True)
     srv.close()
@@ -43,8 +43,8 @@ def test_server_matches_oracle(stm):
     A_b = o.assemble(0.0, 0.05)
     for k in range(3):
         u = o.end_state(o.slab_solve(u, k * 0.05, 0.05, A_b=A_b))
-    assert rel(state, u) < 1e-10
-    assert abs(res["energy"] - o.energy(u)) < 1e-10 * o.energy(u)
+    assert rel(state, u) < 1e-12
+    assert abs(res["energy"] - o.energy(u)) < 1e-12 * o.energy(u)
 
 
 def test_server_alone_vs_mix(stm):

@@ -98,8 +98,8 @@ def test_slab_solves_vs_oracle(stm, precision):
         u = o.end_state(o.slab_solve(u, n * dt, dt, A_b=A_b))
         rc, rep = s.slab_solve(dt)
         assert rc == stm.STM_OK, rep
-    assert rel(s.get_state()[0], u) < (1e-11 if precision == "fp64" else 1e-9)
-    assert abs(s.energy() - e0) <= (1e-11 if precision == "fp64" else 1e-8) * e0
+    assert rel(s.get_state()[0], u) < (1e-12 if precision == "fp64" else 1e-9)
+    assert abs(s.energy() - e0) <= (1e-12 if precision == "fp64" else 1e-8) * e0
 
 
 def test_unsupported(stm):

@@ -52,6 +52,42 @@ def test_noalloc_matches_residual_apply():
         s.close()
 
 
+def test_noalloc_near_limit_back_to_back():
+    """Two differently sized calls queued on one stream before a single synchronize, both
+    close to the fixed scratch size: 1,000 elements at p=4, q=3 (32.4 MB of 33.5 MB) and
+    216 elements at p=7, q=4 (31.9 MB, whose trace pass needs more than 48 KB of shared
+    memory per block).  Each result must equal stm_residual_apply's."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1307_5310_gb300 import stm
+
+    cases = []
+    for k, (dims, p, q, dt) in enumerate((((10, 10, 10), 4, 3, 0.01), ((6, 6, 6), 7, 4, 0.004))):
+        m = meshgen.box_mesh(*dims, hi=(1.0, 0.9, 0.8), p=p, q=q, order="morton")
+        meshgen.random_materials(m, 50 + k, 60 + k)
+        s = stm.Slab(m)
+        U = torch.from_numpy(meshgen.random_coeffs(m, 70 + k)).cuda()
+        R_ref = torch.empty(s.n_test, dtype=torch.float64, device="cuda")
+        s.residual_apply(U, R_ref, 0.0, dt)
+        torch.cuda.synchronize()
+        s.close()
+        R = torch.full_like(R_ref, float("nan"))
+        cases.append((m, p, q, dt, U, R, R_ref) + _device_inputs(m))
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for m, p, q, dt, U, R, R_ref, nbr, h, eps, mu, ne in cases:
+            rc = stm.residual_apply_noalloc(ne, p, q, dt, nbr, h, eps, mu, U, R, stream=stream.cuda_stream)
+            assert rc == stm.STM_OK
+    stream.synchronize()
+    for m, p, q, dt, U, R, R_ref, *_ in cases:
+        err = (torch.linalg.norm(R - R_ref) / torch.linalg.norm(R_ref)).item()
+        assert err < 1e-12, (p, q, err)
+
+
 def test_noalloc_rejects_oversized_request():
     import torch
 
