@@ -86,3 +86,19 @@ def test_layout_sizes():
     assert np.array_equal(np.diff(tr), 6 * (m["nk"].astype(int) * 3 + 1) * n3)
     assert np.array_equal(np.diff(te), 6 * m["nk"].astype(int) * 3 * n3)
     assert meshgen.random_coeffs(m, 1).size == tr[-1]
+
+
+def test_affine_box_mesh_is_parallelepipeds():
+    A = np.array([[1.0, 0.3, -0.2], [0.1, 0.8, 0.25], [-0.15, 0.2, 1.1]])
+    m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.8, 0.6), affine=A)
+    assert m["geometry"] == "affine"
+    X = m["vert"][m["hex"]]                      # [ne, 8, 3]
+    DF = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 4] - X[:, 0]], axis=2)  # columns
+    for v in range(8):
+        b = np.array([v & 1, (v >> 1) & 1, (v >> 2) & 1], dtype=np.float64)
+        assert np.allclose(X[:, v], X[:, 0] + DF @ b, atol=1e-14)
+    # every element is the image of the same box cell: DF = A diag(h)
+    h = np.array([1.0 / 3, 0.4, 0.3])
+    assert np.allclose(DF, (A * h)[None], atol=1e-14)
+    with pytest.raises(ValueError):
+        meshgen.box_mesh(2, affine=-np.eye(3))

@@ -246,10 +246,15 @@ def _energy_identity(m, dt=0.13, seed=11):
     return R @ piU, dE
 
 
-@pytest.mark.parametrize("case", ["brick", "aniso", "curved", "uneven_q", "uneven_p"])
+SHEAR = [[1.0, 0.3, -0.2], [0.1, 0.8, 0.25], [-0.15, 0.2, 1.1]]
+
+
+@pytest.mark.parametrize("case", ["brick", "aniso", "affine", "curved", "uneven_q", "uneven_p"])
 def test_energy_identity(case):
     if case == "brick":
         m = meshgen.box_mesh(2, p=2, q=2)
+    elif case == "affine":
+        m = meshgen.box_mesh(2, 2, 1, p=2, q=2, affine=SHEAR)
     elif case == "aniso":
         m = meshgen.box_mesh(3, 2, 1, hi=(1.0, 0.5, 0.25), p=1, q=3)
     elif case == "curved":
