@@ -128,6 +128,14 @@ typedef struct {
   int32_t zero_guess;    /* 1: GMRES starts each slab from all unknowns 0; 0 (default):
                             from u_1 = u_0, higher modes 0 (the field held constant
                             over the slab).  The converged solution is the same     */
+  int32_t no_tensor_cores; /* 1: the FP32 mass term of trilinear elements runs on the
+                            CUDA cores; 0 (default): on the tensor cores (3xTF32)
+                            for 3 <= p <= 7                                         */
+  int32_t cycles_per_launch; /* GMRES restart cycles per CUDA-graph launch of the slab
+                            solve, each followed by one host read of the solver state
+                            (<= 1: one); cycles after the stop test are skipped on
+                            the device, so a value above the cycles a slab needs runs
+                            the whole solve as one graph launch and one host read   */
 } stm_opts;
 
 typedef struct {

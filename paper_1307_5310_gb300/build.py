@@ -34,7 +34,8 @@ def _units():
     units = []
     for p in range(8):
         units.append(("residual_inst.cu", f"residual_p{p}.o", [f"-DSTM_P={p}"]))
-    for src in ("krylov.cu", "stm_capi.cu", "stm_noalloc.cu", "load.cu", "curved.cu", "hp.cu", "server.cu"):
+    for src in ("krylov.cu", "stm_capi.cu", "stm_noalloc.cu", "load.cu", "curved.cu", "curved_tc.cu", "hp.cu",
+                "server.cu"):
         units.append((src, src.replace(".cu", ".o"), []))
     return units
 

@@ -35,6 +35,13 @@ int launch_mass_curved(int P, int Q, const T* um, int64_t um_es, int64_t um_cs, 
                        int64_t u0_cs, const T* Gw, const T* eps, const T* mu, const CurvedTables& ct, int64_t ne, T* R,
                        cudaStream_t s, const int32_t* skip = nullptr);
 
+// The same FP32 mass term on the tensor cores (tcgen05.mma kind::tf32 with 3xTF32 split
+// products, accumulators in tensor memory) for 3 <= P <= 7; cudaErrorInvalidValue for other
+// degrees.  *err is set to 1 if a bounded wait of the kernel ran out (R is then incomplete).
+int launch_mass_curved_tc(int P, int Q, const float* um, int64_t um_es, int64_t um_cs, const float* u0, int64_t u0_es,
+                          int64_t u0_cs, const float* Gw, const float* eps, const float* mu, const CurvedTables& ct,
+                          int64_t ne, float* R, cudaStream_t s, const int32_t* skip, int* err);
+
 // z[e][f][c][i][s] = sum_d Pinv[e][f][c][d] v[e][f][d][i][s]   (add = false), or x += that (add = true);
 // with k > 0, v is the combination sum_{j<k} y[j] V[j] (ldv apart).
 // With skip non-null nothing is done while *skip is set; with st non-null k and y come

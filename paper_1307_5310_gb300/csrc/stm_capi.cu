@@ -254,6 +254,7 @@ struct stm_ctx {
   float* Pinv32 = nullptr;
   double* mass3_64 = nullptr;  // general affine elements: [ne][2][6] mat * G (constant metric)
   float* mass3_32 = nullptr;
+  int* tc_err = nullptr;       // trilinear meshes: set by the tensor-core mass kernel if a wait ran out
   double* el = nullptr;      // per-element energies (curved)
   CurvedTables ct{};
   // load vector L (Gaussian currents, boundary data g), cached per (t0, dt)
@@ -275,7 +276,7 @@ struct stm_ctx {
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
   };
-  std::map<std::tuple<int, double, const void*>, CycleGraph> cycle_graphs;
+  std::map<std::tuple<int, double, const void*, int>, CycleGraph> cycle_graphs;
   // instrumentation: kernel launch count, optional per-launch event timing
   int64_t launches = 0;
   bool profiling = false;
@@ -549,9 +550,18 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   }
   if (c->geometry == STM_GEOM_TRILINEAR) {
     // curved: the metric-dependent mass term goes first into R; the residual kernels add the rest
-    const int em = launch_mass_curved<T>(c->P, c->Q, a.um, a.um_es, a.um_cs, a.u0, a.u0_es, a.u0_cs,
-                                         curved_ptr<T>(c, 0), curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne,
-                                         R, c->stream, skip);
+    int em;
+    if constexpr (sizeof(T) == 4) {
+      if (!c->opts.no_tensor_cores && c->P >= 3 && c->tc_err)
+        em = launch_mass_curved_tc(c->P, c->Q, a.um, a.um_es, a.um_cs, a.u0, a.u0_es, a.u0_cs, c->Gw32, c->eps32,
+                                   c->mu32, c->ct, c->ne, R, c->stream, skip, c->tc_err);
+      else
+        em = launch_mass_curved<T>(c->P, c->Q, a.um, a.um_es, a.um_cs, a.u0, a.u0_es, a.u0_cs, curved_ptr<T>(c, 0),
+                                   curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne, R, c->stream, skip);
+    } else {
+      em = launch_mass_curved<T>(c->P, c->Q, a.um, a.um_es, a.um_cs, a.u0, a.u0_es, a.u0_cs, curved_ptr<T>(c, 0),
+                                 curved_ptr<T>(c, 1), curved_ptr<T>(c, 2), c->ct, c->ne, R, c->stream, skip);
+    }
     c->launches += 1;
     if (em) return fail(c, STM_EDEVICE, std::string("curved mass launch: ") + cudaGetErrorString((cudaError_t)em));
     a.mass = nullptr;
@@ -582,8 +592,8 @@ int linop_pre(stm_ctx* c, double dt, const T* v, T* out, const int32_t* skip = n
 }
 
 // R(U) = A U - b with mode 0 = state (FP64), modes 1..q = xin and the load b (or none).
-int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* out) {
-  return apply<double>(c, dt, xin, L_TEST, c->state, L_STATE, b, out);
+int resid64(stm_ctx* c, double dt, const double* xin, const double* b, double* out, const int32_t* skip = nullptr) {
+  return apply<double>(c, dt, xin, L_TEST, c->state, L_STATE, b, out, false, skip);
 }
 
 // l_E(v) = (J, v) over I_n x K for a current density sampled on the host (Eq.
@@ -1166,14 +1176,16 @@ int launch_cycle(stm_ctx* c, double dt, const double* b, bool mixed, int64_t ldv
   GmresState* st = c->gst;
   int rc;
   double* R64 = mixed ? c->z : c->V;
-  if ((rc = resid64(c, dt, c->x, b, R64))) return rc;
-  axpy_norm<double>(R64, R64, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream);
-  gmres_reduce(c->red_partial, st, 0, c->stream);
+  // once the slab has stopped (st->halt), this cycle's kernels are all no-ops
+  const int32_t* halt = &st->halt;
+  if ((rc = resid64(c, dt, c->x, b, R64, halt))) return rc;
+  axpy_norm<double>(R64, R64, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream, halt);
+  gmres_reduce(c->red_partial, st, 0, c->stream, halt);
   c->launches += 2;
   if (inexact) {  // GMRES then works on the weighted residual S R
-    scale_blocks<double>(c, R64, c->sw64, n);
-    axpy_norm<double>(R64, R64, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream);
-    gmres_reduce(c->red_partial, st, 1, c->stream);
+    scale_blocks<double>(c, R64, c->sw64, n, halt);
+    axpy_norm<double>(R64, R64, 0, 0, Coef16{}, n, c->red_partial, nullptr, c->stream, halt);
+    gmres_reduce(c->red_partial, st, 1, c->stream, halt);
     c->launches += 2;
   }
   gmres_outer_check(st, c->stream);
@@ -1213,12 +1225,18 @@ void drop_cycle_graphs(stm_ctx* c) {
   c->cycle_graphs.clear();
 }
 
-// Runs one restart cycle: captured once per (precision, dt, load pointer) into a CUDA graph
-// on the capture stream and replayed on the context stream (directly launched while
-// profiling, whose events are recorded around individual kernels).
-int run_cycle(stm_ctx* c, double dt, const double* b, bool mixed, int64_t ldv) {
-  if (c->profiling) return launch_cycle(c, dt, b, mixed, ldv);
-  const auto key = std::make_tuple(mixed ? 1 : 0, dt, (const void*)b);
+// Runs `cycles` restart cycles: captured once per (precision, dt, load pointer, cycles) into a
+// CUDA graph on the capture stream and replayed on the context stream (directly launched
+// while profiling, whose events are recorded around individual kernels).
+int run_cycles(stm_ctx* c, double dt, const double* b, bool mixed, int64_t ldv, int cycles) {
+  if (c->profiling) {
+    for (int k = 0; k < cycles; ++k) {
+      const int rc = launch_cycle(c, dt, b, mixed, ldv);
+      if (rc) return rc;
+    }
+    return STM_OK;
+  }
+  const auto key = std::make_tuple(mixed ? 1 : 0, dt, (const void*)b, cycles);
   auto it = c->cycle_graphs.find(key);
   if (it == c->cycle_graphs.end()) {
     if (!c->cap_stream) STM_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -1227,7 +1245,8 @@ int run_cycle(stm_ctx* c, double dt, const double* b, bool mixed, int64_t ldv) {
     cudaStream_t orig = c->stream;
     STM_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
     c->stream = c->cap_stream;
-    const int rc = launch_cycle(c, dt, b, mixed, ldv);
+    int rc = STM_OK;
+    for (int k = 0; k < cycles && !rc; ++k) rc = launch_cycle(c, dt, b, mixed, ldv);
     c->stream = orig;
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
@@ -1605,6 +1624,10 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
       int bad_h = 0;
       cudaMemcpy(&bad_h, bad_d, sizeof(int), cudaMemcpyDeviceToHost);
       cudaFree(bad_d);
+      if (!affine) {
+        ok = cudaMalloc(&c->tc_err, sizeof(int)) == cudaSuccess;
+        if (ok) cudaMemset(c->tc_err, 0, sizeof(int));
+      }
       if (affine) {
         std::vector<float> m3(c->h_mass3.begin(), c->h_mass3.end());
         ok = cudaMalloc(&c->mass3_64, c->h_mass3.size() * sizeof(double)) == cudaSuccess &&
@@ -1771,7 +1794,7 @@ int32_t stm_destroy(stm_ctx* c) {
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
                   c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
                   c->sw64,    c->sw32,    c->kap64,  c->kap32, c->nkl,    c->tmat64, c->tmat32,
-                  c->mass3_64, c->mass3_32};
+                  c->mass3_64, c->mass3_32, c->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -2193,9 +2216,10 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
   // restart cycles, each one launch sequence (a replayed CUDA graph unless profiling) and one
   // read of the device state: the stop test, the iteration count and the error status
   bool done = false;
-  const int max_cycles = c->opts.max_it + 2;  // every cycle but the last makes >= 1 iteration
-  for (int cyc = 0; cyc < max_cycles; ++cyc) {
-    if ((rc = run_cycle(c, dt, b, mixed, ldv))) return rc;
+  const int per = c->profiling ? 1 : std::max(1, (int)c->opts.cycles_per_launch);
+  const int max_launches = c->opts.max_it + 2;  // every cycle but the last makes >= 1 iteration
+  for (int cyc = 0; cyc < max_launches; ++cyc) {
+    if ((rc = run_cycles(c, dt, b, mixed, ldv, per))) return rc;
     STM_CK(cudaMemcpyAsync(c->h_gst, st, sizeof(GmresState), cudaMemcpyDeviceToHost, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
     const GmresState& h = *c->h_gst;
@@ -2207,11 +2231,16 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
       c->it_marks.clear();
     }
     if (h.status < 0) return fail(c, h.status, "non-finite value in the slab solve");
-    if (h.outer_done) {
-      done = true;
+    if (h.halt) {  // the stop test held, or no progress is possible (iteration cap, zero residual)
+      done = h.outer_done != 0;
       break;
     }
-    if (h.k == 0) break;  // no progress possible: iteration cap or a zero start vector
+  }
+  if (c->tc_err) {  // a bounded wait of the tensor-core mass kernel ran out: no valid result
+    int h_err = 0;
+    STM_CK(cudaMemcpyAsync(&h_err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+    if (h_err) return fail(c, STM_ETIMEOUT, "tensor-core mass kernel: a bounded wait ran out");
   }
   if (c->hp) extract_end_hp(c->state, c->x, c->off_test, c->off_state, c->pq, c->ne, c->stream);
   else k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);

@@ -61,7 +61,7 @@ class stm_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("restart", C.c_int32), ("max_it", C.c_int32),
                 ("deterministic", C.c_int32), ("stream", C.c_int64), ("reorth", C.c_int32), ("graph", C.c_int32),
                 ("eta_tol", C.c_double), ("t_final", C.c_double), ("c_diss", C.c_double),
-                ("zero_guess", C.c_int32)]
+                ("zero_guess", C.c_int32), ("no_tensor_cores", C.c_int32), ("cycles_per_launch", C.c_int32)]
 
 
 class stm_solve_report(C.Structure):
@@ -225,7 +225,7 @@ class Slab:
 
     def __init__(self, mesh: dict, precision=STM_FP64, tol=1e-12, restart=10, max_it=500,
                  deterministic=True, stream=None, reorth=True, graph=True, eta_tol=0.0, t_final=0.0,
-                 c_diss=0.0, zero_guess=False):
+                 c_diss=0.0, zero_guess=False, tensor_cores=True, cycles_per_launch=1):
         L = lib()
         self._keep = {}
         ne = mesh["hex"].shape[0]
@@ -258,7 +258,8 @@ class Slab:
 
             stream = torch.cuda.current_stream().cuda_stream
         o = stm_opts(precision, tol, restart, max_it, 1 if deterministic else 0, int(stream), 1 if reorth else 0,
-                     1 if graph else 0, eta_tol, t_final, c_diss, 1 if zero_guess else 0)
+                     1 if graph else 0, eta_tol, t_final, c_diss, 1 if zero_guess else 0,
+                     0 if tensor_cores else 1, cycles_per_launch)
         h = C.c_void_p()
         rc = L.stm_create(C.byref(h), C.byref(m), C.byref(o))
         if rc != STM_OK:

@@ -63,6 +63,42 @@ def test_residual_curved_fp32(stm):
     assert rel(R, Ro) < 2e-6
 
 
+@pytest.mark.parametrize("p,q,dims", [(3, 2, (3, 2, 2)), (4, 1, (2, 2, 1)), (5, 4, (2, 1, 1)), (6, 3, (2, 1, 1)),
+                                      (7, 6, (2, 1, 1))])
+def test_residual_curved_fp32_tensor_cores(stm, p, q, dims):
+    """FP32 curved mass on the tensor cores (tcgen05, 3xTF32) against the oracle and against
+    the CUDA-core FP32 kernel, both at FP32 accuracy."""
+    m = meshgen.box_mesh(*dims, p=p, q=q, perturb=0.4, order="morton")
+    meshgen.random_materials(m, 4, 5)
+    U32 = meshgen.random_coeffs(m, 6).astype(np.float32)
+    Ro = stdg.Oracle(m).residual(U32.astype(np.float64), 0.0, 0.05)
+    out = {}
+    for tc in (True, False):
+        s = stm.Slab(m, tensor_cores=tc)
+        R = np.empty(s.n_test, np.float32)
+        s.residual_apply(U32, R, 0.0, 0.05, prec=stm.STM_FP32)
+        out[tc] = R
+        s.close()
+    assert rel(out[True], Ro) < 2e-6
+    assert rel(out[True], out[False]) < 2e-6
+
+
+def test_slab_solve_curved_mixed_tensor_cores(stm):
+    """Mixed-precision slab solve on trilinear hexes with p = 3 (FP32 inner mass on the tensor
+    cores) against the oracle's direct solve at 1e-9."""
+    m = meshgen.box_mesh(2, 2, 2, hi=(0.5, 0.5, 0.5), p=3, q=2, perturb=0.3)
+    meshgen.random_materials(m, 16, 17)
+    o = stdg.Oracle(m)
+    u0 = np.random.Generator(np.random.PCG64(18)).uniform(-1, 1, o.ne * 6 * 64)
+    dt = 0.25 / 7
+    uo = o.end_state(o.slab_solve(u0, 0.0, dt))
+    s = stm.Slab(m, precision=stm.STM_MIXED, tol=1e-11, max_it=4000)
+    s.set_state(u0)
+    rc, rep = s.slab_solve(dt)
+    assert rc == stm.STM_OK, rep
+    assert rel(s.get_state()[0], uo) < 1e-9
+
+
 def test_energy_curved(stm):
     m = meshgen.box_mesh(3, 2, 2, p=3, q=1, perturb=0.4)
     meshgen.random_materials(m, 7, 8)
