@@ -300,6 +300,7 @@ __global__ void k_gm_slab_start(GmresState* st, double tol, int max_it, int inex
   st->cycles = 0;
   st->status = 0;
   st->outer_done = 0;
+  st->halt = 0;
   st->skip = 0;
   st->skip_reo = 1;
   st->k = 0;
@@ -311,12 +312,17 @@ __global__ void k_gm_slab_start(GmresState* st, double tol, int max_it, int inex
 __global__ void k_gm_outer_check(GmresState* st) {
   st->k = 0;
   st->skip_reo = 1;
+  if (st->halt) {
+    st->skip = 1;
+    return;
+  }
   const double beta = sqrt(st->red[0]);
   const double ref = st->ref;
   st->rel = ref > 0 ? beta / ref : beta;
   if (!isfinite(st->rel)) {
     st->status = -5;  // STM_ENAN
     st->skip = 1;
+    st->halt = 1;
     return;
   }
   bool done;
@@ -328,6 +334,7 @@ __global__ void k_gm_outer_check(GmresState* st) {
   }
   if (done) st->outer_done = 1;
   st->skip = (done || st->iters >= st->max_it || beta == 0.0) ? 1 : 0;
+  st->halt = st->skip;
 }
 
 __global__ void k_gm_cycle_init(GmresState* st, int slot_start, double floor_rel) {
@@ -335,6 +342,7 @@ __global__ void k_gm_cycle_init(GmresState* st, int slot_start, double floor_rel
   const double b0 = sqrt(st->red[slot_start]);
   if (!(b0 > 0.0)) {
     st->skip = 1;
+    st->halt = 1;
     return;
   }
   st->cycles += 1;
@@ -386,6 +394,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_gm_givens(const double* __rest
   if (!isfinite(after) || !isfinite(st->before)) {
     st->status = -5;  // STM_ENAN
     st->skip = 1;
+    st->halt = 1;
     return;
   }
   const double nw = sqrt(after);

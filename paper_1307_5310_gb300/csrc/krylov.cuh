@@ -44,6 +44,8 @@ struct GmresState {
   int32_t outer_done;             // 1: the slab's stop test holds
   int32_t inexact;                // 1: stop on the weighted norm (eta_it), 0: on rel
   int32_t cycles;                 // restart cycles started
+  int32_t halt;                   // 1: the slab solve has stopped (stop test, cap, zero residual or
+                                  //    error); every later kernel of the slab is skipped
 };
 
 // out[i] = sum_n w[n] V[i*ldv + n] for i < k (k <= 15), and out[k] = sum_n w[n]^2

@@ -196,41 +196,52 @@ __global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3]
+  // A P^{-1} v (pinv set, no slab start): the inverse block-diagonal mass scales every unknown
+  // mode of a (field, component) block, so it is folded into that block's B coefficients once
+  // per element (6 (Q+1) Q products) instead of one multiply per coefficient
+  __shared__ T Bsc[6][kMaxQ][kMaxQ + 1];
   const int nk = TR ? A.nk : 1, QE = TR ? nk * Q : Q;
   for (int64_t blk = blockIdx.x; blk < A.n_elem; blk += gridDim.x) {
     const ElemAddr<T, P, Q, HP, TR> ad(A, blk);
+    if (A.pinv) {
+      for (int it = threadIdx.x; it < 6 * Q * (Q + 1); it += blockDim.x) {
+        const int fc = it / (Q * (Q + 1)), r = it - fc * Q * (Q + 1), i = r / (Q + 1), m = r - i * (Q + 1);
+        Bsc[fc][i][m] = A.tb.B[i][m] * A.pinv[ad.e * 6 + fc];
+      }
+      __syncthreads();
+    }
 #pragma unroll 1
     for (int k = 0; k < nk; ++k) {  // temporal sub-intervals (Sec. 2.2)
-    for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
-      const int fc = it / N3, s = it - fc * N3;
-      T u[Q + 1];
-      // mode 0 of sub-interval k: the slab start, else mode 1 (end value) of sub-interval k - 1
-      if (k == 0) u[0] = A.u0 ? A.u0[ad.u0 + fc * ad.u0_cs + s] : T(0);
-      else u[0] = A.um[ad.um + fc * ad.um_cs + (k - 1) * Q * N3 + s];
+    auto contract = [&](auto prec) {
+      constexpr bool PRE = decltype(prec)::value;
+      for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
+        const int fc = it / N3, s = it - fc * N3;
+        T u[Q + 1];
+        // mode 0 of sub-interval k: the slab start, else mode 1 (end value) of sub-interval k - 1
+        if (k == 0) u[0] = (!PRE && A.u0) ? A.u0[ad.u0 + fc * ad.u0_cs + s] : T(0);
+        else u[0] = A.um[ad.um + fc * ad.um_cs + (k - 1) * Q * N3 + s];
 #pragma unroll
-      for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (k * Q + m - 1) * N3 + s];
-      if (A.pinv) {  // A P^{-1} v: the unknown modes scaled by the inverse block-diagonal mass on load
-        const T sc = A.pinv[ad.e * 6 + fc];
-        if (k > 0) u[0] *= sc;
+        for (int m = 1; m <= Q; ++m) u[m] = A.um[ad.um + fc * ad.um_cs + (k * Q + m - 1) * N3 + s];
+        T* yg = A.y + ad.R + fc * (int64_t)(QE * N3) + k * Q * N3 + s;
 #pragma unroll
-        for (int m = 1; m <= Q; ++m) u[m] *= sc;
-      }
-      T* yg = A.y + ad.R + fc * (int64_t)(QE * N3) + k * Q * N3 + s;
+        for (int i = 0; i < Q; ++i) {
+          T acc = T(0);
+          bool first = true;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        T acc = T(0);
-        bool first = true;
-#pragma unroll
-        for (int m = 0; m <= Q; ++m) {
-          if (b_nz(i, m)) {
-            acc = first ? A.tb.B[i][m] * u[m] : fma(A.tb.B[i][m], u[m], acc);
-            first = false;
+          for (int m = 0; m <= Q; ++m) {
+            if (b_nz(i, m)) {
+              const T bb = PRE ? Bsc[fc][i][m] : A.tb.B[i][m];
+              acc = first ? bb * u[m] : fma(bb, u[m], acc);
+              first = false;
+            }
           }
+          ys[(fc * Q + i) * N3 + s] = acc;
+          yg[i * N3] = acc;
         }
-        ys[(fc * Q + i) * N3 + s] = acc;
-        yg[i * N3] = acc;
       }
-    }
+    };
+    if (A.pinv) contract(std::true_type{});
+    else contract(std::false_type{});
     __syncthreads();
     // traces: items (f, a, bi, i, t)
     for (int it = threadIdx.x; it < 12 * Q * N2; it += blockDim.x) {
@@ -579,18 +590,41 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
   }
 }
 
+// Line of the N^3 tensor along the compile-time axis A at transverse position t.
+template <int N, int A>
+__device__ __forceinline__ int line_base(int t) {
+  if constexpr (A == 0) return t * N;
+  else if constexpr (A == 1) return (t / N) * N * N + (t % N);
+  else return t;
+}
+template <int N, int A>
+constexpr int line_stride() {
+  return A == 0 ? 1 : (A == 1 ? N : N * N);
+}
+
+// Calls f(std::integral_constant<int, a>) for a runtime, warp-uniform axis a.
+template <typename F>
+__device__ __forceinline__ void with_axis(int a, F&& f) {
+  if (a == 0) f(std::integral_constant<int, 0>{});
+  else if (a == 1) f(std::integral_constant<int, 1>{});
+  else f(std::integral_constant<int, 2>{});
+}
+
 // Single-pass variant (used for FP32, where the kernel is bound by memory
-// traffic, not arithmetic): one CTA per element reads its own coefficients
-// once, recomputes the six neighbour face traces from the neighbours'
-// coefficients (face neighbours sit close in memory, so these reads mostly hit
-// L2), forms its own traces in registers inside the line loop, and writes R.
-// No y or trace scratch goes through HBM.
+// traffic, not arithmetic): one CTA per element at a time reads its own
+// coefficients once, recomputes the six neighbour face traces from the
+// neighbours' coefficients (face neighbours sit close in memory, so these
+// reads mostly hit L2), forms its own traces in registers inside the line
+// loop, and writes R.  No y or trace scratch goes through HBM.
 //
 // Work split: (a) all threads form y = B u and the mass rows of the element in
-// shared memory, (b) all threads form the neighbour traces, then (c) every warp
-// owns whole residual planes (field, component, test mode): it runs both line
-// passes of a plane (one per derivative axis) with only warp synchronisation
-// and stores the finished plane to HBM.  Two CTA barriers per element.
+// shared memory; (b) one warp per (face, field, tangential component) forms
+// the neighbour's trace on that face; (c) every warp owns whole residual
+// planes (field, component, test mode): it runs both line passes of a plane
+// (one per derivative axis) with only warp synchronisation and stores the
+// finished plane to HBM.  Two CTA barriers per element.  Line axes are
+// dispatched warp-uniformly to compile-time strides, so every load of a line
+// has an immediate offset.
 template <typename T, int P, int Q, bool PRE>
 __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
   if (A.skip && *A.skip) return;
@@ -609,16 +643,19 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
     // (a) own coefficients: temporal contraction and the mass term
     for (int it = threadIdx.x; it < 6 * N3; it += blockDim.x) {
       const int fc = it / N3, s = it - fc * N3;
+      const T* up = ume + fc * um_cs + s;
       T u[Q + 1], v[Q];
       u[0] = u0e ? u0e[fc * u0_cs + s] : T(0);
 #pragma unroll
-      for (int m = 1; m <= Q; ++m) u[m] = v[m - 1] = ume[fc * um_cs + (m - 1) * N3 + s];
+      for (int m = 1; m <= Q; ++m) u[m] = v[m - 1] = up[(m - 1) * N3];
       if constexpr (PRE) {
         const T sc = A.pinv[e * 6 + fc];
 #pragma unroll
         for (int m = 1; m <= Q; ++m) u[m] *= sc;
       }
       const T mc = A.mass ? A.mass[e * 6 + fc] : T(0);
+      T* yo = ys + fc * Q * N3 + s;
+      T* ro = Rs + fc * Q * N3 + s;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         T acc = T(0);
@@ -630,8 +667,8 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
             first = false;
           }
         }
-        const int o = (fc * Q + i) * N3 + s;
-        ys[o] = acc;
+        yo[i * N3] = acc;
+        const int64_t o = re + (fc * Q + i) * N3 + s;
         T w;
         if (A.mass) {
           // with PRE the mass block times P^{-1} is the identity: the term is v itself
@@ -653,60 +690,61 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
             w = fma(-mr[2], u0f[2 * u0_cs], w);
           }
         } else {
-          w = A.R[re + o];  // curved elements: the mass term is already in R
+          w = A.R[o];  // curved elements: the mass term is already in R
         }
-        if (A.b) w -= A.b[re + o];
-        Rs[o] = w;
+        if (A.b) w -= A.b[o];
+        ro[i * N3] = w;
       }
     }
-    // (b) neighbour traces on the shared faces: items (face, field, comp, t)
-    for (int it = threadIdx.x; it < 24 * N2; it += blockDim.x) {
-      const int t = it % N2, r = it / N2;
-      const int bi = r & 1, fld = (r >> 1) & 1, face = r >> 2;
+    // (b) neighbour traces: one warp per (face, field, tangential component), lanes over t
+    for (int task = warp; task < 24; task += nwarp) {
+      const int bi = task & 1, fld = (task >> 1) & 1, face = task >> 2;
       const int a = face >> 1, side = face & 1;
       const int64_t en = nb[face];
-      if (en < 0) continue;
+      if (en < 0) continue;  // warp-uniform
       const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
-      int base, stride;
-      line_geom<N>(a, t, base, stride);
-      // the neighbour across face (a, side) meets it with its face (a, 1 - side):
-      // L_j(0) = (-1)^j L_j(1) for side 1, L_j(1) for side 0
-      const T* un = A.um + en * A.um_es + (fld * 3 + b) * um_cs + base;
-      T tu[Q + 1];
-      tu[0] = T(0);
-      if (A.u0) {
-        const T* u0n = A.u0 + en * A.u0_es + (fld * 3 + b) * u0_cs + base;
-        T ev = T(0), od = T(0);
+      const T* un = A.um + en * A.um_es + (fld * 3 + b) * um_cs;
+      const T* u0n = A.u0 ? A.u0 + en * A.u0_es + (fld * 3 + b) * u0_cs : nullptr;
+      const T sc = PRE ? A.pinv[en * 6 + fld * 3 + b] : T(1);
+      T* nto = nt + (task * Q) * N2;
+      with_axis(a, [&](auto ac) {
+        constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
+        for (int t = lane; t < N2; t += 32) {
+          const int base = line_base<N, AX>(t);
+          // the neighbour across face (a, side) meets it with its face (a, 1 - side):
+          // L_j(0) = (-1)^j L_j(1) for side 1, L_j(1) for side 0
+          T tu[Q + 1];
+          tu[0] = T(0);
+          if (u0n) {
+            T ev = T(0), od = T(0);
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          if (j & 1) od = fma(A.tb.lv[j], u0n[j * stride], od);
-          else ev = fma(A.tb.lv[j], u0n[j * stride], ev);
+            for (int j = 0; j < N; ++j) {
+              if (j & 1) od = fma(A.tb.lv[j], u0n[base + j * ST], od);
+              else ev = fma(A.tb.lv[j], u0n[base + j * ST], ev);
+            }
+            tu[0] = side ? ev - od : ev + od;
+          }
+          const T* ul = un + base;
+#pragma unroll
+          for (int m = 1; m <= Q; ++m) {
+            T ev = T(0), od = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              if (j & 1) od = fma(A.tb.lv[j], ul[(m - 1) * N3 + j * ST], od);
+              else ev = fma(A.tb.lv[j], ul[(m - 1) * N3 + j * ST], ev);
+            }
+            tu[m] = (side ? ev - od : ev + od) * sc;
+          }
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m <= Q; ++m)
+              if (b_nz(i, m)) acc = fma(A.tb.B[i][m], tu[m], acc);
+            nto[i * N2 + t] = acc;
+          }
         }
-        tu[0] = side ? ev - od : ev + od;
-      }
-#pragma unroll
-      for (int m = 1; m <= Q; ++m) {
-        T ev = T(0), od = T(0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          if (j & 1) od = fma(A.tb.lv[j], un[(m - 1) * N3 + j * stride], od);
-          else ev = fma(A.tb.lv[j], un[(m - 1) * N3 + j * stride], ev);
-        }
-        tu[m] = side ? ev - od : ev + od;
-      }
-      if constexpr (PRE) {
-        const T sc = A.pinv[en * 6 + fld * 3 + b];
-#pragma unroll
-        for (int m = 1; m <= Q; ++m) tu[m] *= sc;
-      }
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m <= Q; ++m)
-          if (b_nz(i, m)) acc = fma(A.tb.B[i][m], tu[m], acc);
-        nt[(r * Q + i) * N2 + t] = acc;
-      }
+      });
     }
     __syncthreads();
     // (c) residual planes (f, c, i), one warp each at a time
@@ -725,41 +763,46 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
         const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
         const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q + i) * N2;
         const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q + i) * N2;
-        for (int t = lane; t < N2; t += 32) {
-          int base, stride;
-          line_geom<N>(a, t, base, stride);
-          T yv[N];
-          T ev = T(0), od = T(0);
+        auto lines = [&](auto ac, auto negc) {
+          constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
+          constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
+          for (int t = lane; t < N2; t += 32) {
+            const int base = line_base<N, AX>(t);
+            const T* yl = yb + base;
+            T yv[N];
+            T ev = T(0), od = T(0);
 #pragma unroll
-          for (int j = 0; j < N; ++j) {
-            yv[j] = yb[base + j * stride];
-            if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
-            else ev = fma(A.tb.lv[j], yv[j], ev);
-          }
-          const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
-          const T jp = hasp ? xp - ntp[t] : ((fp == 0) ? xp + xp : T(0));
-          const T jm = hasm ? xm - ntm[t] : ((fp == 0) ? xm + xm : T(0));
-          const T sp = jp + jm, dm = jp - jm;
-          T* Rl = Rp + base;
-          auto body = [&](auto negc) {
-            constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
+            for (int j = 0; j < N; ++j) {
+              yv[j] = yl[j * ST];
+              if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
+              else ev = fma(A.tb.lv[j], yv[j], ev);
+            }
+            const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
+            // other side: neighbour trace, or the PEC mirror (E: -own, H: +own)
+            const T op = hasp ? ntp[t] : ((fp == 0) ? neg_bits(xp) : xp);
+            const T om = hasm ? ntm[t] : ((fp == 0) ? neg_bits(xm) : xm);
+            const T jp = xp - op, jm = xm - om;
+            const T sp = jp + jm, dm = jp - jm;
             // flux lift folded into the curl operand as in k_apply
             constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
             if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
             if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+            T* Rl = Rp + base;
 #pragma unroll
             for (int al = 0; al < N; ++al) {
-              T r2 = Rl[al * stride];
+              T r2 = Rl[al * ST];
               if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
 #pragma unroll
               for (int be = 0; be < N; ++be)
                 if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
-              Rl[al * stride] = r2;
+              Rl[al * ST] = r2;
             }
-          };
-          if (neg) body(std::true_type{});
-          else body(std::false_type{});
-        }
+          }
+        };
+        with_axis(a, [&](auto ac) {
+          if (neg) lines(ac, std::true_type{});
+          else lines(ac, std::false_type{});
+        });
         __syncwarp();
       }
       T* Rg = A.R + re + pl * N3;

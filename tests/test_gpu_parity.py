@@ -115,6 +115,34 @@ def test_slab_solve_plain_config(stm):
     assert rel(ug, u) < 1e-12
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_slab_solve_one_graph_launch(stm, precision):
+    """The plain configuration (4^3 PEC cavity, p = 2, q = 1) with the whole slab solve captured
+    as one CUDA graph of 16 restart cycles (cycles after the stop test are skipped on the
+    device; one host read per slab): the same result as cycle-by-cycle launches and the
+    oracle's direct solves."""
+    m = meshgen.box_mesh(4, p=2, q=1)
+    o = stdg.Oracle(m)
+    dt = 0.05
+    u = o.project(_cavity, None)
+    A_b = o.assemble(0.0, dt)
+    prec = stm.STM_FP64 if precision == "fp64" else stm.STM_MIXED
+    tol = 1e-14 if precision == "fp64" else 1e-11
+    s1 = stm.Slab(m, precision=prec, tol=tol, restart=10, max_it=2000, cycles_per_launch=16)
+    s2 = stm.Slab(m, precision=prec, tol=tol, restart=10, max_it=2000)
+    s1.set_initial(_cavity, None)
+    s2.set_initial(_cavity, None)
+    for n in range(5):
+        u = o.end_state(o.slab_solve(u, n * dt, dt, A_b=A_b))
+        rc1, rep1 = s1.slab_solve(dt)
+        rc2, rep2 = s2.slab_solve(dt)
+        assert rc1 == stm.STM_OK and rc2 == stm.STM_OK, (rep1, rep2)
+        assert rep1["restarts"] < 16 and rep1["iterations"] == rep2["iterations"]
+    u1, u2 = s1.get_state()[0], s2.get_state()[0]
+    assert np.array_equal(u1, u2)
+    assert rel(u1, u) < (1e-12 if precision == "fp64" else 1e-9)
+
+
 @pytest.mark.parametrize("q", [2, 3])
 def test_slab_solve_higher_q(stm, q):
     m = meshgen.box_mesh(2, 3, 2, hi=(0.5, 0.75, 0.5), p=2, q=q)
