@@ -308,11 +308,9 @@ int mass_pq(const T* um, int64_t um_es, int64_t um_cs, const T* u0, int64_t u0_e
   once_per_device(configured_devices, [&] {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_mass_curved<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   });
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // grid-stride over elements, at most 16 CTAs per SM (a skipped launch costs one wave)
-  const int grid = (int)(ne < 16LL * sms ? ne : 16LL * sms);
+  // grid-stride over elements, one wave of co-resident CTAs (a skipped launch costs one wave)
+  static std::atomic<int> cap[64];
+  const int grid = wave_grid(k_mass_curved<T, P, Q>, 256, sm, ne, cap);
   k_mass_curved<T, P, Q><<<grid, 256, sm, s>>>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, ctab<T>(ct), ne, R,
                                                 skip);
   return (int)cudaGetLastError();

@@ -26,10 +26,12 @@ __global__ void __launch_bounds__(256) k_load_gauss(const double* __restrict__ X
   __shared__ double f0[3][NQ3];
   __shared__ double f1[3][NQ * NQ * N];
   __shared__ double f2[3][NQ * N * N];
-  const int Q = gp.Q;
-  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+  const int Q = gp.Q, QE = gp.elist ? gp.NK * Q : Q;
+  for (int64_t blk = blockIdx.x; blk < ne; blk += gridDim.x) {
+    const int64_t e = gp.elist ? gp.elist[blk] : blk;
     if (threadIdx.x < 24) X8[threadIdx.x] = X8g[e * 24 + threadIdx.x];
-    double* be = b + e * (int64_t)(6 * Q * N3);  // E rows of element e (this CTA owns them)
+    // E rows of element e (this CTA owns them)
+    double* be = b + (gp.elist ? gp.off_test[e] : e * (int64_t)(6 * Q * N3));
     __syncthreads();
     for (int k = 0; k < gp.n_src; ++k) {
       // values at the quadrature points
@@ -87,7 +89,12 @@ __global__ void __launch_bounds__(256) k_load_gauss(const double* __restrict__ X
         const int j = sidx % N, kk = (sidx / N) % N, l = sidx / (N * N);
         double s = 0.0;
         for (int gz = 0; gz < NQ; ++gz) s += f2[c][(gz * N + kk) * N + j] * gp.Lq[l][gz];
-        for (int i = 0; i < Q; ++i) be[(c * Q + i) * N3 + sidx] += gp.tf[k][i] * s;
+        if (gp.elist) {  // every temporal test function of every sub-interval
+          for (int kk = 0; kk < gp.NK; ++kk)
+            for (int i = 0; i < Q; ++i) be[(c * QE + kk * Q + i) * N3 + sidx] += gp.tfk[k][kk][i] * s;
+        } else {
+          for (int i = 0; i < Q; ++i) be[(c * Q + i) * N3 + sidx] += gp.tf[k][i] * s;
+        }
       }
       __syncthreads();
     }

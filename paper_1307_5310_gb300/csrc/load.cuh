@@ -19,6 +19,13 @@ struct GaussParams {
   double inv2sx2[kMaxSrc];    // 1 / (2 sigma_x^2)
   double amp[kMaxSrc];
   double tf[kMaxSrc][kMaxQ];  // dt sum_tau w_tau L_i(xi_tau) exp(-(t - t_k)^2 / (2 sigma_t^2))
+  // uneven degrees / local refinement in time: the same factors per sub-interval kk of a class
+  // with N_K sub-intervals (dt / N_K each), tfk[k][kk][i]; elements of the class in elist, E
+  // rows at off_test[e] with N_K q temporal test functions (null elist: uniform mesh, tf)
+  int NK;
+  double tfk[kMaxSrc][8][kMaxQ];
+  const int32_t* elist;
+  const int64_t* off_test;
   double xq[kMaxNQ], wq[kMaxNQ];
   double Lq[kMaxN][kMaxNQ];   // L_j at the spatial Gauss points
 };

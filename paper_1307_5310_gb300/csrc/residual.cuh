@@ -46,6 +46,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -118,6 +119,32 @@ struct ApplyArgs {
   // metric G = |J| DF^{-1} DF^{-T} in the order xx, yy, zz, xy, xz, yz; mass is then null
   const T* mass3 = nullptr;
 };
+
+// Grid of a grid-stride residual kernel: at most one wave of co-resident CTAs (the
+// occupancy of this kernel, block size and shared memory on the current device), so the
+// elements divide evenly over the resident CTAs (no partial last wave) and a launch the
+// device-side GMRES control skips costs one wave.  The occupancy is cached per device.
+template <typename K>
+int wave_grid(K kernel, int block, size_t smem, int64_t count, std::atomic<int>* cache) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  const int slot = (dev >= 0 && dev < 64) ? dev : 63;
+  int cap = cache[slot].load(std::memory_order_relaxed);
+  if (cap <= 0) {
+    int per_sm = 0, sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    cap = std::max(1, per_sm) * std::max(1, sms);
+    cache[slot].store(cap, std::memory_order_relaxed);
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>(count, cap));
+}
 
 // Runs f() once per CUDA device: the first time it is called with that device current.
 template <typename F>
@@ -526,7 +553,8 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
           for (int j = 0; j < N; ++j) yv[j] = yl[j * stride];
           T* Rl = Rs + fl * FB + (c * Q + i) * N3 + base;
           // the sign s_F eps_{cab} of the line's curl and flux terms is a compile-time constant
-          // of each branch, carried by the table operands of the FMAs (no extra instruction)
+          // of each branch, carried by the table operands of the FMAs (no extra instruction);
+          // lines are ordered by sign, so only the warp at the boundary runs both branches
           auto body = [&](auto negc) {
             constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
             if (A.kap) {
@@ -618,15 +646,15 @@ __device__ __forceinline__ void with_axis(int a, F&& f) {
 // loop, and writes R.  No y or trace scratch goes through HBM.
 //
 // Work split: (a) all threads form y = B u and the mass rows of the element in
-// shared memory; (b) one warp per (face, field, tangential component) forms
-// the neighbour's trace on that face; (c) every warp owns whole residual
-// planes (field, component, test mode): it runs both line passes of a plane
-// (one per derivative axis) with only warp synchronisation and stores the
-// finished plane to HBM.  Two CTA barriers per element.  Line axes are
+// shared memory; (b) one warp per (face, field) forms the neighbour's traces on
+// that face; (c) every warp owns the residual planes of one (field, component):
+// it runs both line passes (one per derivative axis) over all temporal modes
+// with only warp synchronisation and stores them to HBM.  Two CTA barriers per
+// element.  Line axes are
 // dispatched warp-uniformly to compile-time strides, so every load of a line
 // has an immediate offset.
 template <typename T, int P, int Q, bool PRE>
-__global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
+__global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
   if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -696,17 +724,21 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
         ro[i * N3] = w;
       }
     }
-    // (b) neighbour traces: one warp per (face, field, tangential component), lanes over t
-    for (int task = warp; task < 24; task += nwarp) {
-      const int bi = task & 1, fld = (task >> 1) & 1, face = task >> 2;
+    // (b) neighbour traces: one warp per (face, field), both tangential components, lanes over t
+    for (int task = warp; task < 12; task += nwarp) {
+      const int fld = task & 1, face = task >> 1;
       const int a = face >> 1, side = face & 1;
       const int64_t en = nb[face];
       if (en < 0) continue;  // warp-uniform
+      const T* ue = A.um + en * A.um_es;
+      const T* u0e2 = A.u0 ? A.u0 + en * A.u0_es : nullptr;
+#pragma unroll 1
+      for (int bi = 0; bi < 2; ++bi) {
       const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
-      const T* un = A.um + en * A.um_es + (fld * 3 + b) * um_cs;
-      const T* u0n = A.u0 ? A.u0 + en * A.u0_es + (fld * 3 + b) * u0_cs : nullptr;
+      const T* un = ue + (fld * 3 + b) * um_cs;
+      const T* u0n = u0e2 ? u0e2 + (fld * 3 + b) * u0_cs : nullptr;
       const T sc = PRE ? A.pinv[en * 6 + fld * 3 + b] : T(1);
-      T* nto = nt + (task * Q) * N2;
+      T* nto = nt + ((task * 2 + bi) * Q) * N2;
       with_axis(a, [&](auto ac) {
         constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
         for (int t = lane; t < N2; t += 32) {
@@ -745,57 +777,61 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
           }
         }
       });
+      }
     }
     __syncthreads();
-    // (c) residual planes (f, c, i), one warp each at a time
-    for (int pl = warp; pl < 6 * Q; pl += nwarp) {
-      const int fc = pl / Q, i = pl - fc * Q;
+    // (c) residual planes: one warp per (field, component) at a time, all Q temporal test
+    //     modes of it, so the axis, sign, pointers and line geometry are set up once per pass
+    for (int fc = warp; fc < 6; fc += nwarp) {
       const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f, fp = 1 - f;
-      T* Rp = Rs + pl * N3;
+      T* Rp = Rs + fc * Q * N3;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
         const int b = 3 - c - a;
         const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
-        // sign s_F eps_{cab} of the plane's terms along a (warp-uniform)
+        // sign s_F eps_{cab} of the planes' terms along a (warp-uniform)
         const bool neg = ((f == 0) == (((a - c + 3) % 3) == 1));
-        const T* yb = ys + ((fp * 3 + b) * Q + i) * N3;
+        const T* yb = ys + (fp * 3 + b) * Q * N3;
         const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
-        const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q + i) * N2;
-        const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q + i) * N2;
+        const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q) * N2;
+        const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q) * N2;
         auto lines = [&](auto ac, auto negc) {
           constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
           constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
           for (int t = lane; t < N2; t += 32) {
             const int base = line_base<N, AX>(t);
-            const T* yl = yb + base;
-            T yv[N];
-            T ev = T(0), od = T(0);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-              yv[j] = yl[j * ST];
-              if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
-              else ev = fma(A.tb.lv[j], yv[j], ev);
-            }
-            const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
-            // other side: neighbour trace, or the PEC mirror (E: -own, H: +own)
-            const T op = hasp ? ntp[t] : ((fp == 0) ? neg_bits(xp) : xp);
-            const T om = hasm ? ntm[t] : ((fp == 0) ? neg_bits(xm) : xm);
-            const T jp = xp - op, jm = xm - om;
-            const T sp = jp + jm, dm = jp - jm;
-            // flux lift folded into the curl operand as in k_apply
-            constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
-            if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
-            if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
-            T* Rl = Rp + base;
+            for (int i = 0; i < Q; ++i) {
+              const T* yl = yb + i * N3 + base;
+              T yv[N];
+              T ev = T(0), od = T(0);
 #pragma unroll
-            for (int al = 0; al < N; ++al) {
-              T r2 = Rl[al * ST];
-              if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+              for (int j = 0; j < N; ++j) {
+                yv[j] = yl[j * ST];
+                if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
+                else ev = fma(A.tb.lv[j], yv[j], ev);
+              }
+              const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
+              // other side: neighbour trace, or the PEC mirror (E: -own, H: +own)
+              const T op = hasp ? ntp[i * N2 + t] : ((fp == 0) ? neg_bits(xp) : xp);
+              const T om = hasm ? ntm[i * N2 + t] : ((fp == 0) ? neg_bits(xm) : xm);
+              const T jp = xp - op, jm = xm - om;
+              const T sp = jp + jm, dm = jp - jm;
+              // flux lift folded into the curl operand as in k_apply
+              constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
+              if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+              if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+              T* Rl = Rp + i * N3 + base;
 #pragma unroll
-              for (int be = 0; be < N; ++be)
-                if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
-              Rl[al * ST] = r2;
+              for (int al = 0; al < N; ++al) {
+                T r2 = Rl[al * ST];
+                if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+                for (int be = 0; be < N; ++be)
+                  if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+                Rl[al * ST] = r2;
+              }
             }
           }
         };
@@ -805,8 +841,9 @@ __global__ void __launch_bounds__(256) k_fused(ApplyArgs<T> A) {
         });
         __syncwarp();
       }
-      T* Rg = A.R + re + pl * N3;
-      for (int s2 = lane; s2 < N3; s2 += 32) Rg[s2] = Rp[s2];
+      // the Q planes of (f, c) are contiguous in R
+      T* Rg = A.R + re + fc * Q * N3;
+      for (int s2 = lane; s2 < Q * N3; s2 += 32) Rg[s2] = Rp[s2];
     }
     __syncthreads();
   }
@@ -818,6 +855,14 @@ struct LaunchEvents {
   cudaEvent_t start = nullptr, mid = nullptr, stop = nullptr;
 };
 
+// Shared memory of the single-pass FP32 kernel (y and residual planes of both fields, the
+// neighbour traces), and whether it is used: at most 64 KB, so that at least three CTAs share
+// an SM; larger (p, q) run the two-kernel structure in FP32 (trace pass, then apply).
+__host__ __device__ constexpr size_t fused_smem(int P, int Q) {
+  return sizeof(float) * (2 * 6 * Q * (P + 1) * (P + 1) * (P + 1) + 24 * Q * (P + 1) * (P + 1));
+}
+__host__ __device__ constexpr bool fused_fits(int P, int Q) { return fused_smem(P, Q) <= 64 * 1024; }
+
 template <typename T, int P, int Q>
 int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const LaunchEvents& ev, int phase = 0,
                        int block = 256) {
@@ -828,47 +873,69 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   const size_t sm_fused = 2 * sm_prep + sizeof(T) * 24 * Q * N2;
   // kernel attributes are per device: set them once on every device this instantiation launches on
   static std::atomic<uint64_t> configured_devices{0};
+  // the dynamic shared-memory limit is set for every size: static shared memory (k_prep's
+  // folded coefficients, k_apply's face cache) counts against the same 48 KB default
   once_per_device(configured_devices, [&] {
-    if (sm_prep > 48 * 1024) {
-      cudaFuncSetAttribute(k_prep<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
-      cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
-      cudaFuncSetAttribute(k_prep<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
-    }
-    if (sm_apply > 47 * 1024) {  // k_apply also has a little static shared memory
-      cudaFuncSetAttribute(k_apply<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
-      cudaFuncSetAttribute(k_apply<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
-      cudaFuncSetAttribute(k_apply<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
-    }
+    cudaFuncSetAttribute(k_prep<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+    cudaFuncSetAttribute(k_prep<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+    cudaFuncSetAttribute(k_prep<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_prep);
+    cudaFuncSetAttribute(k_apply<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+    cudaFuncSetAttribute(k_apply<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
+    cudaFuncSetAttribute(k_apply<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_apply);
     if constexpr (sizeof(T) == 4) {
-      if (sm_fused > 48 * 1024) {
-        cudaFuncSetAttribute(k_fused<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
-        cudaFuncSetAttribute(k_fused<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
-      }
+      cudaFuncSetAttribute(k_fused<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
+      cudaFuncSetAttribute(k_fused<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
     }
+    cudaGetLastError();
   });
   const bool hp = args.elist != nullptr;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && fused_fits(P, Q)) {
     if (!hp && !args.kap) {
       // single pass: ev.start/ev.stop bracket k_fused (reported in the apply slot)
       if (ev.start) cudaEventRecord(ev.start, s);
       if (ev.mid) cudaEventRecord(ev.mid, s);
-      if (args.pinv) k_fused<T, P, Q, true><<<grid, block, sm_fused, s>>>(args);
-      else k_fused<T, P, Q, false><<<grid, block, sm_fused, s>>>(args);
+      // six warps: the 6 Q residual planes and the 24 neighbour-trace tasks divide evenly
+      constexpr int kFusedThreads = 192;
+      (void)block;
+      static std::atomic<int> cap_t[64], cap_f[64];
+      if (args.pinv)
+        k_fused<T, P, Q, true><<<wave_grid(k_fused<T, P, Q, true>, kFusedThreads, sm_fused, grid, cap_t),
+                                 kFusedThreads, sm_fused, s>>>(args);
+      else
+        k_fused<T, P, Q, false><<<wave_grid(k_fused<T, P, Q, false>, kFusedThreads, sm_fused, grid, cap_f),
+                                  kFusedThreads, sm_fused, s>>>(args);
       if (ev.stop) cudaEventRecord(ev.stop, s);
       return (int)cudaGetLastError();
     }
   }
+  // one-wave grids, cached per (kernel, block size: 64, 128 or 256) and device
+  static std::atomic<int> cap_p[3][3][64], cap_a[3][3][64];
+  const int bs = block <= 64 ? 0 : (block <= 128 ? 1 : 2);
   if (phase != 2) {
     if (ev.start) cudaEventRecord(ev.start, s);
-    if (hp && args.nkl) k_prep<T, P, Q, true, true><<<grid, block, sm_prep, s>>>(args);
-    else if (hp) k_prep<T, P, Q, true><<<grid, block, sm_prep, s>>>(args);
-    else k_prep<T, P, Q, false><<<grid, block, sm_prep, s>>>(args);
+    if (hp && args.nkl) {
+      auto k = k_prep<T, P, Q, true, true>;
+      k<<<wave_grid(k, block, sm_prep, grid, cap_p[0][bs]), block, sm_prep, s>>>(args);
+    } else if (hp) {
+      auto k = k_prep<T, P, Q, true>;
+      k<<<wave_grid(k, block, sm_prep, grid, cap_p[1][bs]), block, sm_prep, s>>>(args);
+    } else {
+      auto k = k_prep<T, P, Q, false>;
+      k<<<wave_grid(k, block, sm_prep, grid, cap_p[2][bs]), block, sm_prep, s>>>(args);
+    }
     if (ev.mid) cudaEventRecord(ev.mid, s);
   }
   if (phase != 1) {
-    if (hp && args.nkl) k_apply<T, P, Q, true, true><<<grid, block, sm_apply, s>>>(args);
-    else if (hp) k_apply<T, P, Q, true><<<grid, block, sm_apply, s>>>(args);
-    else k_apply<T, P, Q, false><<<grid, block, sm_apply, s>>>(args);
+    if (hp && args.nkl) {
+      auto k = k_apply<T, P, Q, true, true>;
+      k<<<wave_grid(k, block, sm_apply, grid, cap_a[0][bs]), block, sm_apply, s>>>(args);
+    } else if (hp) {
+      auto k = k_apply<T, P, Q, true>;
+      k<<<wave_grid(k, block, sm_apply, grid, cap_a[1][bs]), block, sm_apply, s>>>(args);
+    } else {
+      auto k = k_apply<T, P, Q, false>;
+      k<<<wave_grid(k, block, sm_apply, grid, cap_a[2][bs]), block, sm_apply, s>>>(args);
+    }
     if (ev.stop) cudaEventRecord(ev.stop, s);
   }
   return (int)cudaGetLastError();

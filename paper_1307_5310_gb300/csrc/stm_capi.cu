@@ -414,17 +414,25 @@ const T* kap_ptr(stm_ctx* c) {
   else return c->kap32;
 }
 
-// Grid of the residual kernels (grid-stride loops over elements): at most 16 CTAs per SM,
-// so a launch that the device-side GMRES control skips costs a single wave.
+// Whether the residual kernels of precision T use the y / trace scratch: all but the
+// single-pass FP32 kernel (uniform meshes without D_h, shared memory within fused_fits).
+template <typename T>
+bool needs_scratch(const stm_ctx* c) {
+  return sizeof(T) == 8 || c->hp || c->kap64 || !fused_fits(c->P, c->Q);
+}
+
+// Upper bound of the residual kernels' grids (grid-stride loops over elements): the launch
+// sizes each grid to one wave of co-resident CTAs (wave_grid in residual.cuh).
 int res_grid(const stm_ctx* c, int64_t count) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(count, 16LL * c->sms));
+  (void)c;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(count, 1 << 30));
 }
 
 template <typename T>
 int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R,
           bool pre = false, const int32_t* skip = nullptr) {
   T *y = nullptr, *tr = nullptr;
-  if (sizeof(T) == 8 || c->hp || c->kap64) {  // the uniform FP32 kernel is single-pass and needs no scratch
+  if (needs_scratch<T>(c)) {  // the uniform FP32 single-pass kernel needs none
     int rc = scratch<T>(c, &y, &tr);
     if (rc) return rc;
   }
@@ -512,9 +520,10 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         c->launches += 1;
         if (e) {
           if (use_graph) {
-            cudaGraph_t g;
+            cudaGraph_t g = nullptr;
             cudaStreamEndCapture(c->cap_stream, &g);
             if (g) cudaGraphDestroy(g);
+            cudaGetLastError();  // the invalidated capture leaves no error behind
           }
           return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
         }
@@ -876,25 +885,6 @@ void add_host_boundary(stm_ctx* c, double t0, double dt, std::vector<double>& hb
   }
 }
 
-// Gaussian current pulses evaluated on the host (the load path of meshes with
-// uneven degrees or time refinement), as a space-time callback over the
-// context's sources.
-void gauss_sources_host(void* user, int64_t npts, const double* xt, double* out) {
-  const stm_ctx* c = static_cast<const stm_ctx*>(user);
-  for (int64_t k = 0; k < npts; ++k) {
-    double J[3] = {0, 0, 0};
-    for (const stm_gauss_src& sr : c->srcs) {
-      double r2 = 0.0;
-      for (int i = 0; i < 3; ++i) r2 += (xt[4 * k + i] - sr.centre[i]) * (xt[4 * k + i] - sr.centre[i]);
-      const double tt = xt[4 * k + 3] - sr.t0;
-      const double a = sr.amp * std::exp(-r2 / (2.0 * sr.sigma_x * sr.sigma_x)) *
-                       std::exp(-tt * tt / (2.0 * sr.sigma_t * sr.sigma_t));
-      for (int i = 0; i < 3; ++i) J[i] += a * sr.dir[i];
-    }
-    for (int i = 0; i < 3; ++i) out[3 * k + i] = J[i];
-  }
-}
-
 // Load vector b = L on the slab (t0, t0 + dt] (Eq. bilinearform:C): Gaussian
 // currents on the device, boundary data g on the host.  Returns null when no
 // source and no boundary data are set (L = 0).  Cached per (t0, dt).
@@ -914,16 +904,67 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
       return fail(c, STM_ENOMEM, "load vector allocation failed");
     }
   }
-  if (c->hp) {  // uneven degrees or N_K: every term assembled on the host, element by element
-    std::vector<double> hb(n, 0.0);
-    if (c->jfn) add_host_current(c, t0, dt, c->jfn, c->juser, hb);
-    if (!c->srcs.empty()) add_host_current(c, t0, dt, gauss_sources_host, c, hb);
-    if (c->gfn) add_host_boundary(c, t0, dt, hb);
-    STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->hp) {
+    // uneven degrees or N_K: the host callbacks (J, g) are sampled and projected on the
+    // host per element with its own p, q and N_K; the Gaussian pulses are projected on the
+    // device, one launch per (p, q, N_K) class
+    if (c->jfn || c->gfn) {
+      std::vector<double> hb(n, 0.0);
+      if (c->jfn) add_host_current(c, t0, dt, c->jfn, c->juser, hb);
+      if (c->gfn) add_host_boundary(c, t0, dt, hb);
+      STM_CK(cudaMemcpyAsync(c->load64, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      STM_CK(cudaStreamSynchronize(c->stream));
+    } else {
+      STM_CK(cudaMemsetAsync(c->load64, 0, n * sizeof(double), c->stream));
+    }
+    for (const auto& cl : c->classes) {
+      if (c->srcs.empty()) break;
+      const int nqc = cl.P + 2, ntc = cl.Q + 2, NKc = cl.NK;
+      const double dk = dt / NKc;
+      std::vector<double> xq, wq, xt, wt;
+      gauss01(nqc, xq, wq);
+      gauss01(ntc, xt, wt);
+      GaussParams gp;
+      std::memset(&gp, 0, sizeof(gp));
+      gp.n_src = (int)c->srcs.size();
+      gp.Q = cl.Q;
+      gp.NK = NKc;
+      gp.elist = cl.elist;
+      gp.off_test = c->off_test;
+      for (int g = 0; g < nqc; ++g) {
+        gp.xq[g] = xq[g];
+        gp.wq[g] = wq[g];
+        double L[kMaxN];
+        legendre01(cl.P + 1, xq[g], L);
+        for (int j = 0; j <= cl.P; ++j) gp.Lq[j][g] = L[j];
+      }
+      for (int k = 0; k < gp.n_src; ++k) {
+        const stm_gauss_src& sr = c->srcs[k];
+        for (int i = 0; i < 3; ++i) {
+          gp.c[k][i] = sr.centre[i];
+          gp.d[k][i] = sr.dir[i];
+        }
+        gp.inv2sx2[k] = 1.0 / (2.0 * sr.sigma_x * sr.sigma_x);
+        gp.amp[k] = sr.amp;
+        for (int kk = 0; kk < NKc; ++kk)
+          for (int i = 0; i < cl.Q; ++i) {
+            double acc = 0.0;
+            for (int tq = 0; tq < ntc; ++tq) {
+              double Lt[kMaxQ];
+              legendre01(cl.Q, xt[tq], Lt);
+              const double tt = t0 + dk * (kk + xt[tq]) - sr.t0;
+              acc += wt[tq] * Lt[i] * std::exp(-tt * tt / (2.0 * sr.sigma_t * sr.sigma_t));
+            }
+            gp.tfk[k][kk][i] = dk * acc;
+          }
+      }
+      const int e = launch_load_gauss(cl.P, c->X8, cl.count, gp, c->load64, c->stream);
+      c->launches += 1;
+      if (e) return fail(c, STM_EDEVICE, std::string("load kernel: ") + cudaGetErrorString((cudaError_t)e));
+    }
     convert<float, double>(c->load32, c->load64, n, c->stream);
     c->launches += 1;
     STM_CK(cudaGetLastError());
-    STM_CK(cudaStreamSynchronize(c->stream));
     c->load_valid = true;
     c->load_t0 = t0;
     c->load_dt = dt;
@@ -2180,7 +2221,7 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
     }
     STM_CK(cudaMemsetAsync(c->gst, 0, sizeof(GmresState), c->stream));
   }
-  if (mixed && (c->hp || c->kap64)) {  // FP32 residual scratch, allocated before any capture
+  if (mixed && needs_scratch<float>(c)) {  // FP32 residual scratch, allocated before any capture
     float *y32 = nullptr, *tr32 = nullptr;
     if ((rc = scratch<float>(c, &y32, &tr32))) return rc;
   }

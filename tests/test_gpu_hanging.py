@@ -85,6 +85,27 @@ def test_slab_solve_hanging(stm, precision):
     assert rel(s.get_state()[0], uo) < (1e-12 if precision == "fp64" else 1e-9)
 
 
+def test_gauss_source_hanging_hp(stm):
+    """Gaussian current pulses on a 2:1 octree mesh with uneven (p, q): the load projected on
+    the device per (p, q) class, residual vs the oracle's at 1e-12."""
+    m = meshgen.corner_octree_mesh(2, [0.8])
+    meshgen.random_hp(m, 17, p_range=(1, 4), q_range=(1, 3))
+    srcs = [dict(centre=(0.3, 0.35, 0.4), dir=(0.0, 0.6, 0.8), sigma_x=0.2, t0=0.1, sigma_t=0.06, amp=1.5)]
+
+    def J(x, t):
+        sd = srcs[0]
+        r2 = np.sum((x - np.asarray(sd["centre"])) ** 2, axis=-1)
+        a = sd["amp"] * np.exp(-r2 / (2 * sd["sigma_x"] ** 2)) * np.exp(-(t - sd["t0"]) ** 2 / (2 * sd["sigma_t"] ** 2))
+        return a[..., None] * np.asarray(sd["dir"])
+
+    U = meshgen.random_coeffs(m, 18)
+    s = stm.Slab(m)
+    s.set_source_gauss(srcs)
+    R = np.empty(s.n_test)
+    s.residual_apply(U, R, 0.04, 0.05)
+    assert rel(R, stdg.Oracle(m).residual(U, 0.04, 0.05, src=J)) < 1e-12
+
+
 def test_hp_batch_full_size_sampled(stm):
     """~200k elements refined 2:1 towards a corner, p ~ U{1..7}, q ~ U{1..4}, eps ~ {1, 2.25, 4}:
     one apply over all (p, q) classes, checked on sampled elements of both sides of 2:1 faces."""

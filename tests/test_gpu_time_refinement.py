@@ -166,8 +166,9 @@ def test_mms_nodal_order_time_refined(stm, q):
 
 @pytest.mark.parametrize("case", ["nk_q_mixed", "nk_p_mixed"])
 def test_sources_and_boundary_data_uneven(stm, case):
-    """Gaussian pulses and boundary data g on meshes with uneven degrees and N_K: the
-    load is assembled on the host element by element; residual vs the oracle's."""
+    """Gaussian pulses and boundary data g on meshes with uneven degrees and N_K: the pulses
+    projected on the device per (p, q, N_K) class and sub-interval, g sampled and projected
+    on the host per element; residual vs the oracle's."""
     m = _mesh(case)
     srcs = [dict(centre=(0.5, 0.45, 0.55), dir=(0.0, 0.0, 1.0), sigma_x=0.15, t0=0.1, sigma_t=0.05, amp=1.0),
             dict(centre=(0.3, 0.6, 0.4), dir=(0.6, 0.0, 0.8), sigma_x=0.1, t0=0.12, sigma_t=0.08, amp=2.5)]
