@@ -49,10 +49,13 @@ __device__ __forceinline__ uint64_t mat_desc(uint32_t addr, uint32_t lbo, uint32
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(16 >> 3) << 17) |
                                 ((uint32_t)(128 >> 4) << 24);
 
-// Byte offset of element (r, k) in a K-major tile KW values wide: 8-row x 16-byte core
-// matrices, K-adjacent ones 128 bytes apart, 8-row groups KW / 4 * 128 bytes apart.
-__device__ __forceinline__ uint32_t core_ofs(int r, int k, int KW) {
-  return (uint32_t)(((r >> 3) * (KW >> 2) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+// Byte offset of element (r, k) in a K-major operand of ROWS rows: 8-row x 16-byte core
+// matrices with the rows of a K group of 4 values contiguous (16 bytes apart, 8-row groups
+// 128 bytes apart) and the K groups ROWS * 16 bytes apart, so consecutive rows are 16 bytes
+// apart whatever the K width.
+template <int ROWS>
+__device__ __forceinline__ uint32_t core_ofs(int r, int k) {
+  return (uint32_t)((k >> 2) * (ROWS * 16) + r * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -116,6 +119,7 @@ struct TcShape {
   static constexpr int KWB = NQ <= 8 ? 8 : 16;   // K width of the backward contractions
   static constexpr int ROWS = 3 * NQ2;           // largest stage (3 components)
   static constexpr int NT = (ROWS + 127) / 128;  // M = 128 tiles
+  static constexpr int AROWS = NT * 128;          // rows of the A operand buffer
   static constexpr int ABYTES = NT * 128 * 16 * 4;
   // shared memory: A hi, A lo, B forward hi/lo (16 x 8), B backward hi/lo (16 x 16), T3 [3][NQ3]
   static constexpr int OFS_ALO = ABYTES, OFS_BF = 2 * ABYTES, OFS_BB = OFS_BF + 2 * 512, OFS_T3 = OFS_BB + 2 * 1024;
@@ -146,12 +150,12 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
   for (int k = tid; k < 16 * 8; k += kTcThreads) {
     const int n = k / 8, kk = k % 8;  // forward: B[n = g][k = j] = L_j(x_g)
     const float v = (n < NQ && kk < N) ? tb.L[kk][n] : 0.f;
-    put_split(Bf, Bf + 512, core_ofs(n, kk, 8), v);
+    put_split(Bf, Bf + 512, core_ofs<16>(n, kk), v);
   }
   for (int k = tid; k < 16 * S::KWB; k += kTcThreads) {
     const int n = k / S::KWB, kk = k % S::KWB;  // backward: B[n = j][k = g] = L_j(x_g)
     const float v = (n < N && kk < NQ) ? tb.L[n][kk] : 0.f;
-    put_split(Bb, Bb + 1024, core_ofs(n, kk, S::KWB), v);
+    put_split(Bb, Bb + 1024, core_ofs<16>(n, kk), v);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -171,13 +175,14 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
   auto stage = [&](int KW, uint32_t bhi, uint32_t blo) -> bool {
     sync_for_mma();
     if (tid == 0) {
-      const uint32_t sbo = (uint32_t)(KW / 4) * 128;
+      // K groups of 4 values: A ones S::AROWS * 16 bytes apart, B ones 16 * 16; 8-row groups 128
+      constexpr uint32_t lboa = S::AROWS * 16, lbob = 16 * 16;
 #pragma unroll
       for (int t = 0; t < NT; ++t)
         for (int kb = 0; kb < KW / 8; ++kb) {
-          const uint32_t ao = (uint32_t)t * 16 * sbo + kb * 256;
-          const uint64_t dah = mat_desc(a_hi + ao, 128, sbo), dal = mat_desc(a_lo + ao, 128, sbo);
-          const uint64_t dbh = mat_desc(bhi + kb * 256, 128, sbo), dbl = mat_desc(blo + kb * 256, 128, sbo);
+          const uint32_t ao = (uint32_t)t * 128 * 16 + kb * 2 * lboa;
+          const uint64_t dah = mat_desc(a_hi + ao, lboa, 128), dal = mat_desc(a_lo + ao, lboa, 128);
+          const uint64_t dbh = mat_desc(bhi + kb * 2 * lbob, lbob, 128), dbl = mat_desc(blo + kb * 2 * lbob, lbob, 128);
           const uint32_t dt = tmem + 16 * t;
           mma_tf32(dt, dah, dbh, kb > 0 ? 1u : 0u);
           mma_tf32(dt, dah, dbl, 1u);
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
         const int c = x / N3, s = x - c * N3;
         float v = um[e * um_es + (f * 3 + c) * um_cs + i * N3 + s];
         if (i == 0 && u0) v -= u0[e * u0_es + (f * 3 + c) * u0_cs + s];
-        put_split(Ahi, Alo, core_ofs(x / N, s % N, 8), v);
+        put_split(Ahi, Alo, core_ofs<S::AROWS>(x / N, s % N), v);
       }
       if (!(alive = stage(8, bf, bf + 512))) break;
       // S1 -> S2: row (c, l, k), column gx  ->  row (c, l, gx), column k
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
         if (r < 3 * N2) {
           const int cl = r / N, k = r - cl * N;
 #pragma unroll
-          for (int g = 0; g < NQ; ++g) put_split(Ahi, Alo, core_ofs(cl * NQ + g, k, 8), d[t][g]);
+          for (int g = 0; g < NQ; ++g) put_split(Ahi, Alo, core_ofs<S::AROWS>(cl * NQ + g, k), d[t][g]);
         }
       }
       if (!(alive = stage(8, bf, bf + 512))) break;
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
         if (r < 3 * N * NQ) {
           const int c = r / (N * NQ), rem = r - c * N * NQ, l = rem / NQ, gx = rem - l * NQ;
 #pragma unroll
-          for (int g = 0; g < NQ; ++g) put_split(Ahi, Alo, core_ofs((c * NQ + g) * NQ + gx, l, 8), d[t][g]);
+          for (int g = 0; g < NQ; ++g) put_split(Ahi, Alo, core_ofs<S::AROWS>((c * NQ + g) * NQ + gx, l), d[t][g]);
         }
       }
       if (!(alive = stage(8, bf, bf + 512))) break;
@@ -250,9 +255,9 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
         const float gxx = ge[g], gyy = ge[NQ3 + g], gzz = ge[2 * NQ3 + g];
         const float gxy = ge[3 * NQ3 + g], gxz = ge[4 * NQ3 + g], gyz = ge[5 * NQ3 + g];
         const int gz = g / NQ2, g2 = g - gz * NQ2;
-        put_split(Ahi, Alo, core_ofs(g2, gz, S::KWB), mat * fmaf(gxx, vx, fmaf(gxy, vy, gxz * vz)));
-        put_split(Ahi, Alo, core_ofs(NQ2 + g2, gz, S::KWB), mat * fmaf(gxy, vx, fmaf(gyy, vy, gyz * vz)));
-        put_split(Ahi, Alo, core_ofs(2 * NQ2 + g2, gz, S::KWB), mat * fmaf(gxz, vx, fmaf(gyz, vy, gzz * vz)));
+        put_split(Ahi, Alo, core_ofs<S::AROWS>(g2, gz), mat * fmaf(gxx, vx, fmaf(gxy, vy, gxz * vz)));
+        put_split(Ahi, Alo, core_ofs<S::AROWS>(NQ2 + g2, gz), mat * fmaf(gxy, vx, fmaf(gyy, vy, gyz * vz)));
+        put_split(Ahi, Alo, core_ofs<S::AROWS>(2 * NQ2 + g2, gz), mat * fmaf(gxz, vx, fmaf(gyz, vy, gzz * vz)));
       }
       if (!(alive = stage(S::KWB, bb, bb + 1024))) break;
       // B1 -> B2: row (c, gy, gx), column l  ->  row (c, l, gx), column gy
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
         if (r < 3 * NQ2) {
           const int c = r / NQ2, rem = r - c * NQ2, gy = rem / NQ, gx = rem - gy * NQ;
 #pragma unroll
-          for (int l = 0; l < N; ++l) put_split(Ahi, Alo, core_ofs((c * N + l) * NQ + gx, gy, S::KWB), d[t][l]);
+          for (int l = 0; l < N; ++l) put_split(Ahi, Alo, core_ofs<S::AROWS>((c * N + l) * NQ + gx, gy), d[t][l]);
         }
       }
       if (!(alive = stage(S::KWB, bb, bb + 1024))) break;
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mass_tc(const float* __restrict_
         if (r < 3 * N * NQ) {
           const int cl = r / NQ, gx = r - cl * NQ;
 #pragma unroll
-          for (int k = 0; k < N; ++k) put_split(Ahi, Alo, core_ofs(cl * N + k, gx, S::KWB), d[t][k]);
+          for (int k = 0; k < N; ++k) put_split(Ahi, Alo, core_ofs<S::AROWS>(cl * N + k, gx), d[t][k]);
         }
       }
       if (!(alive = stage(S::KWB, bb, bb + 1024))) break;
@@ -308,10 +313,13 @@ int mass_tc_pq(const float* um, int64_t um_es, int64_t um_cs, const float* u0, i
   TcTabs tb;
   for (int j = 0; j < kMaxN; ++j)
     for (int g = 0; g <= kMaxN; ++g) tb.L[j][g] = (float)ct.Lq[j][g];
-  int dev = 0, sms = 152;
+  // one wave of co-resident CTAs: shared memory and the 512 TMEM columns (kTcCols per CTA)
+  // bound the CTAs per SM (the occupancy calculator does not model tensor memory)
+  int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)(ne < 8LL * sms ? ne : 8LL * sms);
+  const int per_sm = std::max(1, std::min(512 / kTcCols, (227 * 1024) / (S::SMEM + 2048)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ne, (int64_t)per_sm * sms));
   k_mass_tc<P, Q><<<grid, kTcThreads, S::SMEM, s>>>(um, um_es, um_cs, u0, u0_es, u0_cs, Gw, eps, mu, tb, ne, R, skip,
                                                     err);
   return (int)cudaGetLastError();
