@@ -171,6 +171,21 @@ int32_t stm_sizes(stm_ctx *ctx, int64_t *n_trial, int64_t *n_test, int64_t *n_st
 int32_t stm_residual_apply(stm_ctx *ctx, double t0, double dt, const void *U, void *R,
                            int32_t prec, int32_t mem);
 
+/* The operator the slab's GMRES iterates on (Sec. 5.4): W = A P^{-1} V (pre = 1)
+ * or W = A V (pre = 0).  A is the linear part of the residual of Eq. residual as
+ * a function of the unknown temporal modes 1..q (slab start mode 0 = 0, no load
+ * L), P the block-diagonal preconditioner of Eq. preconditioner (the time-
+ * derivative terms (eps d_t E, v) + (mu d_t H, w)); on trilinear and general
+ * affine meshes P^{-1} is the cell-mean 3x3 block inverse the solver uses.  V and
+ * W: n_test entries in the test layout (stm_sizes), double (prec = STM_FP64) or
+ * float (prec = STM_FP32), in host (mem = STM_MEM_HOST, copied through device
+ * buffers the context owns) or device memory (STM_MEM_DEVICE, caller-owned; V is
+ * not modified, V and W must not overlap).  Returns STM_EINVAL for a null
+ * pointer, dt <= 0 or a bad prec/mem/pre value, STM_ENOMEM when a staging
+ * buffer cannot be allocated, STM_EDEVICE on a CUDA error. */
+int32_t stm_operator_apply(stm_ctx *ctx, double dt, const void *V, void *W, int32_t pre,
+                           int32_t prec, int32_t mem);
+
 /* Set the state (spatial coefficients of E and H at time t, state layout,
  * double).  The next slab starts from it. */
 int32_t stm_set_state(stm_ctx *ctx, double t, const void *u, int32_t mem);

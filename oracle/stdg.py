@@ -580,6 +580,28 @@ class Oracle:
         A.sum_duplicates()
         return A, b
 
+    def time_derivative(self, U, dt, elems=None) -> np.ndarray:
+        """The preconditioner form of Eq. preconditioner (Sec. 5.4), the time-derivative
+        terms of C_h alone, P(U, V) = (eps d_t E, v) + (mu d_t H, w), for every test basis
+        function V, in the test layout (concatenated over ``elems``)."""
+        elems = range(self.ne) if elems is None else elems
+        U = np.atleast_2d(U)
+        out = []
+        for e in elems:
+            u = self.trial_block(U, e)
+            p, q, nk = int(self.p[e]), int(self.q[e]), int(self.nk[e])
+            xh, wx = _grid3(p + 2)
+            pts = self._pts(e, p, xh, ("vol", p + 2))
+            tau, wt = time_rule(q, nk)
+            Lt = test_time_nk(q, nk, tau)
+            wgt = dt * np.outer(wt, wx * pts.J)
+            _, dE, _ = _fields(u[:, 0], pts, q, tau, dt, nk=nk)
+            _, dH, _ = _fields(u[:, 1], pts, q, tau, dt, nk=nk)
+            RE = _test_project(self.eps[e] * dE, pts, Lt, wgt)
+            RH = _test_project(self.mu[e] * dH, pts, Lt, wgt)
+            out.append(np.stack([RE, RH], axis=1)[0].ravel())
+        return np.concatenate(out) if out else np.zeros(0)
+
     def unknown_mask(self) -> np.ndarray:
         """Boolean mask over the trial vector: True for modes m >= 1 (the slab unknowns)."""
         mask = np.zeros(int(self.trial_off[-1]), dtype=bool)

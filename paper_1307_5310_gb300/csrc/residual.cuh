@@ -849,6 +849,228 @@ __global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
   }
 }
 
+// ---- asynchronous global -> shared copies (cp.async, no register round trip) ----
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Floats of a staging slot for n floats: n plus up to 3 of alignment shift, rounded to 16 bytes.
+__host__ __device__ constexpr int stage_slot(int n) { return (n + 6) & ~3; }
+
+// One warp copies the n floats at src (4-byte aligned) into the 16-byte aligned slot so that
+// float k lands at the returned pointer + k, which sits at the same offset modulo 16 bytes as
+// src: the body moves in 16-byte chunks, the at most 3 + 3 floats around it in 4-byte ones.
+// Completion: cp_async_commit, cp_async_wait_all, then __syncwarp.
+__device__ __forceinline__ const float* stage_warp(float* slot, const float* src, int n, int lane) {
+  const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+  float* dst = slot + mis;
+  const int head = min((4 - mis) & 3, n);
+  const int nb = (n - head) >> 2;
+  const int t0 = head + 4 * nb;
+  for (int k = lane; k < nb; k += 32) cp_async16(dst + head + 4 * k, src + head + 4 * k);
+  if (lane < head) cp_async4(dst + lane, src + lane);
+  if (lane < n - t0) cp_async4(dst + t0 + lane, src + t0 + lane);
+  return dst;
+}
+
+// Single-pass FP32 Krylov apply A P^{-1} v on uniform brick meshes (no slab-start mode, no
+// load): the inner operator of the mixed-precision solve.  Same arithmetic as k_fused with
+// PRE, specialised: (a) forms y = sc B v and the mass term (v itself) with no branches on the
+// generic inputs; (b) stages each neighbour's two tangential component blocks into shared
+// memory with coalesced cp.async copies (one warp per (face, field), two rounds of six) and
+// forms its face traces from there, so the strided trace reads hit shared memory, not L1/L2;
+// (c) and the store are k_fused's.  Launched with 192 threads (six warps).
+template <int P, int Q>
+__global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
+  using T = float;
+  if (A.skip && *A.skip) return;
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N, SS = stage_slot(Q * N3);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3] temporal contraction
+  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3] residual planes (start: the mass term)
+  T* nt = Rs + 6 * Q * N3;                  // [6 faces][2 fields][2 comps][Q][N2] neighbour traces
+  T* stg = reinterpret_cast<T*>(smem_raw + ((sizeof(T) * (12 * Q * N3 + 24 * Q * N2) + 15) & ~size_t(15)));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* slot = stg + warp * 2 * SS;  // this warp's two component slots
+  const int um_cs = (int)A.um_cs;
+  // issues the copies of task (face, fld) = (task >> 1, task & 1): the neighbour's two
+  // tangential components; returns false (nothing issued) on a boundary face
+  auto issue = [&](int64_t e, int task, const T** src) -> bool {
+    const int face = task >> 1, fld = task & 1, a = face >> 1;
+    const int64_t en = A.nbr[e * 6 + face];
+    if (en < 0) return false;
+    const T* ue = A.um + en * A.um_es;
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi) {
+      const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
+      src[bi] = stage_warp(slot + bi * SS, ue + (fld * 3 + b) * um_cs, Q * N3, lane);
+    }
+    cp_async_commit();
+    return true;
+  };
+  // the traces of task `task` from the staged blocks
+  auto traces = [&](int64_t e, int task, const T* const* src) {
+    const int face = task >> 1, fld = task & 1, a = face >> 1, side = face & 1;
+    const int64_t en = A.nbr[e * 6 + face];
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi) {
+      const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
+      const T sc = A.pinv[en * 6 + fld * 3 + b];
+      T* nto = nt + ((task * 2 + bi) * Q) * N2;
+      const T* ub = src[bi];
+      with_axis(a, [&](auto ac) {
+        constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
+        // the neighbour meets face (a, side) with its face (a, 1 - side): L_j(0) = (-1)^j L_j(1)
+        auto run = [&](auto sidec) {
+          constexpr bool S1 = decltype(sidec)::value;
+          for (int t = lane; t < N2; t += 32) {
+            const T* ul = ub + line_base<N, AX>(t);
+            T tu[Q];
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+              T acc = T(0);
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                const T w = (S1 && (j & 1)) ? -A.tb.lv[j] : A.tb.lv[j];
+                acc = fma(w, ul[m * N3 + j * ST], acc);
+              }
+              tu[m] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              T acc = T(0);
+#pragma unroll
+              for (int m = 1; m <= Q; ++m)
+                if (b_nz(i, m)) acc = fma(A.tb.B[i][m], tu[m - 1], acc);
+              nto[i * N2 + t] = sc * acc;
+            }
+          }
+        };
+        if (side) run(std::true_type{});
+        else run(std::false_type{});
+      });
+    }
+  };
+  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
+    const int32_t* nb = A.nbr + e * 6;
+    const T* ume = A.um + e * A.um_es;
+    const int64_t re = e * (int64_t)(6 * Q * N3);
+    // round 1 of the neighbour copies in flight while the own block is contracted
+    const T* src[2];
+    bool have = issue(e, warp, src);
+    // (a) y = sc B v and the mass term v (the mass block times P^{-1} is the identity)
+    for (int it = threadIdx.x; it < 6 * N3; it += 192) {
+      const int fc = it / N3, s = it - fc * N3;
+      const T* up = ume + fc * um_cs + s;
+      T v[Q];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = up[m * N3];
+      const T sc = A.pinv[e * 6 + fc];
+      T* yo = ys + fc * Q * N3 + s;
+      T* ro = Rs + fc * Q * N3 + s;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 1; m <= Q; ++m)
+          if (b_nz(i, m)) acc = fma(A.tb.B[i][m], v[m - 1], acc);
+        yo[i * N3] = sc * acc;
+        ro[i * N3] = v[i];
+      }
+    }
+    // (b) neighbour traces: two rounds of six (face, field) tasks, one per warp
+    if (have) {
+      cp_async_wait_all();
+      __syncwarp();
+      traces(e, warp, src);
+      __syncwarp();  // the slots are refilled next
+    }
+    have = issue(e, warp + 6, src);
+    if (have) {
+      cp_async_wait_all();
+      __syncwarp();
+      traces(e, warp + 6, src);
+    }
+    __syncthreads();
+    // (c) residual planes: one warp per (field, component), all Q temporal test modes
+    for (int fc = warp; fc < 6; fc += 6) {
+      const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f, fp = 1 - f;
+      T* Rp = Rs + fc * Q * N3;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
+        const int b = 3 - c - a;
+        const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
+        const bool neg = ((f == 0) == (((a - c + 3) % 3) == 1));
+        const T* yb = ys + (fp * 3 + b) * Q * N3;
+        const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
+        const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q) * N2;
+        const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q) * N2;
+        auto lines = [&](auto ac, auto negc) {
+          constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
+          constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
+          for (int t = lane; t < N2; t += 32) {
+            const int base = line_base<N, AX>(t);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+              const T* yl = yb + i * N3 + base;
+              T yv[N];
+              T ev = T(0), od = T(0);
+#pragma unroll
+              for (int j = 0; j < N; ++j) {
+                yv[j] = yl[j * ST];
+                if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
+                else ev = fma(A.tb.lv[j], yv[j], ev);
+              }
+              const T xp = ev + od, xm = ev - od;
+              const T op = hasp ? ntp[i * N2 + t] : ((fp == 0) ? neg_bits(xp) : xp);
+              const T om = hasm ? ntm[i * N2 + t] : ((fp == 0) ? neg_bits(xm) : xm);
+              const T jp = xp - op, jm = xm - om;
+              const T sp = jp + jm, dm = jp - jm;
+              constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
+              if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+              if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+              T* Rl = Rp + i * N3 + base;
+#pragma unroll
+              for (int al = 0; al < N; ++al) {
+                T r2 = Rl[al * ST];
+                if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+                for (int be = 0; be < N; ++be)
+                  if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+                Rl[al * ST] = r2;
+              }
+            }
+          }
+        };
+        with_axis(a, [&](auto ac) {
+          if (neg) lines(ac, std::true_type{});
+          else lines(ac, std::false_type{});
+        });
+        __syncwarp();
+      }
+      T* Rg = A.R + re + fc * Q * N3;
+      for (int s2 = lane; s2 < Q * N3; s2 += 32) Rg[s2] = Rp[s2];
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory of k_fused_kry: k_fused's plus six warps' two staging slots each.
+__host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
+  return ((sizeof(float) * (12 * Q * (P + 1) * (P + 1) * (P + 1) + 24 * Q * (P + 1) * (P + 1)) + 15) & ~size_t(15)) +
+         sizeof(float) * 12 * stage_slot(Q * (P + 1) * (P + 1) * (P + 1));
+}
+
 // Optional CUDA events recorded before k_prep, between the kernels and after
 // k_apply (all null: no timing).
 struct LaunchEvents {
@@ -885,6 +1107,8 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
     if constexpr (sizeof(T) == 4) {
       cudaFuncSetAttribute(k_fused<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
       cudaFuncSetAttribute(k_fused<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
+      cudaFuncSetAttribute(k_fused_kry<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_kry_smem(P, Q));
     }
     cudaGetLastError();
   });
@@ -897,8 +1121,13 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       // six warps: the 6 Q residual planes and the 24 neighbour-trace tasks divide evenly
       constexpr int kFusedThreads = 192;
       (void)block;
-      static std::atomic<int> cap_t[64], cap_f[64];
-      if (args.pinv)
+      static std::atomic<int> cap_t[64], cap_f[64], cap_k[64];
+      if (fused_kry_smem(P, Q) <= 74 * 1024 && args.pinv && !args.u0 && !args.b && args.mass && !args.mass3) {
+        // the Krylov operator A P^{-1} v of the mixed-precision solve
+        const size_t smk = fused_kry_smem(P, Q);
+        k_fused_kry<P, Q><<<wave_grid(k_fused_kry<P, Q>, kFusedThreads, smk, grid, cap_k), kFusedThreads, smk, s>>>(
+            args);
+      } else if (args.pinv)
         k_fused<T, P, Q, true><<<wave_grid(k_fused<T, P, Q, true>, kFusedThreads, sm_fused, grid, cap_t),
                                  kFusedThreads, sm_fused, s>>>(args);
       else

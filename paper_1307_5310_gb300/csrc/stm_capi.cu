@@ -186,6 +186,8 @@ struct stm_ctx {
   size_t tmp_in_bytes = 0;
   void* tmp_out = nullptr;
   size_t tmp_out_bytes = 0;
+  void* tmp_op = nullptr;  // P^{-1} V of stm_operator_apply on curved and affine meshes
+  size_t tmp_op_bytes = 0;
   // inverse mass factors 1 / (eps G_c), 1 / (mu G_c): the preconditioner of Eq. preconditioner
   double* inv64 = nullptr;
   float* inv32 = nullptr;
@@ -1831,7 +1833,7 @@ int32_t stm_destroy(stm_ctx* c) {
   if (!c) return STM_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->nbr,     c->mass64,  c->mass32, c->y64,   c->tr64, c->y32, c->tr32,
-                  c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->V, c->z,
+                  c->state,   c->red_partial, c->red_out, c->tmp_in, c->tmp_out, c->tmp_op, c->V, c->z,
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
                   c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
                   c->sw64,    c->sw32,    c->kap64,  c->kap32, c->nkl,    c->tmat64, c->tmat32,
@@ -1894,6 +1896,50 @@ int32_t stm_residual_apply(stm_ctx* c, double t0, double dt, const void* U, void
   if (rc) return rc;
   if (mem == STM_MEM_HOST) {
     STM_CK(cudaMemcpyAsync(R, c->tmp_out, c->n_test * es, cudaMemcpyDeviceToHost, c->stream));
+    STM_CK(cudaStreamSynchronize(c->stream));
+  }
+  STM_CK(cudaGetLastError());
+  return STM_OK;
+}
+
+int32_t stm_operator_apply(stm_ctx* c, double dt, const void* V, void* W, int32_t pre, int32_t prec, int32_t mem) {
+  if (!c || !V || !W) return STM_EINVAL;
+  if (!(dt > 0)) return fail(c, STM_EINVAL, "dt must be positive");
+  if (prec != STM_FP64 && prec != STM_FP32) return fail(c, STM_EINVAL, "prec must be STM_FP64 or STM_FP32");
+  if (mem != STM_MEM_HOST && mem != STM_MEM_DEVICE) return fail(c, STM_EINVAL, "bad memory kind");
+  if (pre != 0 && pre != 1) return fail(c, STM_EINVAL, "pre must be 0 or 1");
+  const size_t es = prec == STM_FP64 ? sizeof(double) : sizeof(float);
+  const void* Vd = V;
+  void* Wd = W;
+  if (mem == STM_MEM_HOST) {
+    int rc = ensure(c, &c->tmp_in, &c->tmp_in_bytes, c->n_test * es);
+    if (!rc) rc = ensure(c, &c->tmp_out, &c->tmp_out_bytes, c->n_test * es);
+    if (rc) return rc;
+    STM_CK(cudaMemcpyAsync(c->tmp_in, V, c->n_test * es, cudaMemcpyHostToDevice, c->stream));
+    Vd = c->tmp_in;
+    Wd = c->tmp_out;
+  }
+  auto run = [&](auto tag) -> int {
+    using S = decltype(tag);
+    const S* v = (const S*)Vd;
+    S* w = (S*)Wd;
+    if (!pre) return linop<S>(c, dt, v, w);
+    if (c->geometry != STM_GEOM_BRICK) {
+      // 3x3 blocks of the (cell-mean) metric mass, then the operator, as in the GMRES cycle
+      int rc = ensure(c, &c->tmp_op, &c->tmp_op_bytes, c->n_test * sizeof(S));
+      if (rc) return rc;
+      S* z = (S*)c->tmp_op;
+      precond_curved<S, S>(z, v, 0, 0, nullptr, curved_ptr<S>(c, 3), (int64_t)c->Q * c->N3, c->ne, false,
+                           c->stream);
+      c->launches += 1;
+      return linop<S>(c, dt, z, w);
+    }
+    return linop_pre<S>(c, dt, v, w);
+  };
+  const int rc = prec == STM_FP64 ? run(double{}) : run(float{});
+  if (rc) return rc;
+  if (mem == STM_MEM_HOST) {
+    STM_CK(cudaMemcpyAsync(W, c->tmp_out, c->n_test * es, cudaMemcpyDeviceToHost, c->stream));
     STM_CK(cudaStreamSynchronize(c->stream));
   }
   STM_CK(cudaGetLastError());

@@ -37,7 +37,7 @@ STM_MEM_DEVICE = 1
 
 # Every exported entry point of include/stm.h.
 EXPORTS = (
-    "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply",
+    "stm_create", "stm_destroy", "stm_last_error", "stm_sizes", "stm_residual_apply", "stm_operator_apply",
     "stm_set_state", "stm_get_state", "stm_set_initial", "stm_slab_solve", "stm_energy",
     "stm_launch_count", "stm_profile_enable", "stm_profile_read", "stm_residual_apply_noalloc",
     "stm_set_source_gauss", "stm_set_boundary", "stm_set_source", "stm_dof_layout", "stm_fp64_probe",
@@ -117,6 +117,7 @@ def lib() -> C.CDLL:
         L.stm_last_error.restype = C.c_char_p
         L.stm_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         L.stm_residual_apply.argtypes = [vp, d, d, vp, vp, i32, i32]
+        L.stm_operator_apply.argtypes = [vp, d, vp, vp, i32, i32, i32]
         L.stm_set_state.argtypes = [vp, d, vp, i32]
         L.stm_get_state.argtypes = [vp, C.POINTER(d), vp, i32]
         L.stm_set_initial.argtypes = [vp, d, FIELD_FN, FIELD_FN, vp]
@@ -289,6 +290,15 @@ class Slab:
         if mu_ != mr:
             raise ValueError("U and R must both be host or both be device arrays")
         return self._check(lib().stm_residual_apply(self.ctx, t0, dt, pu, pr, prec, mu_))
+
+    def operator_apply(self, V, W, dt: float, pre=True, prec=STM_FP64):
+        """W = A P^{-1} V (pre) or A V: the operator of the slab's GMRES, test layout."""
+        dt_ = np.float64 if prec == STM_FP64 else np.float32
+        pv, mv, _ = _ptr(V, dt_)
+        pw, mw, _ = _ptr(W, dt_)
+        if mv != mw:
+            raise ValueError("V and W must both be host or both be device arrays")
+        return self._check(lib().stm_operator_apply(self.ctx, dt, pv, pw, 1 if pre else 0, prec, mv))
 
     def set_state(self, u, t=0.0):
         p, m, _ = _ptr(u, np.float64)

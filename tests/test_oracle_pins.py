@@ -688,3 +688,31 @@ def test_mms_nodal_superconvergence_time_refinement(q):
         errs.append(np.sqrt(2 * o.energy(u - ue)))
     order = np.log2(errs[0] / errs[1])
     assert abs(order - 2 * q) < 0.3, (errs, order)
+
+
+@pytest.mark.parametrize("p,q", [(0, 1), (2, 2), (1, 3)])
+def test_time_derivative_form_closed_form(p, q):
+    """Eq. preconditioner on bricks: the spatial Legendre basis is orthonormal and DF is the
+    constant diag(hx, hy, hz), so (eps d_t E, v) couples only equal spatial modes of one
+    component, with weight eps G_c, G = (hy hz/hx, hx hz/hy, hx hy/hz) (Sec. 2.3).  In time,
+    int_0^1 L_i l_m' is -delta_i0 for m = 0 and delta_{i,m-1} for m >= 1 (the derivative of
+    the trial basis is the orthonormal Legendre basis of one degree less, Sec. 5.1).  So
+    P(U)[f,c,i,s] = mat_f G_c (U[f,c,i+1,s] - delta_i0 U[f,c,0,s]) exactly."""
+    m = meshgen.box_mesh(3, 2, 1, hi=(0.9, 0.5, 0.2), p=p, q=q)
+    meshgen.random_materials(m, 71, 72)
+    orc = stdg.Oracle(m)
+    U = meshgen.random_coeffs(m, 73)
+    dt = 0.037
+    got = orc.time_derivative(U, dt)
+    n3 = (p + 1) ** 3
+    h = np.array([0.9 / 3, 0.5 / 2, 0.2 / 1])
+    G = np.array([h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2]])
+    want = []
+    for e in range(orc.ne):
+        u = U[e * 6 * (q + 1) * n3:(e + 1) * 6 * (q + 1) * n3].reshape(2, 3, q + 1, n3)
+        mat = np.array([m["eps"][e], m["mu"][e]])
+        r = u[:, :, 1:, :].copy()
+        r[:, :, 0, :] -= u[:, :, 0, :]
+        want.append((mat[:, None, None, None] * G[None, :, None, None] * r).ravel())
+    want = np.concatenate(want)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
