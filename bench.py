@@ -107,6 +107,17 @@ def linop_bytes_per_element(p, q, es=4):
     return es * (6 * q * n3 + 6 * q * n3) + 6 * es + 6 * 4
 
 
+def fp32_krylov_kernel(p, q):
+    """Name of the kernel of the mixed solve's FP32 operator A P^{-1} v on uniform bricks, by the
+    launcher's shared-memory rule (residual.cuh: fused_smem <= 64 KB, fused_kry_smem <= 74 KB)."""
+    n3, n2 = (p + 1) ** 3, (p + 1) ** 2
+    fused = 4 * (12 * q * n3 + 24 * q * n2)
+    kry = ((fused + 15) & ~15) + 4 * 12 * ((q * n3 + 6) & ~3)
+    if fused > 64 * 1024:
+        return f"k_prep<float,{p},{q}> + k_apply<float,{p},{q}>"
+    return f"k_fused_kry<{p},{q}>" if kry <= 74 * 1024 else f"k_fused<float,{p},{q},1>"
+
+
 def bytes_per_element(p, q, es=8):
     """Algorithmic HBM bytes of one apply per element: read U, write R, eps/mu."""
     n3 = (p + 1) ** 3
@@ -283,7 +294,8 @@ def curved_flops_per_element(p, q):
 
 
 def time_applies(s, m, dt, prec, reps=5, warm=2):
-    """CUDA-event time of `reps` residual applies through the C ABI on device buffers; profile dict."""
+    """CUDA-event time (ms) of one of `reps` residual applies through the C ABI on device buffers
+    (no per-kernel profile: uneven meshes then run their class kernels side by side)."""
     import torch
 
     from paper_1307_5310_gb300 import stm
@@ -293,17 +305,14 @@ def time_applies(s, m, dt, prec, reps=5, warm=2):
     R = torch.empty(s.n_test, dtype=dtp, device="cuda")
     for _ in range(warm):
         s.residual_apply(U, R, 0.0, dt, prec=prec)
-    s.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
         s.residual_apply(U, R, 0.0, dt, prec=prec)
     e1.record()
     torch.cuda.synchronize()
-    prof = s.profile_read()
-    s.profile(False)
     del U, R
-    return e0.elapsed_time(e1) / reps, prof
+    return e0.elapsed_time(e1) / reps
 
 
 def leg_hp_batch(fp64_peak):
@@ -319,8 +328,8 @@ def leg_hp_batch(fp64_peak):
     fl = sum(sum(flops_per_element(int(pp), int(qq))) for pp, qq in zip(p, q))
     s = stm.Slab(m, tol=1e-9, max_it=400, reorth=False)
     dt = (1.0 / 200) / 15
-    ms64, _ = time_applies(s, m, dt, stm.STM_FP64)
-    ms32, _ = time_applies(s, m, dt, stm.STM_FP32)
+    ms64 = time_applies(s, m, dt, stm.STM_FP64)
+    ms32 = time_applies(s, m, dt, stm.STM_FP32)
     by32 = sum(bytes_per_element(int(pp), int(qq), 4) for pp, qq in zip(p, q))
     ach = fl / (ms64 / 1e3) / 1e12
     s.close()
@@ -348,8 +357,8 @@ def leg_curved(fp64_peak):
         s = stm.Slab(m)
         ne = m["hex"].shape[0]
         dt = (1.0 / 32) / (2 * p + 1)
-        ms64, _ = time_applies(s, m, dt, stm.STM_FP64, reps=3)
-        ms32, _ = time_applies(s, m, dt, stm.STM_FP32, reps=3)
+        ms64 = time_applies(s, m, dt, stm.STM_FP64, reps=3)
+        ms32 = time_applies(s, m, dt, stm.STM_FP32, reps=3)
         fp, fa, fm = curved_flops_per_element(p, q)
         ach = (fp + fa + fm) * ne / (ms64 / 1e3) / 1e12
         dof = ne * 6 * (q + 1) * (p + 1) ** 3
@@ -642,8 +651,8 @@ def leg_dissipative(fp64_peak):
     dt = (1.0 / n) / (2 * p + 1)
     dof = ne * 6 * (q + 1) * (p + 1) ** 3
     s = stm.Slab(m, c_diss=1.0, tol=1e-9, max_it=400, reorth=False)
-    ms64, _ = time_applies(s, m, dt, stm.STM_FP64, reps=3)
-    ms32, _ = time_applies(s, m, dt, stm.STM_FP32, reps=3)
+    ms64 = time_applies(s, m, dt, stm.STM_FP64, reps=3)
+    ms32 = time_applies(s, m, dt, stm.STM_FP32, reps=3)
     u0 = np.random.Generator(np.random.PCG64(1310)).uniform(-1, 1, s.n_state)
     sol64, it64, rc64 = _solve_ms(s, u0, dt, reps=1)
     s.close()
@@ -677,8 +686,8 @@ def leg_time_refinement(fp64_peak):
     dt = (1.0 / n) / (2 * p + 1)
     dof = int(np.sum(6 * (nk * q + 1) * (p + 1) ** 3))
     s = stm.Slab(m, tol=1e-9, max_it=400, reorth=False)
-    ms64, _ = time_applies(s, m, dt, stm.STM_FP64, reps=3)
-    ms32, _ = time_applies(s, m, dt, stm.STM_FP32, reps=3)
+    ms64 = time_applies(s, m, dt, stm.STM_FP64, reps=3)
+    ms32 = time_applies(s, m, dt, stm.STM_FP32, reps=3)
     u0 = np.random.Generator(np.random.PCG64(1310)).uniform(-1, 1, s.n_state)
     sol64, it64, rc64 = _solve_ms(s, u0, dt, reps=1)
     s.close()
@@ -842,9 +851,9 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp64_peak = 4.0 * sms * sm_mhz * 1e6 / 1e12  # 2 FP64 FMA / clock / SM
     ach = fl_apply * ne / (apply_ms / 1e3) / 1e12
-    # DRAM bytes per k_apply launch from one ncu capture of the 32^3 case (2.444 GB), scaled by the
-    # element count to this workload; valid for p=4, q=3 on 64^3 only
-    traffic = 2.444e9 * ne / 32 ** 3 if (args.n, args.p, args.q) == (64, 4, 3) else None
+    # DRAM bytes per k_apply launch from one ncu capture of the 32^3 case (1.936 GB read + 0.572 GB
+    # written), scaled by the element count to this workload; valid for p=4, q=3 on 64^3 only
+    traffic = 2.507e9 * ne / 32 ** 3 if (args.n, args.p, args.q) == (64, 4, 3) else None
     try:  # context: the FP64 FMA rate this GPU reaches in a register-only kernel, measured live
         probe = stm.fp64_probe()
     except Exception:  # reported as missing, never replaced
@@ -919,11 +928,18 @@ def run_ours(args):
         k32 = pm["k_apply_fp32"]
         k32_ms = k32[0] / max(1, k32[1])
         by = linop_bytes_per_element(args.p, args.q, 4) * ne  # the solve's FP32 applies are A P^{-1} v
-        mixed["fp32_kernel"] = {"kernel": f"k_fused<float,{args.p},{args.q}>", "launch_ms": k32_ms,
+        # DRAM bytes per k_fused_kry launch: one ncu capture inside the 32^3 mixed solve (385.1 MB read +
+        # 260.6 MB written), scaled by the element count; p=4, q=3 only
+        kry43 = (args.p, args.q) == (4, 3)
+        traffic32 = 645.7e6 * ne / 32 ** 3 if kry43 else None
+        traffic32_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 32^3 mixed-solve capture x "
+                         f"{ne / 32 ** 3:g} (bytes)") if kry43 else None
+        mixed["fp32_kernel"] = {"kernel": fp32_krylov_kernel(args.p, args.q), "launch_ms": k32_ms,
                                 "gdofs": dof_slab / (k32_ms / 1e3) / 1e9,
                                 "roofline": {"bound": "hbm", "achieved": by / (k32_ms / 1e3) / 1e9, "peak": hbm_peak()[0],
                                              "unit": "GB/s", "frac": by / (k32_ms / 1e3) / 1e9 / hbm_peak()[0],
-                                             "traffic": None, "peak_source": hbm_peak()[1]}}
+                                             "traffic": traffic32, "traffic_source": traffic32_src,
+                                             "peak_source": hbm_peak()[1]}}
         smx.close()
     except Exception as ex:  # reported, never replaced by another path
         mixed = {"error": repr(ex)}

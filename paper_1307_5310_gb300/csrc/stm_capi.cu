@@ -237,6 +237,11 @@ struct stm_ctx {
   // uniform-mesh block size (autotuned), CUDA graphs of multi-class applies
   int block = 256;
   cudaStream_t cap_stream = nullptr;
+  // uneven (p, q): the class kernels of one phase run side by side on these streams
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kAux] = {};
+  std::vector<int> class_order;  // classes by decreasing work, dealt round-robin to aux
   struct GraphKey {
     int prec, um_layout, u0_layout, pre;
     const void *um, *u0, *b, *R;
@@ -484,6 +489,43 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
     a.hslot = c->hslot;
     a.hoff = c->hoff;
     a.hbuf = hbuf_ptr<T>(c);
+    // the classes of one phase are independent: fork them over the auxiliary streams (largest
+    // first, round-robin) and join before the next phase; the timed profile keeps them in order
+    const bool conc = !c->profiling && c->classes.size() > 1;
+    if (conc && !c->fork_ev) {
+      bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+      for (int k = 0; ok && k < stm_ctx::kAux; ++k)
+        ok = cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        return fail(c, STM_EDEVICE, "auxiliary stream set-up failed");
+      }
+    }
+    if (c->class_order.size() != c->classes.size()) {
+      c->class_order.resize(c->classes.size());
+      for (size_t k = 0; k < c->classes.size(); ++k) c->class_order[k] = (int)k;
+      auto work = [&](int k) {
+        const auto& cl = c->classes[k];
+        const double n = cl.P + 1.0;
+        return (double)cl.count * n * n * n * n * cl.Q * cl.NK;
+      };
+      std::stable_sort(c->class_order.begin(), c->class_order.end(), [&](int x, int y) { return work(x) > work(y); });
+    }
+    auto fork = [&]() -> cudaError_t {
+      cudaError_t e = cudaEventRecord(c->fork_ev, ls);
+      for (int k = 0; e == cudaSuccess && k < stm_ctx::kAux; ++k) e = cudaStreamWaitEvent(c->aux[k], c->fork_ev, 0);
+      return e;
+    };
+    auto join = [&]() -> cudaError_t {
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < stm_ctx::kAux; ++k) {
+        const cudaError_t e1 = cudaEventRecord(c->join_ev[k], c->aux[k]);
+        const cudaError_t e2 = cudaStreamWaitEvent(ls, c->join_ev[k], 0);
+        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+      }
+      return e;
+    };
     for (int phase = 1; phase <= 2; ++phase) {
       if (phase == 2 && c->n_slots > 0) {
         // 2:1 faces: equivalent neighbour traces from all classes' traces
@@ -507,20 +549,27 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
         launch_hang<T>(h, ls);
         c->launches += 1;
       }
-      for (size_t k = 0; k < c->classes.size(); ++k) {
+      cudaError_t fe = conc ? fork() : cudaSuccess;
+      for (size_t j = 0; j < c->classes.size(); ++j) {
+        const size_t k = conc ? (size_t)c->class_order[j] : j;
         const auto& cl = c->classes[k];
         a.elist = cl.elist;
         a.n_elem = cl.count;
         a.nk = cl.NK;
         a.tb = make_tables<T>(cl.P, kMaxQ, dt / cl.NK);  // sub-interval length dt / N_K
         LaunchEvents e2 = none;
-        if (phase == 1 && k == 0) e2.start = ev.start;
-        if (phase == 1 && k + 1 == c->classes.size()) e2.mid = ev.mid;
-        if (phase == 2 && k + 1 == c->classes.size()) e2.stop = ev.stop;
+        if (!conc) {
+          if (phase == 1 && k == 0) e2.start = ev.start;
+          if (phase == 1 && k + 1 == c->classes.size()) e2.mid = ev.mid;
+          if (phase == 2 && k + 1 == c->classes.size()) e2.stop = ev.stop;
+        }
         const int grid = res_grid(c, cl.count);
-        const int e = launch_residual_ph<T>(cl.P, cl.Q, a, ls, grid, e2, phase, cl.block);
+        const int e = fe != cudaSuccess ? (int)fe
+                                        : launch_residual_ph<T>(cl.P, cl.Q, a, conc ? c->aux[j % stm_ctx::kAux] : ls,
+                                                                grid, e2, phase, cl.block);
         c->launches += 1;
         if (e) {
+          if (conc) join();  // the forked streams rejoin the origin before the capture ends
           if (use_graph) {
             cudaGraph_t g = nullptr;
             cudaStreamEndCapture(c->cap_stream, &g);
@@ -528,6 +577,18 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
             cudaGetLastError();  // the invalidated capture leaves no error behind
           }
           return fail(c, STM_EDEVICE, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)e));
+        }
+      }
+      if (conc) {
+        const cudaError_t je = join();
+        if (je != cudaSuccess) {
+          if (use_graph) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(c->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+          }
+          return fail(c, STM_EDEVICE, std::string("class join: ") + cudaGetErrorString(je));
         }
       }
     }
@@ -973,7 +1034,7 @@ int build_load(stm_ctx* c, double t0, double dt, const double** out) {
     *out = c->load64;
     return STM_OK;
   }
-  const int P = c->P, Q = c->Q, N = c->N, N3 = c->N3, nq = P + 2, nt = Q + 2;
+  const int P = c->P, Q = c->Q, N = c->N, nq = P + 2, nt = Q + 2;
   std::vector<double> xq, wq, xt, wt;
   gauss01(nq, xq, wq);
   gauss01(nt, xt, wt);
@@ -1064,13 +1125,6 @@ __global__ void k_extract_end(double* state, const double* x, int64_t q, int64_t
 }
 
 int grid1(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
-
-template <typename S>
-const S* inv_ptr(stm_ctx* c);
-template <>
-const double* inv_ptr<double>(stm_ctx* c) { return c->inv64; }
-template <>
-const float* inv_ptr<float>(stm_ctx* c) { return c->inv32; }
 
 // ||v||^2 (fixed-order reduction, FP64 accumulation).
 template <typename S>
@@ -1854,6 +1908,11 @@ int32_t stm_destroy(stm_ctx* c) {
   if (c->gst) cudaFree(c->gst);
   if (c->h_gst) cudaFreeHost(c->h_gst);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (int k = 0; k < stm_ctx::kAux; ++k) {
+    if (c->aux[k]) cudaStreamDestroy(c->aux[k]);
+    if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return STM_OK;
