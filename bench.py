@@ -67,10 +67,11 @@ def parse():
                          "Sec. 6.1.1; iteration_study = GMRES iterations of the Sec. 5.3 resonator vs tolerance "
                          "and initial guess; curved_slabs = 50 mixed slab solves on 32^3 trilinear hexes, p = 3, 5, "
                          "7, Gaussian J)")
-    ap.add_argument("--profile-case", default=None, choices=["apply", "curved", "solve"],
+    ap.add_argument("--profile-case", default=None, choices=["apply", "curved", "solve", "hp"],
                     help="run a small fixed case for a profiler and exit (no JSON line): 'apply' = --steps "
                          "residual applies on --n^3 bricks (p, q), 'curved' = the same on trilinear hexes "
-                         "(q = p - 1), 'solve' = --steps slab solves of the bench workload")
+                         "(q = p - 1), 'solve' = --steps slab solves of the bench workload, 'hp' = --steps "
+                         "residual applies on the hp_batch mesh (2:1 octree, uneven p and q; --n ignored)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"],
                     help="precision of --profile-case")
     ap.add_argument("--reorth", type=int, default=0, help="second Gram-Schmidt pass (DGKS test); off by default: same iteration count and accuracy on this workload")
@@ -662,11 +663,15 @@ def leg_dissipative(fp64_peak):
     fp, fa = flops_per_element(p, q)
     fd = 2 * 3 * 2 * q * (p + 1) ** 2 * 6  # per line: two jumps, two alpha scalings, two combinations
     ach = (fp + fa + fd) * ne / (ms64 / 1e3) / 1e12
+    by32 = (bytes_per_element(p, q, 4) + 24 * 4) * ne  # + the 24 alpha coefficients per element
     return {"workload": "64^3 bricks, p=4, q=3, eps/mu U[1,4], PEC, dt=h/9, c_diss=1",
             "fp64": {"ms_per_apply": ms64, "gdofs": dof / (ms64 / 1e3) / 1e9,
                      "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                                   "frac": ach / fp64_peak, "flops_per_element": fp + fa + fd}},
-            "fp32": {"ms_per_apply": ms32, "gdofs": dof / (ms32 / 1e3) / 1e9},
+            "fp32": {"ms_per_apply": ms32, "gdofs": dof / (ms32 / 1e3) / 1e9, "kernel": f"k_fused<float,{p},{q},0,1>",
+                     "roofline": {"bound": "hbm", "achieved": by32 / (ms32 / 1e3) / 1e9, "peak": hbm_peak()[0],
+                                  "unit": "GB/s", "frac": by32 / (ms32 / 1e3) / 1e9 / hbm_peak()[0],
+                                  "bytes_per_element": by32 / ne, "peak_source": hbm_peak()[1]}},
             "slab_solve_fp64": {"ms": sol64, "iterations": it64, "rc": rc64},
             "slab_solve_mixed": {"ms": solmx, "iterations": itmx, "rc": rcmx}}
 
@@ -1009,9 +1014,14 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print("ok", rc, rep)
         return
-    q = p - 1 if args.profile_case == "curved" else args.q
-    m = meshgen.box_mesh(n, p=p, q=q, order="morton", perturb=0.1 if args.profile_case == "curved" else 0.0)
-    meshgen.random_materials(m, 1307, 1308)
+    if args.profile_case == "hp":
+        m = meshgen.corner_octree_mesh(50, [0.45, 0.2])
+        meshgen.random_hp(m, 1307)
+        n, p = 200, 7  # dt = (1/200)/15, the hp_batch leg's
+    else:
+        q = p - 1 if args.profile_case == "curved" else args.q
+        m = meshgen.box_mesh(n, p=p, q=q, order="morton", perturb=0.1 if args.profile_case == "curved" else 0.0)
+        meshgen.random_materials(m, 1307, 1308)
     s = stm.Slab(m)
     dtp = torch.float64 if args.precision == "fp64" else torch.float32
     U = torch.empty(s.n_trial, dtype=dtp, device="cuda").uniform_(-1, 1)

@@ -653,7 +653,7 @@ __device__ __forceinline__ void with_axis(int a, F&& f) {
 // element.  Line axes are
 // dispatched warp-uniformly to compile-time strides, so every load of a line
 // has an immediate offset.
-template <typename T, int P, int Q, bool PRE>
+template <typename T, int P, int Q, bool PRE, bool KAP = false>
 __global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
   if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
@@ -796,6 +796,14 @@ __global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
         const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
         const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q) * N2;
         const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q) * N2;
+        // D_h (Sec. 4.2): jumps of component c of the same field f on the faces normal to a,
+        // own traces from y^f_c, the neighbour's from its staged traces; alpha-weights per face
+        const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
+        const T* zb = ys + (f * 3 + c) * Q * N3;
+        const T* gtp = nt + ((((2 * a + 1) * 2 + f) * 2 + bc) * Q) * N2;
+        const T* gtm = nt + ((((2 * a) * 2 + f) * 2 + bc) * Q) * N2;
+        const T kpp = KAP ? A.dt_k * A.kap[e * 24 + f * 12 + 4 * a + 2 + bc] : T(0);
+        const T kpm = KAP ? A.dt_k * A.kap[e * 24 + f * 12 + 4 * a + bc] : T(0);
         auto lines = [&](auto ac, auto negc) {
           constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
           constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
@@ -818,19 +826,45 @@ __global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
               const T om = hasm ? ntm[i * N2 + t] : ((fp == 0) ? neg_bits(xm) : xm);
               const T jp = xp - op, jm = xm - om;
               const T sp = jp + jm, dm = jp - jm;
-              // flux lift folded into the curl operand as in k_apply
-              constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
-              if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
-              if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
               T* Rl = Rp + i * N3 + base;
+              if constexpr (KAP) {
+                // own traces of y^f_c; on a PEC face the E jump is the own trace (E - g, g in
+                // the load) and the H jump 0; lifted with L_al(1) and L_al(0) = (-1)^al L_al(1)
+                const T* zl = zb + i * N3 + base;
+                T ze = T(0), zo = T(0);
 #pragma unroll
-              for (int al = 0; al < N; ++al) {
-                T r2 = Rl[al * ST];
-                if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+                for (int j = 0; j < N; ++j) {
+                  if (j & 1) zo = fma(A.tb.lv[j], zl[j * ST], zo);
+                  else ze = fma(A.tb.lv[j], zl[j * ST], ze);
+                }
+                const T zp = ze + zo, zm = ze - zo;
+                const T gop = hasp ? gtp[i * N2 + t] : (f == 0 ? T(0) : zp);
+                const T gom = hasm ? gtm[i * N2 + t] : (f == 0 ? T(0) : zm);
+                const T dp = kpp * (zp - gop), dn = kpm * (zm - gom);
+                const T zev = fma(-sg * A.tb.hf[0], dm, dp + dn), zod = fma(-sg * A.tb.hf[0], sp, dp - dn);
 #pragma unroll
-                for (int be = 0; be < N; ++be)
-                  if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
-                Rl[al * ST] = r2;
+                for (int al = 0; al < N; ++al) {
+                  T r2 = Rl[al * ST];
+                  r2 = fma(A.tb.lv[al], (al & 1) ? zod : zev, r2);
+#pragma unroll
+                  for (int be = 0; be < N; ++be)
+                    if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+                  Rl[al * ST] = r2;
+                }
+              } else {
+                // flux lift folded into the curl operand as in k_apply
+                constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
+                if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+                if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+#pragma unroll
+                for (int al = 0; al < N; ++al) {
+                  T r2 = Rl[al * ST];
+                  if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+                  for (int be = 0; be < N; ++be)
+                    if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+                  Rl[al * ST] = r2;
+                }
               }
             }
           }
@@ -1107,6 +1141,8 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
     if constexpr (sizeof(T) == 4) {
       cudaFuncSetAttribute(k_fused<T, P, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
       cudaFuncSetAttribute(k_fused<T, P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
+      cudaFuncSetAttribute(k_fused<T, P, Q, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
+      cudaFuncSetAttribute(k_fused<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
       cudaFuncSetAttribute(k_fused_kry<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fused_kry_smem(P, Q));
     }
@@ -1114,15 +1150,25 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
   });
   const bool hp = args.elist != nullptr;
   if constexpr (sizeof(T) == 4 && fused_fits(P, Q)) {
-    if (!hp && !args.kap) {
+    if (!hp) {
       // single pass: ev.start/ev.stop bracket k_fused (reported in the apply slot)
       if (ev.start) cudaEventRecord(ev.start, s);
       if (ev.mid) cudaEventRecord(ev.mid, s);
       // six warps: the 6 Q residual planes and the 24 neighbour-trace tasks divide evenly
       constexpr int kFusedThreads = 192;
       (void)block;
-      static std::atomic<int> cap_t[64], cap_f[64], cap_k[64];
-      if (fused_kry_smem(P, Q) <= 74 * 1024 && args.pinv && !args.u0 && !args.b && args.mass && !args.mass3) {
+      static std::atomic<int> cap_t[64], cap_f[64], cap_k[64], cap_dt[64], cap_df[64];
+      if (args.kap) {
+        // the dissipative term D_h (Sec. 4.2) in the same single pass
+        if (args.pinv)
+          k_fused<T, P, Q, true, true><<<wave_grid(k_fused<T, P, Q, true, true>, kFusedThreads, sm_fused, grid, cap_dt),
+                                         kFusedThreads, sm_fused, s>>>(args);
+        else
+          k_fused<T, P, Q, false, true>
+              <<<wave_grid(k_fused<T, P, Q, false, true>, kFusedThreads, sm_fused, grid, cap_df), kFusedThreads,
+                 sm_fused, s>>>(args);
+      } else if (fused_kry_smem(P, Q) <= 74 * 1024 && args.pinv && !args.u0 && !args.b && args.mass &&
+                 !args.mass3) {
         // the Krylov operator A P^{-1} v of the mixed-precision solve
         const size_t smk = fused_kry_smem(P, Q);
         k_fused_kry<P, Q><<<wave_grid(k_fused_kry<P, Q>, kFusedThreads, smk, grid, cap_k), kFusedThreads, smk, s>>>(

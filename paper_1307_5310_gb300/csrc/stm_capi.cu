@@ -422,10 +422,10 @@ const T* kap_ptr(stm_ctx* c) {
 }
 
 // Whether the residual kernels of precision T use the y / trace scratch: all but the
-// single-pass FP32 kernel (uniform meshes without D_h, shared memory within fused_fits).
+// single-pass FP32 kernel (uniform meshes, with or without D_h, shared memory within fused_fits).
 template <typename T>
 bool needs_scratch(const stm_ctx* c) {
-  return sizeof(T) == 8 || c->hp || c->kap64 || !fused_fits(c->P, c->Q);
+  return sizeof(T) == 8 || c->hp || !fused_fits(c->P, c->Q);
 }
 
 // Upper bound of the residual kernels' grids (grid-stride loops over elements): the launch

@@ -47,8 +47,10 @@ def test_residual_fp64(stm, nx, ny, nz, p, q):
     assert rel(stdg.Oracle(m).residual(U, 0.2, 0.05), Ro) > 1e-3
 
 
-def test_residual_fp32(stm):
-    m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.7, 1.3), p=3, q=2, order="morton")
+@pytest.mark.parametrize("p,q", [(3, 2), (4, 3), (7, 1), (5, 4), (0, 2)])
+def test_residual_fp32(stm, p, q):
+    """Single-pass FP32 kernel with D_h for every size whose shared memory fits (all of these)."""
+    m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.7, 1.3), p=p, q=q, order="morton")
     meshgen.random_materials(m, 1, 2)
     U = meshgen.random_coeffs(m, 3).astype(np.float32)
     Ro = stdg.Oracle(m, c_diss=C).residual(U.astype(np.float64), 0.2, 0.05)
@@ -135,3 +137,25 @@ def test_unsupported_meshes(stm):
     m["q"] = np.array([1, 2, 1, 2, 1, 2, 1, 2], dtype=np.uint8)
     with pytest.raises(stm.StmError):
         stm.Slab(m, c_diss=C)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_operator_with_dissipation(stm, prec):
+    """The GMRES operator A P^{-1} with D_h in A (P of Eq. preconditioner has no D_h term)."""
+    m = meshgen.box_mesh(3, 2, 2, p=4, q=3, order="morton")
+    meshgen.random_materials(m, 5, 6)
+    dt = 0.05
+    orc = stdg.Oracle(m, c_diss=C)
+    X = meshgen.random_coeffs(m, 7, kind="test")
+    U = np.zeros(int(orc.trial_off[-1]))
+    U[orc.unknown_mask()] = X
+    V, AX = orc.time_derivative(U, dt), orc.residual(U, 0.0, dt)
+    s = stm.Slab(m, c_diss=C)
+    if prec == "fp64":
+        W = np.empty(s.n_test)
+        s.operator_apply(V, W, dt, pre=True)
+        assert rel(W, AX) < 1e-12
+    else:
+        W = np.empty(s.n_test, np.float32)
+        s.operator_apply(V.astype(np.float32), W, dt, pre=True, prec=stm.STM_FP32)
+        assert rel(W, AX) < 2e-6
