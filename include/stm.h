@@ -251,9 +251,11 @@ int32_t stm_slab_solve(stm_ctx *ctx, double dt, stm_solve_report *rep);
 int32_t stm_energy(stm_ctx *ctx, double *energy);
 
 /* Autotuner (the paper has no counterpart): for every (p, q) class of the mesh
- * (one class on uniform meshes) time the residual kernels with 64, 128 and
- * 256 threads per block, reps times each, on scratch data of the mesh's own
- * layout, and keep the fastest for later applies.  Reports per class (up to
+ * (one class on uniform meshes) time the residual kernels with 64, 128, 256
+ * and 512 threads per block, reps times each, on scratch data of the mesh's
+ * own layout, and keep the fastest for later applies (before any autotune call
+ * a class uses 512 threads where the FP64 passes' shared memory leaves three or
+ * fewer blocks per SM, else 256).  Reports per class (up to
  * n_max) the degrees, the chosen block size and its time in ms; *n_out = the
  * number of classes.  Allocates scratch buffers for the duration of the call. */
 int32_t stm_autotune(stm_ctx *ctx, double dt, int32_t reps, int32_t n_max, int32_t *P, int32_t *Q,

@@ -216,9 +216,21 @@ __device__ __forceinline__ void line_geom(int a, int t, int& base, int& stride) 
   else { base = t; stride = N * N; }
 }
 
+// Largest block of the two-kernel residual passes (k_prep, k_apply) of degree (P, Q): 512
+// threads where the FP64 passes' shared memory (k_apply: y of the other field and the residual
+// rows, both fields per pass up to ~110 KB; k_prep: y) leaves three or fewer blocks per SM, so
+// an SM still holds 32+ warps; 256 elsewhere (a 512 bound there costs registers and blocks).
+__host__ __device__ constexpr int residual_max_threads(int P, int Q) {
+  return (8 * 2 * (12 * Q * (P + 1) * (P + 1) * (P + 1) * 8 > 110 * 1024 ? 1 : 2) * 3 * Q * (P + 1) * (P + 1) * (P + 1) >=
+              56 * 1024 ||
+          8 * 6 * Q * (P + 1) * (P + 1) * (P + 1) >= 56 * 1024)
+             ? 512
+             : 256;
+}
+
 // TR: the mesh has elements with N_K > 1 (HP only); false compiles the one-sub-interval code
 template <typename T, int P, int Q, bool HP, bool TR = false>
-__global__ void __launch_bounds__(256) k_prep(ApplyArgs<T> A) {
+__global__ void __launch_bounds__(residual_max_threads(P, Q)) k_prep(ApplyArgs<T> A) {
   if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -406,7 +418,7 @@ struct ApplyShape {
 };
 
 template <typename T, int P, int Q, bool HP, bool TR = false>
-__global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> A) {
+__global__ void __launch_bounds__(residual_max_threads(P, Q)) k_apply(ApplyArgs<T> A) {
   if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   constexpr int NF = ApplyShape<T, P, Q>::NF;
@@ -1183,9 +1195,10 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       return (int)cudaGetLastError();
     }
   }
-  // one-wave grids, cached per (kernel, block size: 64, 128 or 256) and device
-  static std::atomic<int> cap_p[3][3][64], cap_a[3][3][64];
-  const int bs = block <= 64 ? 0 : (block <= 128 ? 1 : 2);
+  // one-wave grids, cached per (kernel, block size: 64, 128, 256 or 512) and device
+  static std::atomic<int> cap_p[3][4][64], cap_a[3][4][64];
+  block = std::min(block, residual_max_threads(P, Q));
+  const int bs = block <= 64 ? 0 : (block <= 128 ? 1 : (block <= 256 ? 2 : 3));
   if (phase != 2) {
     if (ev.start) cudaEventRecord(ev.start, s);
     if (hp && args.nkl) {

@@ -435,6 +435,11 @@ int res_grid(const stm_ctx* c, int64_t count) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(count, 1 << 30));
 }
 
+// Default threads per block of the two-kernel residual passes of degree (P, Q): the kernels'
+// largest block (residual_max_threads: 512 where shared memory limits the blocks per SM, else
+// 256).  The autotuner may replace it.
+int default_block(int P, int Q) { return residual_max_threads(P, Q); }
+
 template <typename T>
 int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0_layout, const T* b, T* R,
           bool pre = false, const int32_t* skip = nullptr) {
@@ -1388,6 +1393,7 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
   c->ne = m->n_elem;
   c->P = m->p[0];
   c->Q = m->q[0];
+  c->block = default_block(c->P, c->Q);
   c->h_p.resize(c->ne);
   c->h_q.resize(c->ne);
   for (int64_t e = 0; e < c->ne; ++e) {
@@ -1766,7 +1772,7 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
         for (int lk = 0; lk < 4 && okh; ++lk) {
           const auto& L = lists[(pp * (kMaxQ + 1) + qq) * 4 + lk];
           if (L.empty()) continue;
-          stm_ctx::Class cl{pp, qq, (int64_t)L.size(), nullptr, 256};
+          stm_ctx::Class cl{pp, qq, (int64_t)L.size(), nullptr, default_block(pp, qq)};
           cl.NK = 1 << lk;
           okh = cudaMalloc(&cl.elist, L.size() * sizeof(int32_t)) == cudaSuccess;
           if (okh) cudaMemcpy(cl.elist, L.data(), L.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -2442,7 +2448,7 @@ int32_t stm_dof_layout(stm_ctx* c, int64_t* off_trial, int64_t* off_test, int64_
 }  // extern "C"
 
 // Autotuner: for every (p, q) class (or the whole uniform mesh) time the
-// residual kernels with 64, 128 and 256 threads per block on the context's
+// residual kernels with 64, 128, 256 and 512 threads per block on the context's
 // own data layout and keep the fastest; later applies use it.
 template <typename T>
 int autotune_prec(stm_ctx* c, double dt, int reps, std::vector<double>& best_ms) {
@@ -2459,13 +2465,15 @@ int autotune_prec(stm_ctx* c, double dt, int reps, std::vector<double>& best_ms)
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cands[3] = {64, 128, 256};
+  const int cands[4] = {64, 128, 256, 512};
   const size_t ncl = c->hp ? c->classes.size() : 1;
   best_ms.assign(ncl, 0.0);
   for (size_t k = 0; k < ncl && rc == STM_OK; ++k) {
     double best = 1e30;
     int bb = 256;
+    const int P = c->hp ? c->classes[k].P : c->P, Q = c->hp ? c->classes[k].Q : c->Q;
     for (int cb : cands) {
+      if (cb > residual_max_threads(P, Q)) continue;  // beyond the kernels' launch bound
       if (c->hp) c->classes[k].block = cb;
       else c->block = cb;
       float ms = 0.f;
