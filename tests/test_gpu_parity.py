@@ -196,3 +196,65 @@ def test_slab_solve_mixed_precision(stm, reorth):
     rc, rep64 = s64.slab_solve(dt)
     assert rc == stm.STM_OK
     assert rel(s64.get_state()[0], uo) < 1e-9
+
+
+def test_headline_full_size_sampled(stm):
+    """The bench workload in the launch configuration the bench times: 64^3 bricks in Morton
+    order, p = 4, q = 3, eps/mu ~ U[1,4] (PCG64 1307/1308), coefficients ~ U[-1,1] (1309).
+    FP64 residual, FP32 residual (single-pass kernel), and the GMRES operator A P^{-1} in FP64
+    and FP32 (the mixed solve's Krylov kernel), each checked against the oracle on sampled
+    elements (corners, faces and random interior ones) with their face neighbours.  For the
+    operator, V = P X with P from its closed form on bricks (mat_f G_c, pinned against the
+    oracle's time-derivative form), so the expected value is the oracle's residual of X."""
+    import torch
+
+    n, p, q = 64, 4, 3
+    m = meshgen.box_mesh(n, p=p, q=q, order="morton")
+    meshgen.random_materials(m, 1307, 1308)
+    ne, n3 = m["hex"].shape[0], (p + 1) ** 3
+    tper, per = 6 * (q + 1) * n3, 6 * q * n3
+    dt = (1.0 / n) / (2 * p + 1)
+    rng = np.random.Generator(np.random.PCG64(1311))
+    sample = sorted(set([0, ne - 1, int(np.argmax(m["vert"][m["hex"][:, 7]].sum(1)))] +
+                        [int(x) for x in rng.integers(0, ne, 9)]))
+    keep = set(sample)
+    for e in sample:
+        keep |= {int(x) for x in m["nbr"][e] if x >= 0}
+    keep = np.array(sorted(keep))
+    sub = {k: m[k][keep] for k in ("hex", "p", "q", "eps", "mu")}
+    sub.update(vert=m["vert"], geometry=m["geometry"])
+    loc = {int(e): i for i, e in enumerate(keep)}
+    o = stdg.Oracle(sub)
+    s = stm.Slab(m)
+
+    def check(Rdev, Ublocks, bar):
+        Rs = Rdev.view(ne, per)[torch.tensor(sample, device=Rdev.device)].double().cpu().numpy()
+        for k, e in enumerate(sample):
+            Ro = o.element_residual(loc[e], Ublocks, 0.0, dt)[0].ravel()
+            assert rel(Rs[k], Ro) < bar, (e, rel(Rs[k], Ro))
+
+    U = meshgen.random_coeffs(m, 1309)
+    Ud = torch.from_numpy(U).cuda()
+    Rd = torch.empty(s.n_test, dtype=torch.float64, device="cuda")
+    s.residual_apply(Ud, Rd, 0.0, dt)
+    check(Rd, np.concatenate([U[e * tper:(e + 1) * tper] for e in keep]), 1e-12)
+    U32 = Ud.float()
+    R32 = torch.empty(s.n_test, dtype=torch.float32, device="cuda")
+    s.residual_apply(U32, R32, 0.0, dt, prec=stm.STM_FP32)
+    U32h = U32.view(ne, tper)[torch.from_numpy(keep).cuda()].double().cpu().numpy().ravel()
+    check(R32, U32h, 2e-6)
+    del Ud, U32, Rd, R32, U
+
+    # the operator: X unknowns (test layout), V = P X = mat_f G_c X, G_c = h on cubes of edge h
+    X = torch.from_numpy(meshgen.random_coeffs(m, 1310, kind="test")).cuda()
+    mats = torch.from_numpy(np.stack([m["eps"], m["mu"]], 1) / n).cuda()
+    V = (X.view(ne, 2, 3 * q * n3) * mats[:, :, None]).reshape(-1)
+    Xk = X.view(ne, per)[torch.from_numpy(keep).cuda()].cpu().numpy()
+    Ux = np.zeros((len(keep), 2, 3, q + 1, n3))
+    Ux[:, :, :, 1:, :] = Xk.reshape(len(keep), 2, 3, q, n3)
+    W = torch.empty(s.n_test, dtype=torch.float64, device="cuda")
+    s.operator_apply(V, W, dt, pre=True)
+    check(W, Ux.ravel(), 1e-12)
+    W32 = torch.empty(s.n_test, dtype=torch.float32, device="cuda")
+    s.operator_apply(V.float(), W32, dt, pre=True, prec=stm.STM_FP32)
+    check(W32, Ux.ravel(), 2e-6)
