@@ -909,6 +909,20 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ---- bulk copies shared -> global through the tensor memory accelerator (bulk groups) ----
+// Orders this thread's earlier shared-memory writes before later async-proxy reads of them.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// bytes: a multiple of 16; dst and src 16-byte aligned.
+__device__ __forceinline__ void bulk_store(float* dst, const float* src, int bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst),
+               "r"((uint32_t)__cvta_generic_to_shared(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Waits (in hardware) until this thread's committed bulk copies have read their sources / completed.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // Floats of a staging slot for n floats: n plus up to 3 of alignment shift, rounded to 16 bytes.
 __host__ __device__ constexpr int stage_slot(int n) { return (n + 6) & ~3; }
 
@@ -928,23 +942,39 @@ __device__ __forceinline__ const float* stage_warp(float* slot, const float* src
   return dst;
 }
 
+// Shared memory of k_fused_kry: k_fused's (the residual block with 4 floats of slack) plus six
+// warps' two staging slots each.
+__host__ __device__ constexpr size_t kry_stage_offset(int P, int Q) {
+  return ((sizeof(float) * (12 * Q * (P + 1) * (P + 1) * (P + 1) + 4 + 24 * Q * (P + 1) * (P + 1))) + 15) &
+         ~size_t(15);
+}
+__host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
+  return kry_stage_offset(P, Q) + sizeof(float) * 12 * stage_slot(Q * (P + 1) * (P + 1) * (P + 1));
+}
+
 // Single-pass FP32 Krylov apply A P^{-1} v on uniform brick meshes (no slab-start mode, no
 // load): the inner operator of the mixed-precision solve.  Same arithmetic as k_fused with
 // PRE, specialised: (a) forms y = sc B v and the mass term (v itself) with no branches on the
 // generic inputs; (b) stages each neighbour's two tangential component blocks into shared
 // memory with coalesced cp.async copies (one warp per (face, field), two rounds of six) and
 // forms its face traces from there, so the strided trace reads hit shared memory, not L1/L2;
-// (c) and the store are k_fused's.  Launched with 192 threads (six warps).
+// (c) the line passes are k_fused's; (d) the residual block leaves shared memory by one bulk
+// copy (cp.async.bulk, completion by bulk-group waits, no polling), placed in shared memory at
+// its offset modulo 16 bytes in R so only the at most 3 + 3 floats around the 16-byte aligned
+// body need plain stores.  Launched with 192 threads (six warps).
 template <int P, int Q>
 __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
   using T = float;
   if (A.skip && *A.skip) return;
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N, SS = stage_slot(Q * N3);
+  constexpr int EB = 6 * Q * N3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ys = reinterpret_cast<T*>(smem_raw);  // [2][3][Q][N3] temporal contraction
-  T* Rs = ys + 6 * Q * N3;                  // [2][3][Q][N3] residual planes (start: the mass term)
-  T* nt = Rs + 6 * Q * N3;                  // [6 faces][2 fields][2 comps][Q][N2] neighbour traces
-  T* stg = reinterpret_cast<T*>(smem_raw + ((sizeof(T) * (12 * Q * N3 + 24 * Q * N2) + 15) & ~size_t(15)));
+  // [2][3][Q][N3] residual planes (start: the mass term), placed per element at the offset modulo
+  // 16 bytes of its block in R (4 floats of slack), so the block leaves by one bulk copy
+  T* Rb = reinterpret_cast<T*>(smem_raw);
+  T* ys = Rb + EB + 4;  // [2][3][Q][N3] temporal contraction
+  T* nt = ys + EB;      // [6 faces][2 fields][2 comps][Q][N2] neighbour traces
+  T* stg = reinterpret_cast<T*>(smem_raw + kry_stage_offset(P, Q));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* slot = stg + warp * 2 * SS;  // this warp's two component slots
   const int um_cs = (int)A.um_cs;
@@ -1009,10 +1039,15 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
   for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x) {
     const int32_t* nb = A.nbr + e * 6;
     const T* ume = A.um + e * A.um_es;
-    const int64_t re = e * (int64_t)(6 * Q * N3);
+    T* Rg = A.R + e * (int64_t)EB;
+    const int shift = (int)((reinterpret_cast<uintptr_t>(Rg) >> 2) & 3);
+    T* Rs = Rb + shift;
     // round 1 of the neighbour copies in flight while the own block is contracted
     const T* src[2];
     bool have = issue(e, warp, src);
+    // the previous element's residual has left shared memory (its bulk copy has read it)
+    if (threadIdx.x == 0) bulk_wait_read();
+    __syncthreads();
     // (a) y = sc B v and the mass term v (the mass block times P^{-1} is the identity)
     for (int it = threadIdx.x; it < 6 * N3; it += 192) {
       const int fc = it / N3, s = it - fc * N3;
@@ -1104,18 +1139,24 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
         });
         __syncwarp();
       }
-      T* Rg = A.R + re + fc * Q * N3;
-      for (int s2 = lane; s2 < Q * N3; s2 += 32) Rg[s2] = Rp[s2];
     }
+    // (d) the residual block to R: the 16-byte aligned body by one bulk copy, the at most 3 + 3
+    //     floats around it by plain stores
+    fence_proxy_async_smem();
     __syncthreads();
+    const int head = min((4 - shift) & 3, EB), nb16 = (EB - head) >> 2, t0 = head + 4 * nb16;
+    if (threadIdx.x == 0) {
+      if (nb16 > 0) bulk_store(Rg + head, Rs + head, nb16 * 16);
+      bulk_commit();
+    } else if (threadIdx.x <= head) {
+      Rg[threadIdx.x - 1] = Rs[threadIdx.x - 1];
+    } else if (threadIdx.x > 4 && threadIdx.x - 5 < EB - t0) {
+      Rg[t0 + threadIdx.x - 5] = Rs[t0 + threadIdx.x - 5];
+    }
   }
+  if (threadIdx.x == 0) bulk_wait_all();
 }
 
-// Shared memory of k_fused_kry: k_fused's plus six warps' two staging slots each.
-__host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
-  return ((sizeof(float) * (12 * Q * (P + 1) * (P + 1) * (P + 1) + 24 * Q * (P + 1) * (P + 1)) + 15) & ~size_t(15)) +
-         sizeof(float) * 12 * stage_slot(Q * (P + 1) * (P + 1) * (P + 1));
-}
 
 // Optional CUDA events recorded before k_prep, between the kernels and after
 // k_apply (all null: no timing).
