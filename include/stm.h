@@ -182,7 +182,10 @@ int32_t stm_residual_apply(stm_ctx *ctx, double t0, double dt, const void *U, vo
  * buffers the context owns) or device memory (STM_MEM_DEVICE, caller-owned; V is
  * not modified, V and W must not overlap).  Returns STM_EINVAL for a null
  * pointer, dt <= 0 or a bad prec/mem/pre value, STM_ENOMEM when a staging
- * buffer cannot be allocated, STM_EDEVICE on a CUDA error. */
+ * buffer cannot be allocated, STM_EDEVICE on a CUDA error, STM_ETIMEOUT if a
+ * bounded device wait of the FP32 kernel on its asynchronous copies ran out (W
+ * is then invalid; the call synchronises the stream to read that flag when
+ * prec = STM_FP32 and pre = 1). */
 int32_t stm_operator_apply(stm_ctx *ctx, double dt, const void *V, void *W, int32_t pre,
                            int32_t prec, int32_t mem);
 
@@ -207,7 +210,8 @@ int32_t stm_set_initial(stm_ctx *ctx, double t, stm_field_fn E0, stm_field_fn H0
  *   J(x, t) = sum_k amp_k dir_k exp(-|x - centre_k|^2 / (2 sigma_x^2)) exp(-(t - t0_k)^2 / (2 sigma_t^2)).
  * It enters the load l_E(v) = (J, v) of Eq. bilinearform:C, integrated on the
  * device with p+2 Gauss points per direction and q+2 in time (on meshes with
- * uneven degrees or N_K > 1: on the host, per element and sub-interval).
+ * uneven degrees or N_K > 1 each element with its own p, q and sub-intervals,
+ * one launch per (p, q, N_K) class).
  * n_src = 0 removes all sources.  The array is copied. */
 typedef struct {
   double centre[3], dir[3];
@@ -231,8 +235,9 @@ int32_t stm_set_boundary(stm_ctx *ctx, stm_st_field_fn g, void *user);
  * time; the callback gets npts space-time points (x, y, z, t) and writes J.
  * Added to the Gaussian sources of stm_set_source_gauss.  Any mesh: on uneven
  * (p, q) or time-refined meshes each element uses its own degrees and N_K
- * sub-intervals (there the Gaussian sources and the boundary data are
- * assembled on the host the same way); NULL removes it.  The library keeps the
+ * sub-intervals (there the boundary data are assembled on the host the same
+ * way; Gaussian sources are projected on the device per (p, q, N_K) class);
+ * NULL removes it.  The library keeps the
  * pointer; the caller keeps the callback alive while the context uses it. */
 int32_t stm_set_source(stm_ctx *ctx, stm_st_field_fn J, void *user);
 
@@ -244,7 +249,9 @@ int32_t stm_dof_layout(stm_ctx *ctx, int64_t *off_trial, int64_t *off_test, int6
 /* Solve one slab (Sec. 5.4): find modes 1..q of U with R_h(U) = 0 by GMRES
  * (restart opts.restart, right preconditioned by the time-derivative terms of
  * Eq. preconditioner), starting from the state; on return the state is the
- * field at t + dt.  opts.precision selects FP64 or mixed precision. */
+ * field at t + dt.  opts.precision selects FP64 or mixed precision.  Returns
+ * STM_ETIMEOUT (state not advanced) if a bounded device wait of a kernel ran
+ * out. */
 int32_t stm_slab_solve(stm_ctx *ctx, double dt, stm_solve_report *rep);
 
 /* Discrete energy 1/2 int eps E.E + mu H.H of the state (Eq. stability:energydef), FP64. */

@@ -118,6 +118,8 @@ struct ApplyArgs {
   // general affine elements (uniform meshes): mass3[e][f][6] = mat_f G with the constant
   // metric G = |J| DF^{-1} DF^{-T} in the order xx, yy, zz, xy, xz, yz; mass is then null
   const T* mass3 = nullptr;
+  // set to 1 by a kernel whose bounded wait on an asynchronous copy ran out (its R is invalid)
+  int* err = nullptr;
 };
 
 // Grid of a grid-stride residual kernel: at most one wave of co-resident CTAs (the
@@ -923,6 +925,64 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
+// ---- bulk copies global -> shared, completed on an mbarrier (transaction bytes) ----
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bytes: a multiple of 16; dst and src 16-byte aligned.
+__device__ __forceinline__ void bulk_load(float* dst, const float* src, int bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          (uint32_t)__cvta_generic_to_shared(dst)),
+      "l"(src), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+// Polls the barrier's phase `parity` at most `tries` times; true once it has completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int tries) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  for (int k = 0; k < tries; ++k) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// One warp copies the n floats at src (4-byte aligned) into the 16-byte aligned slot (layout as
+// stage_warp): lane 0 issues the 16-byte aligned body as one bulk copy completing on `bar`, the
+// at most 3 + 3 floats around it move by plain loads and stores.  Returns the body's bytes (the
+// caller announces the sum of a round's bodies on `bar` before the copies are issued: see
+// stage_bytes) and sets *dst_out.
+__device__ __forceinline__ int stage_bytes(const float* src, int n) {
+  const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+  const int head = min((4 - mis) & 3, n);
+  return ((n - head) >> 2) * 16;
+}
+__device__ __forceinline__ const float* stage_warp_bulk(float* slot, const float* src, int n, int lane,
+                                                        uint64_t* bar) {
+  const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+  float* dst = slot + mis;
+  const int head = min((4 - mis) & 3, n);
+  const int nb = (n - head) >> 2;
+  const int t0 = head + 4 * nb;
+  if (lane == 0 && nb > 0) bulk_load(dst + head, src + head, nb * 16, bar);
+  if (lane < head) dst[lane] = src[lane];
+  if (lane >= 4 && lane - 4 < n - t0) dst[t0 + lane - 4] = src[t0 + lane - 4];
+  return dst;
+}
+
 // Floats of a staging slot for n floats: n plus up to 3 of alignment shift, rounded to 16 bytes.
 __host__ __device__ constexpr int stage_slot(int n) { return (n + 6) & ~3; }
 
@@ -949,7 +1009,7 @@ __host__ __device__ constexpr size_t kry_stage_offset(int P, int Q) {
          ~size_t(15);
 }
 __host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
-  return kry_stage_offset(P, Q) + sizeof(float) * 12 * stage_slot(Q * (P + 1) * (P + 1) * (P + 1));
+  return kry_stage_offset(P, Q) + sizeof(float) * 12 * stage_slot(Q * (P + 1) * (P + 1) * (P + 1)) + 6 * 8;
 }
 
 // Single-pass FP32 Krylov apply A P^{-1} v on uniform brick meshes (no slab-start mode, no
@@ -977,6 +1037,14 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
   T* stg = reinterpret_cast<T*>(smem_raw + kry_stage_offset(P, Q));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* slot = stg + warp * 2 * SS;  // this warp's two component slots
+  // this warp's barrier for its staging copies (after the slots; 8-byte aligned)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stg + 12 * SS) + warp;
+  __shared__ int failed;  // a bounded wait ran out: every warp leaves at the next barrier
+  if (threadIdx.x == 0) failed = 0;
+  if (lane == 0) mbar_init(bar, 1);
+  mbar_init_fence();
+  __syncthreads();
+  uint32_t parity = 0;
   const int um_cs = (int)A.um_cs;
   // issues the copies of task (face, fld) = (task >> 1, task & 1): the neighbour's two
   // tangential components; returns false (nothing issued) on a boundary face
@@ -985,13 +1053,37 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
     const int64_t en = A.nbr[e * 6 + face];
     if (en < 0) return false;
     const T* ue = A.um + en * A.um_es;
+    // this warp's reads of the slots (generic proxy) come before the next bulk writes into them
+    fence_proxy_async_smem();
+    __syncwarp();
+    const T* cs[2];
+    int bytes = 0;
 #pragma unroll
     for (int bi = 0; bi < 2; ++bi) {
       const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
-      src[bi] = stage_warp(slot + bi * SS, ue + (fld * 3 + b) * um_cs, Q * N3, lane);
+      cs[bi] = ue + (fld * 3 + b) * um_cs;
+      bytes += stage_bytes(cs[bi], Q * N3);
     }
-    cp_async_commit();
+    if (lane == 0) mbar_arrive_tx(bar, bytes);  // announced before the copies can complete
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi) src[bi] = stage_warp_bulk(slot + bi * SS, cs[bi], Q * N3, lane, bar);
     return true;
+  };
+  // waits for the round's copies (bounded: 1 << 22 polls), then makes the plain-stored floats
+  // of the other lanes visible; false if the wait ran out
+  bool my_fail = false;  // this warp's copies of the round that timed out may still be in flight
+  auto arrived = [&]() -> bool {
+    const bool ok = mbar_wait(bar, parity, 1 << 22);
+    parity ^= 1;
+    __syncwarp();
+    if (!ok) {
+      my_fail = true;
+      if (lane == 0) {
+        failed = 1;
+        if (A.err) atomicExch(A.err, 1);
+      }
+    }
+    return ok;
   };
   // the traces of task `task` from the staged blocks
   auto traces = [&](int64_t e, int task, const T* const* src) {
@@ -1069,19 +1161,18 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
       }
     }
     // (b) neighbour traces: two rounds of six (face, field) tasks, one per warp
+    bool ok = true;
     if (have) {
-      cp_async_wait_all();
-      __syncwarp();
-      traces(e, warp, src);
+      ok = arrived();
+      if (ok) traces(e, warp, src);
       __syncwarp();  // the slots are refilled next
     }
-    have = issue(e, warp + 6, src);
-    if (have) {
-      cp_async_wait_all();
-      __syncwarp();
-      traces(e, warp + 6, src);
+    if (ok) {
+      have = issue(e, warp + 6, src);
+      if (have && arrived()) traces(e, warp + 6, src);
     }
     __syncthreads();
+    if (failed) break;  // uniform: read after the barrier
     // (c) residual planes: one warp per (field, component), all Q temporal test modes
     for (int fc = warp; fc < 6; fc += 6) {
       const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f, fp = 1 - f;
@@ -1155,6 +1246,7 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
     }
   }
   if (threadIdx.x == 0) bulk_wait_all();
+  if (my_fail && lane == 0) mbar_wait(bar, parity ^ 1, 1 << 22);  // let a late copy land before exit
 }
 
 

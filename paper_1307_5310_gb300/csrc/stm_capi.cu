@@ -262,6 +262,7 @@ struct stm_ctx {
   double* mass3_64 = nullptr;  // general affine elements: [ne][2][6] mat * G (constant metric)
   float* mass3_32 = nullptr;
   int* tc_err = nullptr;       // trilinear meshes: set by the tensor-core mass kernel if a wait ran out
+  int* wait_err = nullptr;     // set by the FP32 Krylov kernel if a bounded wait on its copies ran out
   double* el = nullptr;      // per-element energies (curved)
   CurvedTables ct{};
   // load vector L (Gaussian currents, boundary data g), cached per (t0, dt)
@@ -435,6 +436,18 @@ int res_grid(const stm_ctx* c, int64_t count) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(count, 1 << 30));
 }
 
+// STM_ETIMEOUT if a bounded wait of the FP32 Krylov kernel on its asynchronous copies ran out
+// (the flag stays set: every later result of the context is suspect), else STM_OK.
+int check_wait_err(stm_ctx* c) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, c->wait_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    return fail(c, STM_EDEVICE, std::string("error flag read: ") + cudaGetErrorString(e));
+  }
+  return h ? fail(c, STM_ETIMEOUT, "FP32 Krylov kernel: a bounded wait on its copies ran out") : STM_OK;
+}
+
 // Default threads per block of the two-kernel residual passes of degree (P, Q): the kernels'
 // largest block (residual_max_threads: 512 where shared memory limits the blocks per SM, else
 // 256).  The autotuner may replace it.
@@ -459,6 +472,7 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
   a.dt_k = (T)dt;
   a.pinv = pre ? pinv_ptr<T>(c) : nullptr;
   a.skip = skip;
+  a.err = c->wait_err;
   const int N3 = c->N3, Q = c->Q;
   if (c->hp) {
     a.um = um;
@@ -1674,6 +1688,7 @@ int32_t stm_create(stm_ctx** out, const stm_mesh* m, const stm_opts* o) {
             cudaMalloc(&c->state, c->n_state * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->red_partial, (kMaxDots + 1) * kRedBlocks * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->red_out, (kMaxDots + 1) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->wait_err, sizeof(int)) == cudaSuccess && cudaMemset(c->wait_err, 0, sizeof(int)) == cudaSuccess &&
             cudaMallocHost(&c->h_pinned, (kMaxDots + 1) * sizeof(double)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -1897,7 +1912,7 @@ int32_t stm_destroy(stm_ctx* c) {
                   c->x,       c->V32,     c->z32,    c->inv64, c->inv32, c->X8, c->eps64, c->mu64,
                   c->eps32,   c->mu32,    c->Gw64,   c->Gw32,  c->Pinv64, c->Pinv32, c->el, c->load64, c->load32,
                   c->sw64,    c->sw32,    c->kap64,  c->kap32, c->nkl,    c->tmat64, c->tmat32,
-                  c->mass3_64, c->mass3_32, c->tc_err};
+                  c->mass3_64, c->mass3_32, c->tc_err, c->wait_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -2001,7 +2016,8 @@ int32_t stm_operator_apply(stm_ctx* c, double dt, const void* V, void* W, int32_
     }
     return linop_pre<S>(c, dt, v, w);
   };
-  const int rc = prec == STM_FP64 ? run(double{}) : run(float{});
+  int rc = prec == STM_FP64 ? run(double{}) : run(float{});
+  if (!rc && prec == STM_FP32 && pre) rc = check_wait_err(c);
   if (rc) return rc;
   if (mem == STM_MEM_HOST) {
     STM_CK(cudaMemcpyAsync(W, c->tmp_out, c->n_test * es, cudaMemcpyDeviceToHost, c->stream));
@@ -2394,6 +2410,7 @@ int32_t stm_slab_solve(stm_ctx* c, double dt, stm_solve_report* rep) {
     STM_CK(cudaStreamSynchronize(c->stream));
     if (h_err) return fail(c, STM_ETIMEOUT, "tensor-core mass kernel: a bounded wait ran out");
   }
+  if (int rc = check_wait_err(c)) return rc;
   if (c->hp) extract_end_hp(c->state, c->x, c->off_test, c->off_state, c->pq, c->ne, c->stream);
   else k_extract_end<<<grid1(c->n_state), 256, 0, c->stream>>>(c->state, c->x, c->Q, c->N3, c->n_state);
   c->launches += 1;
