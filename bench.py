@@ -872,7 +872,12 @@ def run_ours(args):
                 "fp64_probe_tflops": probe, "frac_of_probe": (ach / probe) if probe else None,
                 "prep": {"kernel": f"k_prep<double,{args.p},{args.q}>", "launch_ms": prep_ms,
                          "achieved": fl_prep * ne / (prep_ms / 1e3) / 1e12,
-                         "frac": fl_prep * ne / (prep_ms / 1e3) / 1e12 / fp64_peak}}
+                         "frac": fl_prep * ne / (prep_ms / 1e3) / 1e12 / fp64_peak},
+                # the whole FP64 residual apply (both launches, the flop model of both)
+                "combined": {"kernels": f"k_prep + k_apply <double,{args.p},{args.q}>",
+                             "launch_ms": prep_ms + apply_ms,
+                             "achieved": (fl_prep + fl_apply) * ne / ((prep_ms + apply_ms) / 1e3) / 1e12,
+                             "frac": (fl_prep + fl_apply) * ne / ((prep_ms + apply_ms) / 1e3) / 1e12 / fp64_peak}}
 
     # ---- end to end through the C ABI with pinned host buffers ---------------------------------
     hb_in, hb_out = stm.HostBuffer(u_host.numel()), stm.HostBuffer(u_host.numel())
