@@ -652,6 +652,111 @@ __device__ __forceinline__ void with_axis(int a, F&& f) {
   else f(std::integral_constant<int, 2>{});
 }
 
+// The two derivative passes over the residual planes of field f, component c of one element
+// (single-pass FP32 kernels): for every temporal test mode, lines along each axis a != c add the
+// curl of y of the other field (component b = 3 - c - a) and the flux lift of its jumps, folded
+// into the curl operand (own traces from y, the other side from the neighbour traces nt or the
+// PEC mirror); with KAP also the dissipative term D_h of Sec. 4.2 (jumps of y^f_c, unfolded
+// lift).  Rp: the (f, c) planes [Q][N3] in shared memory, holding the mass term; ys: y of both
+// fields [2][3][Q][N3]; nt: neighbour traces [6 faces][2 fields][2 comps][Q][N2]; nb: the six
+// neighbours of element e.  One warp, lanes over the lines of a pass.
+template <typename T, int N, int Q, bool KAP>
+__device__ __forceinline__ void fused_lines(const ApplyArgs<T>& A, int64_t e, int f, int c, const T* ys,
+                                            const T* nt, const int32_t* nb, T* Rp, int lane) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int fp = 1 - f;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
+    const int b = 3 - c - a;
+    const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
+    // sign s_F eps_{cab} of the planes' terms along a (warp-uniform)
+    const bool neg = ((f == 0) == (((a - c + 3) % 3) == 1));
+    const T* yb = ys + (fp * 3 + b) * Q * N3;
+    const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
+    const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q) * N2;
+    const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q) * N2;
+    // D_h (Sec. 4.2): jumps of component c of the same field f on the faces normal to a,
+    // own traces from y^f_c, the neighbour's from its staged traces; alpha-weights per face
+    const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
+    const T* zb = ys + (f * 3 + c) * Q * N3;
+    const T* gtp = nt + ((((2 * a + 1) * 2 + f) * 2 + bc) * Q) * N2;
+    const T* gtm = nt + ((((2 * a) * 2 + f) * 2 + bc) * Q) * N2;
+    const T kpp = KAP ? A.dt_k * A.kap[e * 24 + f * 12 + 4 * a + 2 + bc] : T(0);
+    const T kpm = KAP ? A.dt_k * A.kap[e * 24 + f * 12 + 4 * a + bc] : T(0);
+    auto lines = [&](auto ac, auto negc) {
+      constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
+      constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
+      for (int t = lane; t < N2; t += 32) {
+        const int base = line_base<N, AX>(t);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const T* yl = yb + i * N3 + base;
+          T yv[N];
+          T ev = T(0), od = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            yv[j] = yl[j * ST];
+            if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
+            else ev = fma(A.tb.lv[j], yv[j], ev);
+          }
+          const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
+          // other side: neighbour trace, or the PEC mirror (E: -own, H: +own)
+          const T op = hasp ? ntp[i * N2 + t] : ((fp == 0) ? neg_bits(xp) : xp);
+          const T om = hasm ? ntm[i * N2 + t] : ((fp == 0) ? neg_bits(xm) : xm);
+          const T jp = xp - op, jm = xm - om;
+          const T sp = jp + jm, dm = jp - jm;
+          T* Rl = Rp + i * N3 + base;
+          if constexpr (KAP) {
+            // own traces of y^f_c; on a PEC face the E jump is the own trace (E - g, g in
+            // the load) and the H jump 0; lifted with L_al(1) and L_al(0) = (-1)^al L_al(1)
+            const T* zl = zb + i * N3 + base;
+            T ze = T(0), zo = T(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              if (j & 1) zo = fma(A.tb.lv[j], zl[j * ST], zo);
+              else ze = fma(A.tb.lv[j], zl[j * ST], ze);
+            }
+            const T zp = ze + zo, zm = ze - zo;
+            const T gop = hasp ? gtp[i * N2 + t] : (f == 0 ? T(0) : zp);
+            const T gom = hasm ? gtm[i * N2 + t] : (f == 0 ? T(0) : zm);
+            const T dp = kpp * (zp - gop), dn = kpm * (zm - gom);
+            const T zev = fma(-sg * A.tb.hf[0], dm, dp + dn), zod = fma(-sg * A.tb.hf[0], sp, dp - dn);
+#pragma unroll
+            for (int al = 0; al < N; ++al) {
+              T r2 = Rl[al * ST];
+              r2 = fma(A.tb.lv[al], (al & 1) ? zod : zev, r2);
+#pragma unroll
+              for (int be = 0; be < N; ++be)
+                if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+              Rl[al * ST] = r2;
+            }
+          } else {
+            // flux lift folded into the curl operand as in k_apply
+            constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
+            if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
+            if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
+#pragma unroll
+            for (int al = 0; al < N; ++al) {
+              T r2 = Rl[al * ST];
+              if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
+#pragma unroll
+              for (int be = 0; be < N; ++be)
+                if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
+              Rl[al * ST] = r2;
+            }
+          }
+        }
+      }
+    };
+    with_axis(a, [&](auto ac) {
+      if (neg) lines(ac, std::true_type{});
+      else lines(ac, std::false_type{});
+    });
+    __syncwarp();
+  }
+}
+
 // Single-pass variant (used for FP32, where the kernel is bound by memory
 // traffic, not arithmetic): one CTA per element at a time reads its own
 // coefficients once, recomputes the six neighbour face traces from the
@@ -797,98 +902,9 @@ __global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
     // (c) residual planes: one warp per (field, component) at a time, all Q temporal test
     //     modes of it, so the axis, sign, pointers and line geometry are set up once per pass
     for (int fc = warp; fc < 6; fc += nwarp) {
-      const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f, fp = 1 - f;
+      const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f;
       T* Rp = Rs + fc * Q * N3;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
-        const int b = 3 - c - a;
-        const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
-        // sign s_F eps_{cab} of the planes' terms along a (warp-uniform)
-        const bool neg = ((f == 0) == (((a - c + 3) % 3) == 1));
-        const T* yb = ys + (fp * 3 + b) * Q * N3;
-        const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
-        const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q) * N2;
-        const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q) * N2;
-        // D_h (Sec. 4.2): jumps of component c of the same field f on the faces normal to a,
-        // own traces from y^f_c, the neighbour's from its staged traces; alpha-weights per face
-        const int bc = (a == 0) ? c - 1 : (a == 1 ? c / 2 : c);
-        const T* zb = ys + (f * 3 + c) * Q * N3;
-        const T* gtp = nt + ((((2 * a + 1) * 2 + f) * 2 + bc) * Q) * N2;
-        const T* gtm = nt + ((((2 * a) * 2 + f) * 2 + bc) * Q) * N2;
-        const T kpp = KAP ? A.dt_k * A.kap[e * 24 + f * 12 + 4 * a + 2 + bc] : T(0);
-        const T kpm = KAP ? A.dt_k * A.kap[e * 24 + f * 12 + 4 * a + bc] : T(0);
-        auto lines = [&](auto ac, auto negc) {
-          constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
-          constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
-          for (int t = lane; t < N2; t += 32) {
-            const int base = line_base<N, AX>(t);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-              const T* yl = yb + i * N3 + base;
-              T yv[N];
-              T ev = T(0), od = T(0);
-#pragma unroll
-              for (int j = 0; j < N; ++j) {
-                yv[j] = yl[j * ST];
-                if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
-                else ev = fma(A.tb.lv[j], yv[j], ev);
-              }
-              const T xp = ev + od, xm = ev - od;  // own traces at x^_a = 1 and 0
-              // other side: neighbour trace, or the PEC mirror (E: -own, H: +own)
-              const T op = hasp ? ntp[i * N2 + t] : ((fp == 0) ? neg_bits(xp) : xp);
-              const T om = hasm ? ntm[i * N2 + t] : ((fp == 0) ? neg_bits(xm) : xm);
-              const T jp = xp - op, jm = xm - om;
-              const T sp = jp + jm, dm = jp - jm;
-              T* Rl = Rp + i * N3 + base;
-              if constexpr (KAP) {
-                // own traces of y^f_c; on a PEC face the E jump is the own trace (E - g, g in
-                // the load) and the H jump 0; lifted with L_al(1) and L_al(0) = (-1)^al L_al(1)
-                const T* zl = zb + i * N3 + base;
-                T ze = T(0), zo = T(0);
-#pragma unroll
-                for (int j = 0; j < N; ++j) {
-                  if (j & 1) zo = fma(A.tb.lv[j], zl[j * ST], zo);
-                  else ze = fma(A.tb.lv[j], zl[j * ST], ze);
-                }
-                const T zp = ze + zo, zm = ze - zo;
-                const T gop = hasp ? gtp[i * N2 + t] : (f == 0 ? T(0) : zp);
-                const T gom = hasm ? gtm[i * N2 + t] : (f == 0 ? T(0) : zm);
-                const T dp = kpp * (zp - gop), dn = kpm * (zm - gom);
-                const T zev = fma(-sg * A.tb.hf[0], dm, dp + dn), zod = fma(-sg * A.tb.hf[0], sp, dp - dn);
-#pragma unroll
-                for (int al = 0; al < N; ++al) {
-                  T r2 = Rl[al * ST];
-                  r2 = fma(A.tb.lv[al], (al & 1) ? zod : zev, r2);
-#pragma unroll
-                  for (int be = 0; be < N; ++be)
-                    if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
-                  Rl[al * ST] = r2;
-                }
-              } else {
-                // flux lift folded into the curl operand as in k_apply
-                constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
-                if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
-                if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
-#pragma unroll
-                for (int al = 0; al < N; ++al) {
-                  T r2 = Rl[al * ST];
-                  if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
-#pragma unroll
-                  for (int be = 0; be < N; ++be)
-                    if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
-                  Rl[al * ST] = r2;
-                }
-              }
-            }
-          }
-        };
-        with_axis(a, [&](auto ac) {
-          if (neg) lines(ac, std::true_type{});
-          else lines(ac, std::false_type{});
-        });
-        __syncwarp();
-      }
+      fused_lines<T, N, Q, KAP>(A, e, f, c, ys, nt, nb, Rp, lane);
       // the Q planes of (f, c) are contiguous in R
       T* Rg = A.R + re + fc * Q * N3;
       for (int s2 = lane; s2 < Q * N3; s2 += 32) Rg[s2] = Rp[s2];
@@ -1018,11 +1034,12 @@ __host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
 // generic inputs; (b) stages each neighbour's two tangential component blocks into shared
 // memory with coalesced cp.async copies (one warp per (face, field), two rounds of six) and
 // forms its face traces from there, so the strided trace reads hit shared memory, not L1/L2;
-// (c) the line passes are k_fused's; (d) the residual block leaves shared memory by one bulk
+// (c) the line passes (fused_lines, shared with k_fused; with KAP the dissipative term D_h);
+// (d) the residual block leaves shared memory by one bulk
 // copy (cp.async.bulk, completion by bulk-group waits, no polling), placed in shared memory at
 // its offset modulo 16 bytes in R so only the at most 3 + 3 floats around the 16-byte aligned
 // body need plain stores.  Launched with 192 threads (six warps).
-template <int P, int Q>
+template <int P, int Q, bool KAP = false>
 __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
   using T = float;
   if (A.skip && *A.skip) return;
@@ -1174,62 +1191,9 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
     __syncthreads();
     if (failed) break;  // uniform: read after the barrier
     // (c) residual planes: one warp per (field, component), all Q temporal test modes
-    for (int fc = warp; fc < 6; fc += 6) {
-      const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f, fp = 1 - f;
-      T* Rp = Rs + fc * Q * N3;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int a = (k == 0) ? (c == 0 ? 1 : 0) : (c == 2 ? 1 : 2);
-        const int b = 3 - c - a;
-        const int bi = (a == 0) ? b - 1 : (a == 1 ? b / 2 : b);
-        const bool neg = ((f == 0) == (((a - c + 3) % 3) == 1));
-        const T* yb = ys + (fp * 3 + b) * Q * N3;
-        const bool hasp = nb[2 * a + 1] >= 0, hasm = nb[2 * a] >= 0;
-        const T* ntp = nt + ((((2 * a + 1) * 2 + fp) * 2 + bi) * Q) * N2;
-        const T* ntm = nt + ((((2 * a) * 2 + fp) * 2 + bi) * Q) * N2;
-        auto lines = [&](auto ac, auto negc) {
-          constexpr int AX = decltype(ac)::value, ST = line_stride<N, AX>();
-          constexpr T sg = decltype(negc)::value ? T(-1) : T(1);
-          for (int t = lane; t < N2; t += 32) {
-            const int base = line_base<N, AX>(t);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-              const T* yl = yb + i * N3 + base;
-              T yv[N];
-              T ev = T(0), od = T(0);
-#pragma unroll
-              for (int j = 0; j < N; ++j) {
-                yv[j] = yl[j * ST];
-                if (j & 1) od = fma(A.tb.lv[j], yv[j], od);
-                else ev = fma(A.tb.lv[j], yv[j], ev);
-              }
-              const T xp = ev + od, xm = ev - od;
-              const T op = hasp ? ntp[i * N2 + t] : ((fp == 0) ? neg_bits(xp) : xp);
-              const T om = hasm ? ntm[i * N2 + t] : ((fp == 0) ? neg_bits(xm) : xm);
-              const T jp = xp - op, jm = xm - om;
-              const T sp = jp + jm, dm = jp - jm;
-              constexpr int B0 = ((N - 1) & 1) ? N - 1 : N - 2, B1 = ((N - 1) & 1) ? N - 2 : N - 1;
-              if constexpr (B0 >= 1) yv[B0] = fma(A.tb.kq[B0], dm, yv[B0]);
-              if constexpr (B1 >= 2) yv[B1] = fma(A.tb.kq[B1], sp, yv[B1]);
-              T* Rl = Rp + i * N3 + base;
-#pragma unroll
-              for (int al = 0; al < N; ++al) {
-                T r2 = Rl[al * ST];
-                if (al == N - 1) r2 = fma(-sg * A.tb.hf[al], (al & 1) ? sp : dm, r2);
-#pragma unroll
-                for (int be = 0; be < N; ++be)
-                  if (d_nz(al, be)) r2 = fma(sg * A.tb.Dt[al][be], yv[be], r2);
-                Rl[al * ST] = r2;
-              }
-            }
-          }
-        };
-        with_axis(a, [&](auto ac) {
-          if (neg) lines(ac, std::true_type{});
-          else lines(ac, std::false_type{});
-        });
-        __syncwarp();
-      }
+    {
+      const int f = warp >= 3 ? 1 : 0, c = warp - 3 * f;
+      fused_lines<T, N, Q, KAP>(A, e, f, c, ys, nt, nb, Rs + warp * Q * N3, lane);
     }
     // (d) the residual block to R: the 16-byte aligned body by one bulk copy, the at most 3 + 3
     //     floats around it by plain stores
@@ -1290,6 +1254,8 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       cudaFuncSetAttribute(k_fused<T, P, Q, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fused);
       cudaFuncSetAttribute(k_fused_kry<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fused_kry_smem(P, Q));
+      cudaFuncSetAttribute(k_fused_kry<P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_kry_smem(P, Q));
     }
     cudaGetLastError();
   });
@@ -1302,19 +1268,23 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       // six warps: the 6 Q residual planes and the 24 neighbour-trace tasks divide evenly
       constexpr int kFusedThreads = 192;
       (void)block;
-      static std::atomic<int> cap_t[64], cap_f[64], cap_k[64], cap_dt[64], cap_df[64];
+      static std::atomic<int> cap_t[64], cap_f[64], cap_k[64], cap_dt[64], cap_df[64], cap_dk[64];
+      const bool krylov = fused_kry_smem(P, Q) <= 74 * 1024 && args.pinv && !args.u0 && !args.b && args.mass &&
+                          !args.mass3;  // the operator A P^{-1} v of the mixed-precision solve
       if (args.kap) {
         // the dissipative term D_h (Sec. 4.2) in the same single pass
-        if (args.pinv)
+        if (krylov)
+          k_fused_kry<P, Q, true><<<wave_grid(k_fused_kry<P, Q, true>, kFusedThreads, fused_kry_smem(P, Q), grid,
+                                              cap_dk),
+                                    kFusedThreads, fused_kry_smem(P, Q), s>>>(args);
+        else if (args.pinv)
           k_fused<T, P, Q, true, true><<<wave_grid(k_fused<T, P, Q, true, true>, kFusedThreads, sm_fused, grid, cap_dt),
                                          kFusedThreads, sm_fused, s>>>(args);
         else
           k_fused<T, P, Q, false, true>
               <<<wave_grid(k_fused<T, P, Q, false, true>, kFusedThreads, sm_fused, grid, cap_df), kFusedThreads,
                  sm_fused, s>>>(args);
-      } else if (fused_kry_smem(P, Q) <= 74 * 1024 && args.pinv && !args.u0 && !args.b && args.mass &&
-                 !args.mass3) {
-        // the Krylov operator A P^{-1} v of the mixed-precision solve
+      } else if (krylov) {
         const size_t smk = fused_kry_smem(P, Q);
         k_fused_kry<P, Q><<<wave_grid(k_fused_kry<P, Q>, kFusedThreads, smk, grid, cap_k), kFusedThreads, smk, s>>>(
             args);
