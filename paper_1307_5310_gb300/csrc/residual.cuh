@@ -1028,10 +1028,12 @@ __host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
   return kry_stage_offset(P, Q) + sizeof(float) * 12 * stage_slot(Q * (P + 1) * (P + 1) * (P + 1)) + 6 * 8;
 }
 
-// Single-pass FP32 Krylov apply A P^{-1} v on uniform brick meshes (no slab-start mode, no
-// load): the inner operator of the mixed-precision solve.  Same arithmetic as k_fused with
-// PRE, specialised: (a) forms y = sc B v and the mass term (v itself) with no branches on the
-// generic inputs; (b) stages each neighbour's two tangential component blocks into shared
+// Single-pass FP32 Krylov operator on uniform meshes (no slab-start mode, no load): the inner
+// operator of the mixed-precision solve.  MODE 0: A P^{-1} v on bricks (P^{-1} on load, the
+// mass term is v itself); MODE 1: A z on curved elements, the mass term already in R (the
+// tensor-core or CUDA-core curved mass, z = P^{-1} v from the 3x3 block pass); MODE 2: A z on
+// general affine elements (constant 3x3 metric mass).  Same arithmetic as k_fused,
+// specialised: (a) forms y = sc B v and the mass term with no branches on the generic inputs; (b) stages each neighbour's two tangential component blocks into shared
 // memory with coalesced cp.async copies (one warp per (face, field), two rounds of six) and
 // forms its face traces from there, so the strided trace reads hit shared memory, not L1/L2;
 // (c) the line passes (fused_lines, shared with k_fused; with KAP the dissipative term D_h);
@@ -1039,7 +1041,7 @@ __host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
 // copy (cp.async.bulk, completion by bulk-group waits, no polling), placed in shared memory at
 // its offset modulo 16 bytes in R so only the at most 3 + 3 floats around the 16-byte aligned
 // body need plain stores.  Launched with 192 threads (six warps).
-template <int P, int Q, bool KAP = false>
+template <int P, int Q, bool KAP = false, int MODE = 0>
 __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
   using T = float;
   if (A.skip && *A.skip) return;
@@ -1109,7 +1111,7 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
 #pragma unroll
     for (int bi = 0; bi < 2; ++bi) {
       const int b = (a == 0) ? 1 + bi : (a == 1 ? 2 * bi : bi);
-      const T sc = A.pinv[en * 6 + fld * 3 + b];
+      const T sc = MODE == 0 ? A.pinv[en * 6 + fld * 3 + b] : T(1);
       T* nto = nt + ((task * 2 + bi) * Q) * N2;
       const T* ub = src[bi];
       with_axis(a, [&](auto ac) {
@@ -1157,16 +1159,25 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
     // the previous element's residual has left shared memory (its bulk copy has read it)
     if (threadIdx.x == 0) bulk_wait_read();
     __syncthreads();
-    // (a) y = sc B v and the mass term v (the mass block times P^{-1} is the identity)
+    // (a) y = sc B v and the mass term: on bricks with P^{-1} on load (MODE 0) v itself (the
+    //     mass block times P^{-1} is the identity), on curved elements (MODE 1) the term already
+    //     in R, on general affine elements (MODE 2) the constant 3x3 metric mass of v
     for (int it = threadIdx.x; it < 6 * N3; it += 192) {
       const int fc = it / N3, s = it - fc * N3;
       const T* up = ume + fc * um_cs + s;
       T v[Q];
 #pragma unroll
       for (int m = 0; m < Q; ++m) v[m] = up[m * N3];
-      const T sc = A.pinv[e * 6 + fc];
+      const T sc = MODE == 0 ? A.pinv[e * 6 + fc] : T(1);
       T* yo = ys + fc * Q * N3 + s;
       T* ro = Rs + fc * Q * N3 + s;
+      T mr[3] = {T(0), T(0), T(0)};
+      const T* uf = ume + s;
+      if constexpr (MODE == 2) {
+        const int f = fc >= 3 ? 1 : 0, c = fc - 3 * f;
+        sym3_row(A.mass3 + (e * 2 + f) * 6, c, mr);
+        uf += (f * 3) * um_cs;
+      }
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         T acc = T(0);
@@ -1174,7 +1185,10 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
         for (int m = 1; m <= Q; ++m)
           if (b_nz(i, m)) acc = fma(A.tb.B[i][m], v[m - 1], acc);
         yo[i * N3] = sc * acc;
-        ro[i * N3] = v[i];
+        if constexpr (MODE == 0) ro[i * N3] = v[i];
+        if constexpr (MODE == 1) ro[i * N3] = Rg[(fc * Q + i) * N3 + s];
+        if constexpr (MODE == 2)
+          ro[i * N3] = fma(mr[2], uf[2 * um_cs + i * N3], fma(mr[1], uf[um_cs + i * N3], mr[0] * uf[i * N3]));
       }
     }
     // (b) neighbour traces: two rounds of six (face, field) tasks, one per warp
@@ -1256,6 +1270,10 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
                            (int)fused_kry_smem(P, Q));
       cudaFuncSetAttribute(k_fused_kry<P, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fused_kry_smem(P, Q));
+      cudaFuncSetAttribute(k_fused_kry<P, Q, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_kry_smem(P, Q));
+      cudaFuncSetAttribute(k_fused_kry<P, Q, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_kry_smem(P, Q));
     }
     cudaGetLastError();
   });
@@ -1269,11 +1287,13 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
       constexpr int kFusedThreads = 192;
       (void)block;
       static std::atomic<int> cap_t[64], cap_f[64], cap_k[64], cap_dt[64], cap_df[64], cap_dk[64];
-      const bool krylov = fused_kry_smem(P, Q) <= 74 * 1024 && args.pinv && !args.u0 && !args.b && args.mass &&
-                          !args.mass3;  // the operator A P^{-1} v of the mixed-precision solve
+      // the Krylov operator of the mixed-precision solve (no slab-start mode, no load): bricks with
+      // P^{-1} on load (mode 0), curved with the mass term in R (mode 1), general affine (mode 2)
+      const int kmode = (args.pinv && args.mass && !args.mass3) ? 0 : (!args.pinv && !args.mass && !args.mass3 ? 1 : (!args.pinv && args.mass3 ? 2 : -1));
+      const bool krylov = fused_kry_smem(P, Q) <= 74 * 1024 && !args.u0 && !args.b && kmode >= 0;
       if (args.kap) {
         // the dissipative term D_h (Sec. 4.2) in the same single pass
-        if (krylov)
+        if (krylov && kmode == 0)
           k_fused_kry<P, Q, true><<<wave_grid(k_fused_kry<P, Q, true>, kFusedThreads, fused_kry_smem(P, Q), grid,
                                               cap_dk),
                                     kFusedThreads, fused_kry_smem(P, Q), s>>>(args);
@@ -1286,8 +1306,16 @@ int launch_residual_pq(const ApplyArgs<T>& args, cudaStream_t s, int grid, const
                  sm_fused, s>>>(args);
       } else if (krylov) {
         const size_t smk = fused_kry_smem(P, Q);
-        k_fused_kry<P, Q><<<wave_grid(k_fused_kry<P, Q>, kFusedThreads, smk, grid, cap_k), kFusedThreads, smk, s>>>(
-            args);
+        static std::atomic<int> cap_k1[64], cap_k2[64];
+        if (kmode == 0)
+          k_fused_kry<P, Q><<<wave_grid(k_fused_kry<P, Q>, kFusedThreads, smk, grid, cap_k), kFusedThreads, smk, s>>>(
+              args);
+        else if (kmode == 1)
+          k_fused_kry<P, Q, false, 1><<<wave_grid(k_fused_kry<P, Q, false, 1>, kFusedThreads, smk, grid, cap_k1),
+                                        kFusedThreads, smk, s>>>(args);
+        else
+          k_fused_kry<P, Q, false, 2><<<wave_grid(k_fused_kry<P, Q, false, 2>, kFusedThreads, smk, grid, cap_k2),
+                                        kFusedThreads, smk, s>>>(args);
       } else if (args.pinv)
         k_fused<T, P, Q, true><<<wave_grid(k_fused<T, P, Q, true>, kFusedThreads, sm_fused, grid, cap_t),
                                  kFusedThreads, sm_fused, s>>>(args);
