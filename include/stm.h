@@ -190,7 +190,10 @@ int32_t stm_operator_apply(stm_ctx *ctx, double dt, const void *V, void *W, int3
                            int32_t prec, int32_t mem);
 
 /* Set the state (spatial coefficients of E and H at time t, state layout,
- * double).  The next slab starts from it. */
+ * double).  The next slab starts from it.  With mem = STM_MEM_HOST, host memory
+ * the device addresses directly (from stm_host_alloc, cudaMallocHost or
+ * registered) is moved by a copy kernel over the host link, other host memory
+ * by the copy engines; both calls return when the transfer is complete. */
 int32_t stm_set_state(stm_ctx *ctx, double t, const void *u, int32_t mem);
 int32_t stm_get_state(stm_ctx *ctx, double *t, void *u, int32_t mem);
 

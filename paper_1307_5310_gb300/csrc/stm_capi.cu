@@ -436,6 +436,36 @@ int res_grid(const stm_ctx* c, int64_t count) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(count, 1 << 30));
 }
 
+__global__ void k_copy_words(double* __restrict__ dst, const double* __restrict__ src, int64_t n, int vec);
+
+// Moves n doubles between host and device memory on the context stream (to_device: src on the
+// host, dst on the device; otherwise the reverse).  Host memory the device addresses directly (page-locked by
+// stm_host_alloc or cudaMallocHost, or registered) is read or written by a copy kernel: its
+// concurrent requests keep the host link busy where a copy-engine transfer of a large buffer
+// stalls on its first touch after other device work; other host memory goes through
+// cudaMemcpyAsync.
+int host_transfer(stm_ctx* c, double* dst, const double* src, int64_t n, bool to_device) {
+  const void* host = to_device ? (const void*)src : (const void*)dst;
+  cudaPointerAttributes at{};
+  const bool mapped = cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                      at.devicePointer != nullptr;
+  cudaGetLastError();
+  if (mapped && n > 0) {
+    double* hd = (double*)at.devicePointer;
+    double* d = to_device ? dst : hd;
+    const double* s = to_device ? hd : src;
+    const int vec = ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(s)) & 15) == 0 ? 1 : 0;
+    const int64_t blocks = std::min<int64_t>((int64_t)c->sms * 16, std::max<int64_t>(1, (n / 2 + 255) / 256));
+    k_copy_words<<<(int)blocks, 256, 0, c->stream>>>(d, s, n, vec);
+    c->launches += 1;
+    STM_CK(cudaGetLastError());
+    return STM_OK;
+  }
+  STM_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                         c->stream));
+  return STM_OK;
+}
+
 // STM_ETIMEOUT if a bounded wait of the FP32 Krylov kernel on its asynchronous copies ran out
 // (the flag stays set: every later result of the context is suspect), else STM_OK.
 int check_wait_err(stm_ctx* c) {
@@ -1125,6 +1155,22 @@ __global__ void __launch_bounds__(256) k_fma_probe(double* out, int iters, doubl
 #pragma unroll
   for (int k = 0; k < kProbeChains; ++k) acc += v[k];
   out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = acc;
+}
+
+// dst[i] = src[i] for n 8-byte words, one side in host memory the device addresses directly
+// (page-locked or registered): the SMs' many concurrent requests stream over the host link
+// without the copy engines' first-touch stalls.  vec: both pointers 16-byte aligned.
+__global__ void k_copy_words(double* __restrict__ dst, const double* __restrict__ src, int64_t n, int vec) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const int64_t n2 = n / 2;
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    for (int64_t i = tid; i < n2; i += nth) d2[i] = s2[i];
+    if (tid == 0 && (n & 1)) dst[n - 1] = src[n - 1];
+  } else {
+    for (int64_t i = tid; i < n; i += nth) dst[i] = src[i];
+  }
 }
 
 __global__ void k_init_guess(double* x, const double* state, int64_t q, int64_t n3, int64_t n) {
@@ -2029,8 +2075,12 @@ int32_t stm_operator_apply(stm_ctx* c, double dt, const void* V, void* W, int32_
 
 int32_t stm_set_state(stm_ctx* c, double t, const void* u, int32_t mem) {
   if (!c || !u) return STM_EINVAL;
-  STM_CK(cudaMemcpyAsync(c->state, u, c->n_state * sizeof(double),
-                         mem == STM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+  if (mem == STM_MEM_HOST) {
+    int rc = host_transfer(c, c->state, (const double*)u, c->n_state, true);
+    if (rc) return rc;
+  } else {
+    STM_CK(cudaMemcpyAsync(c->state, u, c->n_state * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
   STM_CK(cudaStreamSynchronize(c->stream));
   c->t = t;
   return STM_OK;
@@ -2038,8 +2088,12 @@ int32_t stm_set_state(stm_ctx* c, double t, const void* u, int32_t mem) {
 
 int32_t stm_get_state(stm_ctx* c, double* t, void* u, int32_t mem) {
   if (!c || !u) return STM_EINVAL;
-  STM_CK(cudaMemcpyAsync(u, c->state, c->n_state * sizeof(double),
-                         mem == STM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  if (mem == STM_MEM_HOST) {
+    int rc = host_transfer(c, (double*)u, c->state, c->n_state, false);
+    if (rc) return rc;
+  } else {
+    STM_CK(cudaMemcpyAsync(u, c->state, c->n_state * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
   STM_CK(cudaStreamSynchronize(c->stream));
   if (t) *t = c->t;
   return STM_OK;

@@ -78,6 +78,37 @@ def test_residual_device_memory(stm):
     assert np.array_equal(Rd.cpu().numpy(), Rh)  # same kernels, same order: bitwise
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_state_transfer_page_locked(stm, offset):
+    """stm_set_state / stm_get_state with page-locked host buffers (the kernel transfer; offset 1
+    misaligns the buffers by 8 bytes, the scalar variant), pageable numpy arrays (the copy
+    engines) and device memory all move the state bit for bit."""
+    import torch
+
+    m = meshgen.box_mesh(3, 2, 2, p=3, q=2, order="morton")
+    s = stm.Slab(m)
+    n = s.n_state
+    u = np.random.Generator(np.random.PCG64(41)).uniform(-1, 1, n)
+    hin, hout = stm.HostBuffer(n + 1), stm.HostBuffer(n + 1)
+    a_in, a_out = hin.array[offset:offset + n], hout.array[offset:offset + n]
+    a_in[:] = u
+    a_out[:] = 0.0
+    s.set_state(a_in, t=0.25)
+    back, t = s.get_state(a_out)
+    assert t == 0.25 and np.array_equal(a_out, u)
+    plain, _ = s.get_state(np.empty(n))
+    assert np.array_equal(plain, u)
+    ud = torch.empty(n, dtype=torch.float64, device="cuda")
+    s.get_state(ud)
+    torch.cuda.synchronize()
+    assert np.array_equal(ud.cpu().numpy(), u)
+    s.set_state(np.ascontiguousarray(u[::-1]))
+    s.get_state(a_out)
+    assert np.array_equal(a_out, u[::-1])
+    hin.close()
+    hout.close()
+
+
 def test_energy_and_projection(stm):
     m = meshgen.box_mesh(3, 2, 2, hi=(1.0, 0.5, 0.8), p=3, q=1)
     meshgen.random_materials(m, 1, 9)
