@@ -744,7 +744,7 @@ def serving_stream(n_req, n_max, rate=50.0, seed=1311):
     return reqs, np.cumsum(gaps)
 
 
-def run_stream(reqs, arrivals, precision, workers=8):
+def run_stream(reqs, arrivals, precision, workers=16):
     """Submit the stream at its arrival times to a server and wait for every result."""
     from paper_1307_5310_gb300 import stm
 
@@ -774,7 +774,7 @@ def leg_serving(n_req=48, n_max=24, rate=50.0, seed=1311):
     from paper_1307_5310_gb300 import stm
 
     reqs, arrivals = serving_stream(n_req, n_max, rate, seed)
-    out = {"requests": n_req, "offered_req_per_s": rate, "workers": 8,
+    out = {"requests": n_req, "offered_req_per_s": rate, "workers": 16,
            "workload": f"Poisson stream (mean {rate:g} req/s) of {n_req} requests; n^3 unit-cube bricks, n "
                        f"log-uniform in [8,{n_max}] (x4), p~U{{2..6}}, q~U{{1..3}}, 1-4 eps/mu boxes U[1,4], "
                        "1-3 Gaussian pulses, cavity or scattering, 10 slabs each to 1e-9 relative residual"}
