@@ -913,20 +913,6 @@ __global__ void __launch_bounds__(192) k_fused(ApplyArgs<T> A) {
   }
 }
 
-// ---- asynchronous global -> shared copies (cp.async, no register round trip) ----
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // ---- bulk copies shared -> global through the tensor memory accelerator (bulk groups) ----
 // Orders this thread's earlier shared-memory writes before later async-proxy reads of them.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -976,11 +962,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int tr
   return false;
 }
 
-// One warp copies the n floats at src (4-byte aligned) into the 16-byte aligned slot (layout as
-// stage_warp): lane 0 issues the 16-byte aligned body as one bulk copy completing on `bar`, the
-// at most 3 + 3 floats around it move by plain loads and stores.  Returns the body's bytes (the
-// caller announces the sum of a round's bodies on `bar` before the copies are issued: see
-// stage_bytes) and sets *dst_out.
+// Staging of n floats at src (4-byte aligned) into a 16-byte aligned shared-memory slot: float
+// k lands at the returned pointer + k, which sits at the same offset modulo 16 bytes as src.
+// stage_bytes: the bytes of the 16-byte aligned body, which the caller announces on the
+// barrier before the copies are issued.  stage_warp_bulk (one warp): lane 0 issues the body as
+// one bulk copy completing on `bar`; the at most 3 + 3 floats around it move by plain loads and
+// stores (visible to the warp after the barrier wait and a __syncwarp).
 __device__ __forceinline__ int stage_bytes(const float* src, int n) {
   const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
   const int head = min((4 - mis) & 3, n);
@@ -1002,22 +989,6 @@ __device__ __forceinline__ const float* stage_warp_bulk(float* slot, const float
 // Floats of a staging slot for n floats: n plus up to 3 of alignment shift, rounded to 16 bytes.
 __host__ __device__ constexpr int stage_slot(int n) { return (n + 6) & ~3; }
 
-// One warp copies the n floats at src (4-byte aligned) into the 16-byte aligned slot so that
-// float k lands at the returned pointer + k, which sits at the same offset modulo 16 bytes as
-// src: the body moves in 16-byte chunks, the at most 3 + 3 floats around it in 4-byte ones.
-// Completion: cp_async_commit, cp_async_wait_all, then __syncwarp.
-__device__ __forceinline__ const float* stage_warp(float* slot, const float* src, int n, int lane) {
-  const int mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
-  float* dst = slot + mis;
-  const int head = min((4 - mis) & 3, n);
-  const int nb = (n - head) >> 2;
-  const int t0 = head + 4 * nb;
-  for (int k = lane; k < nb; k += 32) cp_async16(dst + head + 4 * k, src + head + 4 * k);
-  if (lane < head) cp_async4(dst + lane, src + lane);
-  if (lane < n - t0) cp_async4(dst + t0 + lane, src + t0 + lane);
-  return dst;
-}
-
 // Shared memory of k_fused_kry: k_fused's (the residual block with 4 floats of slack) plus six
 // warps' two staging slots each.
 __host__ __device__ constexpr size_t kry_stage_offset(int P, int Q) {
@@ -1033,14 +1004,17 @@ __host__ __device__ constexpr size_t fused_kry_smem(int P, int Q) {
 // mass term is v itself); MODE 1: A z on curved elements, the mass term already in R (the
 // tensor-core or CUDA-core curved mass, z = P^{-1} v from the 3x3 block pass); MODE 2: A z on
 // general affine elements (constant 3x3 metric mass).  Same arithmetic as k_fused,
-// specialised: (a) forms y = sc B v and the mass term with no branches on the generic inputs; (b) stages each neighbour's two tangential component blocks into shared
-// memory with coalesced cp.async copies (one warp per (face, field), two rounds of six) and
-// forms its face traces from there, so the strided trace reads hit shared memory, not L1/L2;
-// (c) the line passes (fused_lines, shared with k_fused; with KAP the dissipative term D_h);
-// (d) the residual block leaves shared memory by one bulk
-// copy (cp.async.bulk, completion by bulk-group waits, no polling), placed in shared memory at
-// its offset modulo 16 bytes in R so only the at most 3 + 3 floats around the 16-byte aligned
-// body need plain stores.  Launched with 192 threads (six warps).
+// specialised:
+//  (a) forms y = sc B v and the mass term with no branches on the generic inputs;
+//  (b) stages each neighbour's two tangential component blocks into shared memory by bulk
+//      copies (one warp per (face, field), two batches of six, completion on the warp's
+//      mbarrier with bounded polling) and forms its face traces from there, so the strided
+//      trace reads hit shared memory, not L1/L2;
+//  (c) the line passes (fused_lines, shared with k_fused; with KAP the dissipative term D_h);
+//  (d) the residual block leaves shared memory by one bulk copy (completion by bulk-group
+//      waits, no polling), placed in shared memory at its offset modulo 16 bytes in R so only
+//      the at most 3 + 3 floats around the 16-byte aligned body need plain stores.
+// Launched with 192 threads (six warps).
 template <int P, int Q, bool KAP = false, int MODE = 0>
 __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
   using T = float;
@@ -1088,9 +1062,9 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
     for (int bi = 0; bi < 2; ++bi) src[bi] = stage_warp_bulk(slot + bi * SS, cs[bi], Q * N3, lane, bar);
     return true;
   };
-  // waits for the round's copies (bounded: 1 << 22 polls), then makes the plain-stored floats
+  // waits for the batch's copies (bounded: 1 << 22 polls), then makes the plain-stored floats
   // of the other lanes visible; false if the wait ran out
-  bool my_fail = false;  // this warp's copies of the round that timed out may still be in flight
+  bool my_fail = false;  // this warp's copies of the batch that timed out may still be in flight
   auto arrived = [&]() -> bool {
     const bool ok = mbar_wait(bar, parity, 1 << 22);
     parity ^= 1;
@@ -1153,7 +1127,7 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
     T* Rg = A.R + e * (int64_t)EB;
     const int shift = (int)((reinterpret_cast<uintptr_t>(Rg) >> 2) & 3);
     T* Rs = Rb + shift;
-    // round 1 of the neighbour copies in flight while the own block is contracted
+    // the first batch of neighbour copies in flight while the own block is contracted
     const T* src[2];
     bool have = issue(e, warp, src);
     // the previous element's residual has left shared memory (its bulk copy has read it)
@@ -1191,7 +1165,7 @@ __global__ void __launch_bounds__(192) k_fused_kry(ApplyArgs<float> A) {
           ro[i * N3] = fma(mr[2], uf[2 * um_cs + i * N3], fma(mr[1], uf[um_cs + i * N3], mr[0] * uf[i * N3]));
       }
     }
-    // (b) neighbour traces: two rounds of six (face, field) tasks, one per warp
+    // (b) neighbour traces: two batches of six (face, field) tasks, one per warp
     bool ok = true;
     if (have) {
       ok = arrived();
