@@ -439,11 +439,11 @@ int res_grid(const stm_ctx* c, int64_t count) {
 __global__ void k_copy_words(double* __restrict__ dst, const double* __restrict__ src, int64_t n, int vec);
 
 // Moves n doubles between host and device memory on the context stream (to_device: src on the
-// host, dst on the device; otherwise the reverse).  Host memory the device addresses directly (page-locked by
-// stm_host_alloc or cudaMallocHost, or registered) is read or written by a copy kernel: its
-// concurrent requests keep the host link busy where a copy-engine transfer of a large buffer
-// stalls on its first touch after other device work; other host memory goes through
-// cudaMemcpyAsync.
+// host, dst on the device; otherwise the reverse).  Host memory the device addresses directly
+// (page-locked by stm_host_alloc or cudaMallocHost, or registered) is read or written by a copy
+// kernel: its concurrent requests keep the host link busy where a copy-engine transfer of a
+// large buffer stalls on its first touch after other device work; other host memory goes
+// through cudaMemcpyAsync.
 int host_transfer(stm_ctx* c, double* dst, const double* src, int64_t n, bool to_device) {
   const void* host = to_device ? (const void*)src : (const void*)dst;
   cudaPointerAttributes at{};
@@ -546,8 +546,16 @@ int apply(stm_ctx* c, double dt, const T* um, int um_layout, const T* u0, int u0
       for (int k = 0; ok && k < stm_ctx::kAux; ++k)
         ok = cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
-      if (!ok) {
+      if (!ok) {  // leave nothing half made: the next call tries again
         cudaGetLastError();
+        for (int k = 0; k < stm_ctx::kAux; ++k) {
+          if (c->aux[k]) cudaStreamDestroy(c->aux[k]);
+          if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+          c->aux[k] = nullptr;
+          c->join_ev[k] = nullptr;
+        }
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        c->fork_ev = nullptr;
         return fail(c, STM_EDEVICE, "auxiliary stream set-up failed");
       }
     }
