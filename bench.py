@@ -938,10 +938,10 @@ def run_ours(args):
         k32 = pm["k_apply_fp32"]
         k32_ms = k32[0] / max(1, k32[1])
         by = linop_bytes_per_element(args.p, args.q, 4) * ne  # the solve's FP32 applies are A P^{-1} v
-        # DRAM bytes per k_fused_kry launch: one ncu capture inside the 32^3 mixed solve (350.0 MB read +
-        # 261.1 MB written), scaled by the element count; p=4, q=3 only
+        # DRAM bytes per k_fused_kry launch: one ncu capture inside the 32^3 mixed solve (347.0 MB read +
+        # 260.7 MB written), scaled by the element count; p=4, q=3 only
         kry43 = (args.p, args.q) == (4, 3)
-        traffic32 = 611.1e6 * ne / 32 ** 3 if kry43 else None
+        traffic32 = 607.7e6 * ne / 32 ** 3 if kry43 else None
         traffic32_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, 32^3 mixed-solve capture x "
                          f"{ne / 32 ** 3:g} (bytes)") if kry43 else None
         mixed["fp32_kernel"] = {"kernel": fp32_krylov_kernel(args.p, args.q), "launch_ms": k32_ms,
