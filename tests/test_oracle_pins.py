@@ -716,3 +716,63 @@ def test_time_derivative_form_closed_form(p, q):
         want.append((mat[:, None, None, None] * G[None, :, None, None] * r).ravel())
     want = np.concatenate(want)
     assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def _time_derivative_pin_error(m, U, dt):
+    """Largest deviation of Oracle.time_derivative from mat_f G_c (U_{i+1} - delta_i0 U_0)."""
+    orc = stdg.Oracle(m)
+    got = orc.time_derivative(U, dt)
+    p, q = int(m["p"][0]), int(m["q"][0])
+    n3 = (p + 1) ** 3
+    lo, hi = np.min(m["vert"], axis=0), np.max(m["vert"], axis=0)
+    ncell = np.array([len(np.unique(m["vert"][:, d])) - 1 for d in range(3)])
+    h = (hi - lo) / ncell
+    G = np.array([h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2]])
+    want = []
+    for e in range(orc.ne):
+        u = U[e * 6 * (q + 1) * n3:(e + 1) * 6 * (q + 1) * n3].reshape(2, 3, q + 1, n3)
+        mat = np.array([m["eps"][e], m["mu"][e]])
+        r = u[:, :, 1:, :].copy()
+        r[:, :, 0, :] -= u[:, :, 0, :]
+        want.append((mat[:, None, None, None] * G[None, :, None, None] * r).ravel())
+    want = np.concatenate(want)
+    return np.max(np.abs(got - want)) / np.max(np.abs(want))
+
+
+def test_planted_mistakes_fail_time_derivative_pin(monkeypatch):
+    """The closed-form pin of Eq. preconditioner catches a dropped Jacobian, eps and mu
+    swapped, and the derivative of the wrong trial functions."""
+    m = meshgen.box_mesh(3, 2, 1, hi=(0.9, 0.5, 0.2), p=1, q=2)
+    meshgen.random_materials(m, 81, 82)
+    U = meshgen.random_coeffs(m, 83)
+    dt = 0.05
+    assert _time_derivative_pin_error(m, U, dt) < 1e-13
+
+    # 1) eps and mu swapped in the form
+    orig_init = stdg.Oracle.__init__
+
+    def swapped(self, mesh, c_diss=0.0):
+        orig_init(self, mesh, c_diss)
+        self.eps, self.mu = self.mu, self.eps
+    monkeypatch.setattr(stdg.Oracle, "__init__", swapped)
+    assert _time_derivative_pin_error(m, U, dt) > 1e-3
+    monkeypatch.setattr(stdg.Oracle, "__init__", orig_init)
+
+    # 2) the measure J dropped from the projection weights
+    orig_tp = stdg._test_project
+
+    def no_measure(a, pts, Lt, wgt):
+        return orig_tp(a, pts, Lt, wgt / pts.J[None, :])
+    monkeypatch.setattr(stdg, "_test_project", no_measure)
+    assert _time_derivative_pin_error(m, U, dt) > 1e-3
+    monkeypatch.setattr(stdg, "_test_project", orig_tp)
+
+    # 3) the time derivative taken of the test basis instead of the trial basis
+    orig_trial = stdg.trial_time_nk
+
+    def wrong_deriv(q, nk, tau, deriv=False):
+        out = orig_trial(q, nk, tau, deriv)
+        return out[::-1] if deriv else out
+    monkeypatch.setattr(stdg, "trial_time_nk", wrong_deriv)
+    assert _time_derivative_pin_error(m, U, dt) > 1e-3
+
