@@ -289,3 +289,7 @@ def test_headline_full_size_sampled(stm):
     W32 = torch.empty(s.n_test, dtype=torch.float32, device="cuda")
     s.operator_apply(V.float(), W32, dt, pre=True, prec=stm.STM_FP32)
     check(W32, Ux.ravel(), 2e-6)
+    # hand the ~35 GB of full-size buffers back to the device for the tests that follow
+    s.close()
+    del X, V, W, W32
+    torch.cuda.empty_cache()
