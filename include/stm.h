@@ -176,7 +176,10 @@ int32_t stm_residual_apply(stm_ctx *ctx, double t0, double dt, const void *U, vo
  * a function of the unknown temporal modes 1..q (slab start mode 0 = 0, no load
  * L), P the block-diagonal preconditioner of Eq. preconditioner (the time-
  * derivative terms (eps d_t E, v) + (mu d_t H, w)); on trilinear and general
- * affine meshes P^{-1} is the cell-mean 3x3 block inverse the solver uses.  V and
+ * affine meshes P^{-1} is the cell-mean 3x3 block inverse the solver uses, and
+ * on time-refined meshes (N_K > 1, where the form couples each sub-interval to
+ * the end value of the one before) the inverse of its diagonal blocks, as in
+ * the solver.  V and
  * W: n_test entries in the test layout (stm_sizes), double (prec = STM_FP64) or
  * float (prec = STM_FP32), in host (mem = STM_MEM_HOST, copied through device
  * buffers the context owns) or device memory (STM_MEM_DEVICE, caller-owned; V is
